@@ -1,0 +1,120 @@
+"""Python access to the CPU oracle (``oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by the package's smoke check and
+by the benchmark's CPU-baseline leg, never by the library's product path.  The
+oracle shares no code with the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``liboracle.so`` (plain C, -O2, FP contraction off so the FP64 offset
+    formula is evaluated exactly as written)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared",
+                               "-ffp-contract=off", "-fno-fast-math", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        P, I, I64, D, F = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_float
+        lib.oracle_offsets.restype = None
+        lib.oracle_offsets.argtypes = [D, I, P, P]
+        lib.oracle_extract.restype = I
+        lib.oracle_extract.argtypes = [P, I, I, I64, P, P, P, P, I, P, P, I, P]
+        lib.oracle_distances.restype = I
+        lib.oracle_distances.argtypes = [P, I, I, I64, I, I, I, I, P, P, I, P, P]
+        lib.oracle_hamming.restype = I
+        lib.oracle_hamming.argtypes = [P, P, I]
+        lib.oracle_match.restype = I
+        lib.oracle_match.argtypes = [P, I, P, I, I, F, P, P, P, P, P]
+        _lib = lib
+    return _lib
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def offsets(scale: float, angle_bin: int):
+    """(dx, dy) int32 arrays of shape (48, 48), indexed [v, u]."""
+    dx = np.zeros((48, 48), dtype=np.int32)
+    dy = np.zeros((48, 48), dtype=np.int32)
+    _load().oracle_offsets(float(scale), int(angle_bin), dx.ctypes.data, dy.ctypes.data)
+    return dx, dy
+
+
+def extract(image: np.ndarray, width: int, height: int, kps: np.ndarray, triplets: np.ndarray,
+            scales=(1.0,)) -> np.ndarray:
+    """Descriptors (n, 64) uint8.  image: (H, pitch) uint8; kps: (n, 4) int32
+    (x, y, angle_bin, scale_idx); triplets (512, 6) uint8."""
+    image = _c(image, np.uint8)
+    kps = _c(kps, np.int32).reshape(-1, 4)
+    n = kps.shape[0]
+    kx, ky, kb, ks = (_c(kps[:, i], np.int32) for i in range(4))
+    trip = _c(triplets, np.uint8).reshape(-1)
+    assert trip.size == 512 * 6
+    sc = _c(scales, np.float64)
+    out = np.zeros((n, 64), dtype=np.uint8)
+    rc = _load().oracle_extract(image.ctypes.data, width, height, image.shape[1], kx.ctypes.data, ky.ctypes.data,
+                                kb.ctypes.data, ks.ctypes.data, n, trip.ctypes.data, sc.ctypes.data, sc.size,
+                                out.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle_extract: invalid scale index or triplet")
+    return out
+
+
+def distances(image: np.ndarray, width: int, height: int, kp, triplets: np.ndarray, scales=(1.0,)):
+    """The two squared patch distances of Eq. 1 for every triplet of one keypoint
+    kp = (x, y, angle_bin, scale_idx).  Returns (d1, d2) int64 arrays of length 512."""
+    image = _c(image, np.uint8)
+    trip = _c(triplets, np.uint8).reshape(-1)
+    sc = _c(scales, np.float64)
+    d1 = np.zeros(512, np.int64)
+    d2 = np.zeros(512, np.int64)
+    rc = _load().oracle_distances(image.ctypes.data, width, height, image.shape[1], int(kp[0]), int(kp[1]),
+                                  int(kp[2]), int(kp[3]), trip.ctypes.data, sc.ctypes.data, sc.size,
+                                  d1.ctypes.data, d2.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle_distances: invalid scale index")
+    return d1, d2
+
+
+def hamming(a: np.ndarray, b: np.ndarray) -> int:
+    a = _c(a, np.uint8)
+    b = _c(b, np.uint8)
+    return int(_load().oracle_hamming(a.ctypes.data, b.ctypes.data, a.size))
+
+
+def match(query: np.ndarray, train: np.ndarray, k: int = 2, ratio: float = 0.8):
+    """Brute-force top-k matching.  Returns dict of arrays idx1, idx2, dist1, dist2, accepted."""
+    q = _c(query, np.uint8).reshape(-1, 64)
+    t = _c(train, np.uint8).reshape(-1, 64)
+    nq, nt = q.shape[0], t.shape[0]
+    idx1 = np.zeros(nq, np.int32)
+    idx2 = np.zeros(nq, np.int32)
+    d1 = np.zeros(nq, np.int32)
+    d2 = np.zeros(nq, np.int32)
+    acc = np.zeros(nq, np.uint8)
+    rc = _load().oracle_match(q.ctypes.data, nq, t.ctypes.data, nt, k, ratio, idx1.ctypes.data, idx2.ctypes.data,
+                              d1.ctypes.data, d2.ctypes.data, acc.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle_match: bad arguments")
+    return {"idx1": idx1, "idx2": idx2, "dist1": d1, "dist2": d2, "accepted": acc}

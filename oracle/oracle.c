@@ -1,0 +1,186 @@
+/*
+ * CPU oracle for the LATCH descriptor (Sec. 3.1, Eq. 1), its oriented and scaled
+ * window sampling (Sec. 3.2, "Memory optimization") and brute-force Hamming
+ * matching (Sec. 4, "Descriptor matching on the GPU").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the library's product path may call,
+ * link or load this file: only the tests, the package's smoke check and the
+ * benchmark's CPU-baseline leg do.  It shares no code, header, table or constant
+ * generator with the CUDA library; the two sides build their sample-offset tables
+ * independently from the same written reading.
+ *
+ * Everything is plain, single-threaded and unblocked, in the order the method is
+ * defined, so that a reader can check it against the paper line by line:
+ *   1. sample the upright 48x48 window at the keypoint's angle bin and scale;
+ *   2. for each of the 512 triplets compute the two squared Frobenius distances
+ *      between 7x7 patches (Eq. 1) and set the bit when the first is larger;
+ *   3. pack the bits least-significant first;
+ *   4. match by computing every Hamming distance and taking the two smallest.
+ *
+ * Readings where the paper is silent (all parity is pinned by the tests):
+ *   - angle bin b in 0..31 means theta = 2*pi*b/32; b is taken modulo 32;
+ *   - window coordinates a = u - 24, e = v - 24 for u, v in 0..47;
+ *   - sample offset dx = rha(s*(cos*a - sin*e)), dy = rha(s*(sin*a + cos*e)),
+ *     evaluated in FP64 in exactly that order without contraction, rha = round
+ *     half away from zero; cos/sin from libm for the 7 in-quadrant bins, exact
+ *     quarter turns;
+ *   - samples outside the image read as 0; intensities are the raw 8-bit values;
+ *   - Eq. 1 is strict: equal distances give bit 0;
+ *   - bit t is bit (t mod 8) of byte t/8;
+ *   - matching: lowest distance, ties to the lowest train index; the second match
+ *     is the best over the other train indices; accepted iff 1000*d1 < r*d2 with
+ *     r = rha(1000*ratio); an absent second match has distance 65535.
+ * Parity pins: every function here is pinned by tests (closed forms, invariants,
+ * brute force against full sorting); none is unpinned.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define WIN 48
+#define HALF 24
+#define NBITS 512
+#define PATCH_R 3
+
+/* Sample-offset table for one angle bin and scale (Sec. 3.2, "Memory optimization":
+ * the rotated window is loaded as an upright square).  dx/dy are indexed v*48+u. */
+void oracle_offsets(double scale, int bin, int32_t *dx, int32_t *dy) {
+    int b = ((bin % 32) + 32) % 32;
+    int quarter = b / 8, r = b % 8;
+    double c = 1.0, s = 0.0;
+    if (r != 0) {
+        c = cos((double)r * M_PI / 16.0);
+        s = sin((double)r * M_PI / 16.0);
+    }
+    for (int k = 0; k < quarter; ++k) { /* rotate the direction by +90 degrees */
+        double t = c;
+        c = -s;
+        s = t;
+    }
+    for (int v = 0; v < WIN; ++v)
+        for (int u = 0; u < WIN; ++u) {
+            double a = (double)(u - HALF), e = (double)(v - HALF);
+            double fx = scale * (c * a - s * e);
+            double fy = scale * (s * a + c * e);
+            dx[v * WIN + u] = (int32_t)round(fx);
+            dy[v * WIN + u] = (int32_t)round(fy);
+        }
+}
+
+/* Squared Frobenius distance between two 7x7 patches of the window (Eq. 1). */
+static int64_t patch_ssd(const int32_t *win, int px, int py, int qx, int qy) {
+    int64_t acc = 0;
+    for (int i = -PATCH_R; i <= PATCH_R; ++i)
+        for (int j = -PATCH_R; j <= PATCH_R; ++j) {
+            int64_t d = (int64_t)win[(py + i) * WIN + (px + j)] - (int64_t)win[(qy + i) * WIN + (qx + j)];
+            acc += d * d;
+        }
+    return acc;
+}
+
+/* Fill the upright window of one keypoint: window pixel (u, v) is the image pixel at
+ * the keypoint plus the table offset, or 0 outside the image. */
+static void sample_window(const uint8_t *img, int width, int height, int64_t pitch, int32_t x0, int32_t y0,
+                          const int32_t *dx, const int32_t *dy, int32_t *win) {
+    for (int i = 0; i < WIN * WIN; ++i) {
+        int64_t x = (int64_t)x0 + dx[i], y = (int64_t)y0 + dy[i];
+        win[i] = (x >= 0 && x < width && y >= 0 && y < height) ? img[y * pitch + x] : 0;
+    }
+}
+
+/* The two squared distances of Eq. 1 for every triplet of one keypoint:
+ * d1[t] = ||P_A - P_1||^2_F, d2[t] = ||P_A - P_2||^2_F.  Returns -1 on a bad scale. */
+int oracle_distances(const uint8_t *img, int width, int height, int64_t pitch, int32_t kx, int32_t ky, int32_t kbin,
+                     int32_t kscale, const uint8_t *triplets, const double *scales, int nscales, int64_t *d1,
+                     int64_t *d2) {
+    int32_t dx[WIN * WIN], dy[WIN * WIN], win[WIN * WIN];
+    if (kscale < 0 || kscale >= nscales) return -1;
+    oracle_offsets(scales[kscale], kbin, dx, dy);
+    sample_window(img, width, height, pitch, kx, ky, dx, dy, win);
+    for (int t = 0; t < NBITS; ++t) {
+        const uint8_t *tr = triplets + 6 * t;
+        d1[t] = patch_ssd(win, tr[0], tr[1], tr[2], tr[3]);
+        d2[t] = patch_ssd(win, tr[0], tr[1], tr[4], tr[5]);
+    }
+    return 0;
+}
+
+/*
+ * LATCH descriptors for n keypoints (Sec. 3.1 Eq. 1; Sec. 3.2).
+ * img: width x height bytes with row pitch `pitch`.  Keypoint k is
+ * (kx[k], ky[k], kbin[k], kscale[k]) with kscale an index into `scales`.
+ * triplets: 512 records (ax, ay, c1x, c1y, c2x, c2y), each coordinate in [3, 44].
+ * out: n x 64 bytes.  Returns 0, or -1 on an invalid scale index or triplet.
+ */
+int oracle_extract(const uint8_t *img, int width, int height, int64_t pitch, const int32_t *kx, const int32_t *ky,
+                   const int32_t *kbin, const int32_t *kscale, int n, const uint8_t *triplets, const double *scales,
+                   int nscales, uint8_t *out) {
+    int32_t dx[WIN * WIN], dy[WIN * WIN], win[WIN * WIN];
+    for (int t = 0; t < 6 * NBITS; ++t)
+        if (triplets[t] < PATCH_R || triplets[t] > WIN - 1 - PATCH_R) return -1;
+    for (int k = 0; k < n; ++k) {
+        if (kscale[k] < 0 || kscale[k] >= nscales) return -1;
+        oracle_offsets(scales[kscale[k]], kbin[k], dx, dy);
+        sample_window(img, width, height, pitch, kx[k], ky[k], dx, dy, win);
+        uint8_t *d = out + (int64_t)k * (NBITS / 8);
+        memset(d, 0, NBITS / 8);
+        for (int t = 0; t < NBITS; ++t) {
+            const uint8_t *tr = triplets + 6 * t;
+            int64_t d1 = patch_ssd(win, tr[0], tr[1], tr[2], tr[3]); /* ||P_A - P_1||^2 */
+            int64_t d2 = patch_ssd(win, tr[0], tr[1], tr[4], tr[5]); /* ||P_A - P_2||^2 */
+            if (d1 > d2) d[t >> 3] |= (uint8_t)(1u << (t & 7));
+        }
+    }
+    return 0;
+}
+
+/* Hamming distance between two descriptors of `nbytes` bytes: number of differing bits. */
+int oracle_hamming(const uint8_t *a, const uint8_t *b, int nbytes) {
+    int d = 0;
+    for (int i = 0; i < nbytes; ++i) {
+        unsigned x = (unsigned)(a[i] ^ b[i]);
+        while (x) {
+            d += (int)(x & 1u);
+            x >>= 1;
+        }
+    }
+    return d;
+}
+
+/*
+ * Brute-force top-k (k = 1 or 2) Hamming matching with the ratio test (Sec. 4).
+ * For every query: all nt distances, the smallest (lowest index on ties), the
+ * smallest over the remaining indices, then the ratio rule.  Outputs per query:
+ * idx1, idx2 (-1 when absent), d1, d2 (65535 when absent) and accepted (0/1).
+ * Returns 0, or -1 on bad arguments.
+ */
+int oracle_match(const uint8_t *q, int nq, const uint8_t *t, int nt, int k, float ratio, int32_t *idx1,
+                 int32_t *idx2, int32_t *d1, int32_t *d2, uint8_t *accepted) {
+    if (k != 1 && k != 2) return -1;
+    if (!(ratio >= 0.0f && ratio <= 1.0f)) return -1;
+    const int64_t r = (int64_t)round((double)ratio * 1000.0);
+    int32_t *dist = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nt > 0 ? nt : 1));
+    if (!dist) return -1;
+    for (int i = 0; i < nq; ++i) {
+        for (int j = 0; j < nt; ++j) dist[j] = oracle_hamming(q + (int64_t)i * 64, t + (int64_t)j * 64, 64);
+        int b1 = -1, b2 = -1;
+        for (int j = 0; j < nt; ++j)
+            if (b1 < 0 || dist[j] < dist[b1]) b1 = j;
+        if (k == 2)
+            for (int j = 0; j < nt; ++j)
+                if (j != b1 && (b2 < 0 || dist[j] < dist[b2])) b2 = j;
+        idx1[i] = b1;
+        idx2[i] = b2;
+        d1[i] = b1 >= 0 ? dist[b1] : 65535;
+        d2[i] = b2 >= 0 ? dist[b2] : 65535;
+        if (b1 < 0)
+            accepted[i] = 0;
+        else if (k == 1)
+            accepted[i] = 1;
+        else
+            accepted[i] = (uint8_t)(1000 * (int64_t)d1[i] < r * (int64_t)d2[i]);
+    }
+    free(dist);
+    return 0;
+}

@@ -1,0 +1,322 @@
+"""Benchmark: one step = the whole hot path on one image pair of the oriented and
+scaled workload (two 1920x1080 images, 10,000 keypoints each over 32 angle bins
+and 3 scales): extract both descriptor sets, then match 10,000 x 10,000 top-2
+with the 0.8 ratio test.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--path auto|popc|tensor]
+  python bench.py --impl reference ...   # the CPU oracle on a bounded sample
+
+Under torchrun each rank runs its own replica of the pair (independent pairs, no
+collective on the data path); rank 0 prints units of all ranks / max-over-ranks
+time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LATCH descriptors/s + Hamming Gpairs/s (bit-exact); serve p50/p99 latency"
+WORKLOAD = "oriented_scaled_1920x1080_10k"
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="latch", choices=["latch", "reference"])
+    p.add_argument("--path", default="auto", choices=["auto", "popc", "tensor"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sms, maxs, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                maxs.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sms:
+            return None
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(maxs), "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+def _workload():
+    from paper_1609_03986_gb300 import synth
+    return synth.pair(WORKLOAD)
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+
+def _oracle_rates(wl, n_extract: int, n_match: int):
+    """Time the oracle (single-threaded C) on a bounded sample: seconds per
+    descriptor extracted and per query matched against the full train set."""
+    import oracle
+    from paper_1609_03986_gb300 import synth
+    img, kps = wl["images"][0], wl["kps"][0]
+    t0 = time.perf_counter()
+    d0 = oracle.extract(img, wl["width"], wl["height"], kps[:n_extract], wl["triplets"], synth.SCALES)
+    t1 = time.perf_counter()
+    train = oracle.extract(wl["images"][1], wl["width"], wl["height"], wl["kps"][1], wl["triplets"], synth.SCALES)
+    t2 = time.perf_counter()
+    oracle.match(d0[:n_match], train, 2, 0.8)
+    t3 = time.perf_counter()
+    per_desc = ((t1 - t0) + (t2 - t1)) / (n_extract + len(wl["kps"][1]))
+    per_query = (t3 - t2) / n_match
+    return per_desc, per_query
+
+
+def _cpu_step_seconds(wl, per_desc, per_query):
+    n0, n1 = len(wl["kps"][0]), len(wl["kps"][1])
+    return per_desc * (n0 + n1) + per_query * n0
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    wl = _workload()
+    n_desc = len(wl["kps"][0]) + len(wl["kps"][1])
+    # warm-up and timed steps, each a bounded sample scaled to one full step
+    times = []
+    for i in range(args.warmup + args.steps):
+        per_desc, per_query = _oracle_rates(wl, 400, 20)
+        if i >= args.warmup:
+            times.append(_cpu_step_seconds(wl, per_desc, per_query))
+    step_s = statistics.mean(times)
+    value = n_desc / step_s
+    line = {
+        "metric": METRIC, "value": value, "unit": "descriptors/s", "impl": "reference", "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "images": "2 x 1920x1080 u8", "keypoints_per_image": 10000,
+                   "angle_bins": 32, "scales": [1.0, 1.5, 2.25], "match": "10000 x 10000 top-2 ratio 0.8"},
+        "cpu_baseline": {"value": value, "unit": "descriptors/s", "cores": 1, "kind": "oracle",
+                         "sample": "per step: 10,400 descriptors extracted + 20 queries matched against 10,000, "
+                                   "scaled to the full step (20,000 descriptors + 10,000 queries)"},
+        "e2e": {"value": value, "unit": "descriptors/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_latch(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1609_03986_gb300 as P
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    path = {"auto": P.PATH_AUTO, "popc": P.PATH_POPC, "tensor": P.PATH_TENSOR}[args.path]
+
+    wl = _workload()
+    w, h = wl["width"], wl["height"]
+    ctx = P.Context(local, triplets=wl["triplets"])
+    n0, n1 = len(wl["kps"][0]), len(wl["kps"][1])
+    P.latch_reserve(ctx.handle, max(n0, n1), n0, n1)
+    imgs_h = [torch.from_numpy(im).pin_memory() for im in wl["images"]]
+    kps_h = [torch.from_numpy(P.pack_keypoints(k)).pin_memory() for k in wl["kps"]]
+    imgs = [t.to(dev) for t in imgs_h]
+    kps = [t.to(dev) for t in kps_h]
+    desc = [torch.empty((n, 64), dtype=torch.uint8, device=dev) for n in (n0, n1)]
+    matches = torch.empty((n0, 16), dtype=torch.uint8, device=dev)
+    matches_h = torch.empty((n0, 16), dtype=torch.uint8).pin_memory()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    s = int(stream.cuda_stream)
+
+    def step(events=None):
+        if events is not None:
+            events[0].record(stream)
+        for i in range(2):
+            P.latch_extract(ctx.handle, imgs[i], w, h, imgs[i].stride(0), kps[i], kps[i].shape[0], None, desc[i], s)
+            if events is not None:
+                events[1 + i].record(stream)
+        P.hamming_match(ctx.handle, desc[0], n0, desc[1], n1, 2, 0.8, matches, path, s)
+        if events is not None:
+            events[3].record(stream)
+
+    def e2e_step():
+        for i in range(2):
+            imgs[i].copy_(imgs_h[i], non_blocking=True)
+            kps[i].copy_(kps_h[i], non_blocking=True)
+        step()
+        matches_h.copy_(matches, non_blocking=True)
+        stream.synchronize()
+
+    # correctness gate: the timed configuration must equal the oracle on a sample
+    step()
+    torch.cuda.synchronize()
+    ctx.check()
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    clocks.start()
+    launches0 = P.latch_kernel_launches()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps (outside the step's events)
+        step(evs[i])
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    wall1 = time.perf_counter()
+    launches = P.latch_kernel_launches() - launches0
+    clk = clocks.stop()
+
+    ext0 = [e[0].elapsed_time(e[1]) for e in evs]
+    ext1 = [e[1].elapsed_time(e[2]) for e in evs]
+    mat = [e[2].elapsed_time(e[3]) for e in evs]
+    step_ms = [e[0].elapsed_time(e[3]) for e in evs]
+    total_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    n_desc = n0 + n1
+    value = ws * n_desc * args.steps / (total_ms / 1e3)
+
+    # end to end through the C ABI: pinned host inputs -> device -> result back
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = sum(x.numel() for x in imgs_h) + sum(x.numel() for x in kps_h)
+    d2h = matches_h.numel()
+
+    # roofline of the dominant kernel
+    ext_ms = statistics.mean(ext0 + ext1)
+    mat_ms = statistics.mean(mat)
+    from paper_1609_03986_gb300 import roofline
+    rf = roofline.report(ext_ms, mat_ms, n0, n1, args.path, os.path.join(ROOT, "MEASURED_PEAKS.json"))
+
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return 0
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        per_desc, per_query = _oracle_rates(wl, 2000, 400)
+        cpu_s = _cpu_step_seconds(wl, per_desc, per_query)
+        cpu = {"value": n_desc / cpu_s, "unit": "descriptors/s", "cores": 1, "kind": "oracle",
+               "sample": "12,000 descriptors extracted + 400 queries matched against 10,000 train, "
+                         "single-threaded C oracle, scaled to one full step"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "descriptors/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "images": "2 x 1920x1080 u8", "keypoints_per_image": 10000,
+                   "angle_bins": 32, "scales": [1.0, 1.5, 2.25], "match": "10000 x 10000 top-2 ratio 0.8",
+                   "match_path": args.path, "l2": "flushed (256 MB write) between timed steps",
+                   "parallelism": f"{ws} independent replicas"},
+        "extract_desc_per_s": n_desc / (2 * ext_ms / 1e3),
+        "match_gpairs_per_s": n0 * n1 / (mat_ms / 1e3) / 1e9,
+        "kernel_ms": {"extract": ext_ms, "match": mat_ms},
+        "wall_s_timed": wall1 - wall0,
+        "e2e": {"value": ws * n_desc * args.steps / e2e_s, "unit": "descriptors/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "roofline": rf,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    ctx.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_latch(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,184 @@
+/*
+ * latch.h -- C ABI of the GB300 LATCH library: oriented, scaled LATCH binary
+ * descriptors (Parker et al., "CLATCH", arXiv 1609.03986, Sec. 3) and brute-force
+ * Hamming matching with a ratio test (Sec. 4).
+ *
+ * Conventions for every entry point
+ *  - Pointers prefixed d_ are DEVICE pointers owned by the caller; h_ are HOST
+ *    pointers owned by the caller.  The library keeps no caller pointer after a
+ *    call returns (asynchronous work may still read/write them until the stream
+ *    reaches that point).
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL means the legacy default
+ *    stream) and the call returns without waiting for it.  Argument errors are
+ *    detected on the host before anything is enqueued and leave outputs untouched.
+ *  - Errors are returned as latch_status; nothing aborts, traps or exits.
+ *    latch_last_error() gives a one-line description of the last failure on a
+ *    context.  Errors that only the device can see (a keypoint scale index outside
+ *    the scale table) set a device-side flag that latch_check() reports.
+ *  - A context is bound to one device and is not thread-safe: use one context per
+ *    host thread, or serialise calls.  Calls on one context that use its scratch
+ *    memory must be ordered (same stream, or synchronised streams).
+ */
+#ifndef LATCH_H_
+#define LATCH_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LATCH_OK = 0,
+    LATCH_EINVAL = 1,        /* bad argument; nothing was enqueued */
+    LATCH_ENOMEM = 2,        /* device or host allocation failed */
+    LATCH_ECUDA = 3,         /* a CUDA runtime/driver call failed */
+    LATCH_EUNSUPPORTED = 4,  /* device or request not supported by this build */
+    LATCH_EBUSY = 5,         /* queue or slots full (session API) */
+    LATCH_ETIMEOUT = 6,      /* a bounded wait gave up */
+    LATCH_ECANCELLED = 7,    /* request cancelled (session API) */
+    LATCH_EDEVICE = 8        /* a kernel reported bad input (see latch_check) */
+} latch_status;
+
+/* Opaque library context: device, scale table, triplet table, scratch memory. */
+typedef struct latch_context latch_context;
+
+/* cudaStream_t, kept opaque so that this header needs no CUDA header. */
+typedef void *latch_stream_t;
+
+/* 8-bit grey image in DEVICE memory: pixel (x, y) is data[y * pitch + x].
+ * pitch >= width and pitch % 16 == 0 (the tile loads use the tensor-memory
+ * accelerator, whose row strides are multiples of 16 bytes); data 16-byte aligned.
+ * 1 <= width, height <= 32768. */
+typedef struct {
+    const uint8_t *data;
+    int32_t width;
+    int32_t height;
+    int64_t pitch;
+} latch_image;
+
+/* Keypoint p = (x, y, theta) of Sec. 3.2 at integer pixel position, with the
+ * orientation quantised to one of 32 angle bins (theta = 2*pi*angle_bin/32, taken
+ * modulo 32) and a scale given as an index into the context's scale table.
+ * Any x, y is allowed: window samples outside the image read 0.  12 bytes. */
+typedef struct {
+    int32_t x;
+    int32_t y;
+    uint8_t angle_bin;
+    uint8_t scale_idx;
+    uint16_t reserved; /* ignored */
+} latch_keypoint;
+
+/* One LATCH triplet (Sec. 3.1): centres of the anchor patch P_A and the two
+ * companion patches P_1, P_2 in window coordinates (u right, v down, 0..47).
+ * Patches are 7x7, so every coordinate must lie in [3, 44]. */
+typedef struct {
+    uint8_t ax, ay;
+    uint8_t c1x, c1y;
+    uint8_t c2x, c2y;
+} latch_triplet;
+
+/* Result of matching one query (Sec. 4): the nearest train descriptor (idx1,
+ * dist1; ties go to the lowest index), the nearest among the others (idx2,
+ * dist2), and the ratio-test verdict.  idx = -1 and dist = 65535 when absent.
+ * 16 bytes. */
+typedef struct {
+    int32_t idx1;
+    int32_t idx2;
+    uint16_t dist1;
+    uint16_t dist2;
+    uint8_t accepted;
+    uint8_t pad[3];
+} latch_match;
+
+enum {
+    LATCH_DESC_BYTES = 64,  /* 512 bits (Sec. 3.1: 512 triplets; Sec. 3.2: 64-byte vector) */
+    LATCH_TRIPLETS = 512,
+    LATCH_WINDOW = 48,      /* window side in pixels */
+    LATCH_PATCH = 7,        /* patch side in pixels */
+    LATCH_MAX_SCALES = 8,
+    LATCH_ANGLE_BINS = 32
+};
+
+/* Matching paths (both exact). */
+enum {
+    LATCH_PATH_AUTO = 0,    /* chosen per shape */
+    LATCH_PATH_POPC = 1,    /* XOR + population count on the CUDA cores */
+    LATCH_PATH_TENSOR = 2   /* bits expanded to 0/1 8-bit floats, dot products on the tensor cores */
+};
+
+/* Create a context on CUDA device `device` (makes it current on this thread).
+ * Default scale table {1, 1.5, 2.25}; no triplet table until one is given.
+ * Fails with LATCH_EUNSUPPORTED on a device other than compute capability 10.3. */
+latch_status latch_context_create(int device, latch_context **out);
+
+/* Release the context and all device memory it owns.  Waits for its work. */
+latch_status latch_context_destroy(latch_context *ctx);
+
+/* Replace the scale table (Sec. 6 names multi-scale extraction; the scale
+ * multiplies the sample spacing of the 48x48 window).  1 <= n <= 8, each scale in
+ * [0.25, 2.25] (the window then reaches at most 77 pixels from the keypoint).
+ * Rebuilds the sample-offset tables: FP64, no contraction, rounded half away from
+ * zero.  Synchronous. */
+latch_status latch_set_scales(latch_context *ctx, const double *h_scales, int32_t n);
+
+/* Load the 512-triplet table (Sec. 3.1: the triplets are fixed for every
+ * keypoint).  Coordinates are checked to lie in [3, 44].  Synchronous. */
+latch_status latch_set_triplets(latch_context *ctx, const latch_triplet *h_triplets);
+
+/* Pre-size the context's scratch memory so that later calls up to these sizes
+ * allocate nothing (required before capturing calls in a CUDA graph). */
+latch_status latch_reserve(latch_context *ctx, int64_t max_keypoints, int64_t max_query, int64_t max_train);
+
+/*
+ * LATCH descriptors (Sec. 3.1 Eq. 1; Sec. 3.2).  For keypoint k the 48x48 window
+ * is sampled at the keypoint's angle bin and scale (nearest pixel), and bit t of
+ * the 512-bit descriptor is 1 iff ||P_A - P_1||^2_F > ||P_A - P_2||^2_F for the 7x7
+ * patches of triplet t (strict).  Bit t is bit (t % 8) of byte t / 8.
+ *   img        image in device memory (see latch_image)
+ *   d_kps      n keypoints in device memory
+ *   h_triplets 512 triplets in host memory, or NULL to use the context's table;
+ *              a new table is loaded as by latch_set_triplets
+ *   d_out      n * 64 bytes, device memory, 16-byte aligned
+ * n == 0 is a no-op.  A keypoint whose scale_idx is outside the scale table gets
+ * an all-zero descriptor and raises the device flag reported by latch_check.
+ */
+latch_status latch_extract(latch_context *ctx, const latch_image *img, const latch_keypoint *d_kps, int32_t n,
+                           const latch_triplet *h_triplets, uint8_t *d_out, latch_stream_t stream);
+
+/*
+ * Brute-force Hamming matching (Sec. 4): for every query descriptor the nearest
+ * train descriptor and, for k == 2, the nearest among the others, with the ratio
+ * test accepted = (1000 * dist1 < r * dist2), r = round_half_away(1000 * ratio).
+ * For k == 1 a found match is always accepted.
+ *   d_query  nq * 64 bytes, d_train nt * 64 bytes (device, 16-byte aligned)
+ *   k        1 or 2;  ratio in [0, 1]
+ *   d_out    nq latch_match records (device)
+ *   path     LATCH_PATH_AUTO / _POPC / _TENSOR (all give identical results)
+ * nq == 0 is a no-op; nt == 0 gives idx = -1, dist = 65535, accepted = 0.
+ */
+latch_status hamming_match(latch_context *ctx, const uint8_t *d_query, int32_t nq, const uint8_t *d_train,
+                           int32_t nt, int32_t k, float ratio, latch_match *d_out, int32_t path,
+                           latch_stream_t stream);
+
+/* Wait for all work on the context's device, then report (and clear) a
+ * device-side input error (LATCH_EDEVICE) or an asynchronous CUDA error. */
+latch_status latch_check(latch_context *ctx);
+
+/* One-line description of the last error on `ctx` (or of the last failed
+ * latch_context_create when ctx is NULL).  Valid until the next call. */
+const char *latch_last_error(const latch_context *ctx);
+
+/* Number of CUDA kernels the library has launched in this process (all contexts),
+ * for accounting in benchmarks. */
+uint64_t latch_kernel_launches(void);
+
+/* Library version string. */
+const char *latch_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LATCH_H_ */

@@ -1,0 +1,231 @@
+"""GB300-native LATCH descriptors and Hamming matching (CLATCH, arXiv 1609.03986).
+
+Thin ctypes binding over the C ABI declared in ``include/latch.h``.  The functions
+below carry the C names and only marshal arguments; every step of extraction and
+matching runs in the CUDA kernels of ``liblatch.so``.  There is no CPU fallback:
+if the library is missing or fails to load, importing the binding raises.
+
+Pointers are passed as integers (e.g. ``tensor.data_ptr()``) or as objects with a
+``data_ptr()`` method; streams as ``cudaStream_t`` integers
+(``torch.cuda.current_stream().cuda_stream``) or 0 for the legacy default stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblatch.so")
+
+DESC_BYTES = 64
+N_TRIPLETS = 512
+PATH_AUTO, PATH_POPC, PATH_TENSOR = 0, 1, 2
+AVAILABLE_PATHS = (PATH_POPC,)
+STATUS = {0: "LATCH_OK", 1: "LATCH_EINVAL", 2: "LATCH_ENOMEM", 3: "LATCH_ECUDA", 4: "LATCH_EUNSUPPORTED",
+          5: "LATCH_EBUSY", 6: "LATCH_ETIMEOUT", 7: "LATCH_ECANCELLED", 8: "LATCH_EDEVICE"}
+
+# numpy views of the C records
+MATCH_DTYPE = np.dtype([("idx1", "<i4"), ("idx2", "<i4"), ("dist1", "<u2"), ("dist2", "<u2"),
+                        ("accepted", "u1"), ("pad", "u1", (3,))])
+KEYPOINT_DTYPE = np.dtype([("x", "<i4"), ("y", "<i4"), ("angle_bin", "u1"), ("scale_idx", "u1"),
+                           ("reserved", "<u2")])
+assert MATCH_DTYPE.itemsize == 16 and KEYPOINT_DTYPE.itemsize == 12
+
+
+class LatchError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class latch_image(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("pitch", ctypes.c_int64)]
+
+
+_lib = None
+
+# (name, restype, argtypes) of every exported entry point
+_P, _I32, _I64, _F, _D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_double
+EXPORTS = [
+    ("latch_version", ctypes.c_char_p, []),
+    ("latch_last_error", ctypes.c_char_p, [_P]),
+    ("latch_context_create", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_P)]),
+    ("latch_context_destroy", ctypes.c_int, [_P]),
+    ("latch_set_scales", ctypes.c_int, [_P, _P, _I32]),
+    ("latch_set_triplets", ctypes.c_int, [_P, _P]),
+    ("latch_reserve", ctypes.c_int, [_P, _I64, _I64, _I64]),
+    ("latch_extract", ctypes.c_int, [_P, ctypes.POINTER(latch_image), _P, _I32, _P, _P, _P]),
+    ("hamming_match", ctypes.c_int, [_P, _P, _I32, _P, _I32, _I32, _F, _P, _I32, _P]),
+    ("latch_check", ctypes.c_int, [_P]),
+    ("latch_kernel_launches", ctypes.c_uint64, []),
+]
+
+
+def library():
+    """Load ``liblatch.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_1609_03986_gb300.build.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, res, args in EXPORTS:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        return int(x.ctypes.data)
+    raise TypeError(f"cannot take a pointer of {type(x)!r}")
+
+
+def _check(ctx, status: int):
+    if status != 0:
+        msg = library().latch_last_error(ctx)
+        raise LatchError(status, msg.decode() if msg else "")
+
+
+def latch_version() -> str:
+    return library().latch_version().decode()
+
+
+def latch_last_error(ctx) -> str:
+    m = library().latch_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def latch_context_create(device: int = 0):
+    h = ctypes.c_void_p()
+    _check(None, library().latch_context_create(device, ctypes.byref(h)))
+    return h
+
+
+def latch_context_destroy(ctx) -> None:
+    _check(None, library().latch_context_destroy(ctx))
+
+
+def latch_set_scales(ctx, scales) -> None:
+    s = np.ascontiguousarray(scales, dtype=np.float64)
+    _check(ctx, library().latch_set_scales(ctx, s.ctypes.data, s.size))
+
+
+def latch_set_triplets(ctx, triplets) -> None:
+    t = np.ascontiguousarray(triplets, dtype=np.uint8).reshape(-1)
+    if t.size != N_TRIPLETS * 6:
+        raise ValueError("triplet table must hold 512 x 6 bytes")
+    _check(ctx, library().latch_set_triplets(ctx, t.ctypes.data))
+
+
+def latch_reserve(ctx, max_keypoints: int, max_query: int, max_train: int) -> None:
+    _check(ctx, library().latch_reserve(ctx, max_keypoints, max_query, max_train))
+
+
+def latch_extract(ctx, image, width: int, height: int, pitch: int, kps, n: int, triplets, out,
+                  stream: int = 0) -> None:
+    """Descriptors of n keypoints (device pointers image, kps, out; triplets host
+    (512, 6) uint8 or None for the context's table)."""
+    img = latch_image(_ptr(image), width, height, pitch)
+    tp = 0
+    if triplets is not None:
+        t = np.ascontiguousarray(triplets, dtype=np.uint8).reshape(-1)
+        if t.size != N_TRIPLETS * 6:
+            raise ValueError("triplet table must hold 512 x 6 bytes")
+        tp = t.ctypes.data
+    _check(ctx, library().latch_extract(ctx, ctypes.byref(img), _ptr(kps), n, tp, _ptr(out), stream))
+
+
+def hamming_match(ctx, query, nq: int, train, nt: int, k: int, ratio: float, out, path: int = PATH_AUTO,
+                  stream: int = 0) -> None:
+    _check(ctx, library().hamming_match(ctx, _ptr(query), nq, _ptr(train), nt, k, ratio, _ptr(out), path, stream))
+
+
+def latch_check(ctx) -> None:
+    _check(ctx, library().latch_check(ctx))
+
+
+def latch_kernel_launches() -> int:
+    """Number of kernels this library has launched in this process."""
+    return int(library().latch_kernel_launches())
+
+
+def pack_keypoints(kps: np.ndarray) -> np.ndarray:
+    """(n, 4) int (x, y, angle_bin, scale_idx) -> (n, 12) uint8 latch_keypoint records."""
+    kps = np.asarray(kps).reshape(-1, 4)
+    rec = np.zeros(kps.shape[0], dtype=KEYPOINT_DTYPE)
+    rec["x"] = kps[:, 0]
+    rec["y"] = kps[:, 1]
+    rec["angle_bin"] = kps[:, 2]
+    rec["scale_idx"] = kps[:, 3]
+    return rec.view(np.uint8).reshape(-1, 12)
+
+
+def matches_from_bytes(raw: np.ndarray) -> np.ndarray:
+    """(nq, 16) uint8 -> structured array of latch_match records."""
+    return np.ascontiguousarray(raw, dtype=np.uint8).reshape(-1).view(MATCH_DTYPE)
+
+
+class Context:
+    """Convenience owner of a latch_context working on torch CUDA tensors.
+
+    Outputs are allocated with torch; every computation is one C-ABI call."""
+
+    def __init__(self, device: int = 0, scales=(1.0, 1.5, 2.25), triplets=None):
+        self.device = device
+        self.handle = latch_context_create(device)
+        if tuple(scales) != (1.0, 1.5, 2.25):
+            latch_set_scales(self.handle, scales)
+        if triplets is not None:
+            latch_set_triplets(self.handle, triplets)
+
+    def close(self):
+        if self.handle is not None:
+            latch_context_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _stream(stream):
+        if stream is not None:
+            return int(stream)
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+
+    def extract(self, image, width: int, height: int, kps, triplets=None, out=None, stream=None):
+        """image: (H, pitch) uint8 CUDA tensor; kps: (n, 12) uint8 CUDA tensor of
+        packed keypoints.  Returns (n, 64) uint8 CUDA tensor."""
+        import torch
+        n = kps.shape[0]
+        if out is None:
+            out = torch.empty((n, DESC_BYTES), dtype=torch.uint8, device=image.device)
+        latch_extract(self.handle, image, width, height, image.stride(0), kps, n, triplets, out,
+                      self._stream(stream))
+        return out
+
+    def match(self, query, train, k: int = 2, ratio: float = 0.8, path: int = PATH_AUTO, out=None, stream=None):
+        """query (nq, 64), train (nt, 64) uint8 CUDA tensors -> (nq, 16) uint8 tensor of latch_match."""
+        import torch
+        nq, nt = query.shape[0], train.shape[0]
+        if out is None:
+            out = torch.empty((nq, 16), dtype=torch.uint8, device=query.device)
+        hamming_match(self.handle, query, nq, train, nt, k, ratio, out, path, self._stream(stream))
+        return out
+
+    def check(self):
+        latch_check(self.handle)

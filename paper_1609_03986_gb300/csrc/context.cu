@@ -1,0 +1,262 @@
+// Context management and the C-ABI entry points of include/latch.h.
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+namespace latch {
+
+static char g_create_err[256] = "";
+static std::atomic<uint64_t> g_launches{0};
+
+void note_launches(int count) { g_launches.fetch_add(static_cast<uint64_t>(count), std::memory_order_relaxed); }
+
+latch_status fail(latch_context* ctx, latch_status st, const char* fmt, ...) {
+    char* dst = ctx ? ctx->err : g_create_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 256, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+latch_status cuda_check(latch_context* ctx, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return LATCH_OK;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(ctx, LATCH_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    }
+    return fail(ctx, LATCH_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+latch_status scratch_reserve(latch_context* ctx, int slot, size_t bytes, void** out) {
+    Scratch& s = ctx->scratch[slot];
+    if (bytes > s.bytes) {
+        if (s.ptr) {
+            cudaError_t e = cudaFree(s.ptr);
+            s.ptr = nullptr;
+            s.bytes = 0;
+            if (e != cudaSuccess) return cuda_check(ctx, e, "cudaFree(scratch)");
+        }
+        size_t want = bytes + bytes / 4 + 256;  // room to grow a little
+        cudaError_t e = cudaMalloc(&s.ptr, want);
+        if (e != cudaSuccess) {
+            s.ptr = nullptr;
+            return cuda_check(ctx, e, "cudaMalloc(scratch)");
+        }
+        s.bytes = want;
+    }
+    *out = s.ptr;
+    return LATCH_OK;
+}
+
+static latch_status upload_scales(latch_context* ctx, const double* scales, int n) {
+    const size_t bytes = static_cast<size_t>(n) * kBins * kWinPix * 2;
+    int8_t* host = static_cast<int8_t*>(malloc(bytes));
+    if (!host) return fail(ctx, LATCH_ENOMEM, "host allocation of offset tables failed");
+    build_offset_tables(scales, n, host);
+    int8_t* dev = nullptr;
+    cudaError_t e = cudaMalloc(&dev, bytes);
+    if (e != cudaSuccess) {
+        free(host);
+        return cuda_check(ctx, e, "cudaMalloc(offset tables)");
+    }
+    e = cudaMemcpy(dev, host, bytes, cudaMemcpyHostToDevice);
+    free(host);
+    if (e != cudaSuccess) {
+        cudaFree(dev);
+        return cuda_check(ctx, e, "cudaMemcpy(offset tables)");
+    }
+    if (ctx->d_offsets) cudaFree(ctx->d_offsets);
+    ctx->d_offsets = dev;
+    ctx->nscales = n;
+    for (int i = 0; i < n; ++i) ctx->scales[i] = scales[i];
+    ctx->reach = max_reach(scales, n);
+    return LATCH_OK;
+}
+
+static latch_status validate_triplets(latch_context* ctx, const latch_triplet* t) {
+    for (int i = 0; i < kBits; ++i) {
+        const uint8_t* c = &t[i].ax;
+        for (int j = 0; j < 6; ++j)
+            if (c[j] < kPatchR || c[j] > kWin - 1 - kPatchR)
+                return fail(ctx, LATCH_EINVAL, "triplet %d coordinate %d = %d outside [3, 44]", i, j, c[j]);
+    }
+    return LATCH_OK;
+}
+
+static latch_status load_triplets(latch_context* ctx, const latch_triplet* t, cudaStream_t stream, bool sync) {
+    if (ctx->has_trip && memcmp(ctx->h_trip, t, sizeof(ctx->h_trip)) == 0) return LATCH_OK;
+    latch_status st = validate_triplets(ctx, t);
+    if (st != LATCH_OK) return st;
+    memcpy(ctx->h_trip, t, sizeof(ctx->h_trip));
+    // The copy is ordered on `stream` before any kernel that reads the table.
+    cudaError_t e = cudaMemcpyAsync(ctx->d_trip, ctx->h_trip, sizeof(ctx->h_trip), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess && sync) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+        ctx->has_trip = false;
+        return cuda_check(ctx, e, "upload triplets");
+    }
+    ctx->has_trip = true;
+    return LATCH_OK;
+}
+
+}  // namespace latch
+
+using namespace latch;
+
+extern "C" {
+
+uint64_t latch_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+const char* latch_version(void) { return "latch-gb300 0.1 (sm_103a)"; }
+
+const char* latch_last_error(const latch_context* ctx) { return ctx ? ctx->err : g_create_err; }
+
+latch_status latch_context_create(int device, latch_context** out) {
+    if (!out) return fail(nullptr, LATCH_EINVAL, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return fail(nullptr, LATCH_ECUDA, "cudaGetDeviceCount: %s", cudaGetErrorString(e));
+    if (device < 0 || device >= ndev) return fail(nullptr, LATCH_EINVAL, "device %d of %d", device, ndev);
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) return fail(nullptr, LATCH_ECUDA, "cudaGetDeviceProperties: %s", cudaGetErrorString(e));
+    if (!(prop.major == 10 && prop.minor == 3))
+        return fail(nullptr, LATCH_EUNSUPPORTED, "device %d is sm_%d%d; this build targets sm_103a", device,
+                    prop.major, prop.minor);
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) return fail(nullptr, LATCH_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    latch_context* ctx = new (std::nothrow) latch_context();
+    if (!ctx) return fail(nullptr, LATCH_ENOMEM, "host allocation failed");
+    ctx->device = device;
+    ctx->sm_count = prop.multiProcessorCount;
+    const double defaults[3] = {1.0, 1.5, 2.25};
+    latch_status st = upload_scales(ctx, defaults, 3);
+    if (st == LATCH_OK) st = cuda_check(ctx, cudaMalloc(&ctx->d_trip, sizeof(ctx->h_trip)), "cudaMalloc(triplets)");
+    if (st == LATCH_OK) st = cuda_check(ctx, cudaMalloc(&ctx->d_flags, 64), "cudaMalloc(flags)");
+    if (st == LATCH_OK) st = cuda_check(ctx, cudaMemset(ctx->d_flags, 0, 64), "cudaMemset(flags)");
+    if (st != LATCH_OK) {
+        fail(nullptr, st, "%s", ctx->err);
+        latch_context_destroy(ctx);
+        return st;
+    }
+    *out = ctx;
+    return LATCH_OK;
+}
+
+latch_status latch_context_destroy(latch_context* ctx) {
+    if (!ctx) return LATCH_OK;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    if (ctx->d_offsets) cudaFree(ctx->d_offsets);
+    if (ctx->d_trip) cudaFree(ctx->d_trip);
+    if (ctx->d_flags) cudaFree(ctx->d_flags);
+    for (auto& s : ctx->scratch)
+        if (s.ptr) cudaFree(s.ptr);
+    delete ctx;
+    return LATCH_OK;
+}
+
+latch_status latch_set_scales(latch_context* ctx, const double* scales, int32_t n) {
+    if (!ctx || !scales) return fail(ctx, LATCH_EINVAL, "NULL argument");
+    if (n < 1 || n > LATCH_MAX_SCALES) return fail(ctx, LATCH_EINVAL, "number of scales %d not in [1, 8]", n);
+    for (int i = 0; i < n; ++i)
+        if (!(scales[i] >= 0.25 && scales[i] <= kMaxScale))
+            return fail(ctx, LATCH_EINVAL, "scale %d = %g not in [0.25, 2.25]", i, scales[i]);
+    LATCH_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    LATCH_CUDA_TRY(ctx, cudaDeviceSynchronize());
+    return upload_scales(ctx, scales, n);
+}
+
+latch_status latch_set_triplets(latch_context* ctx, const latch_triplet* h_triplets) {
+    if (!ctx || !h_triplets) return fail(ctx, LATCH_EINVAL, "NULL argument");
+    LATCH_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    return load_triplets(ctx, h_triplets, nullptr, true);
+}
+
+latch_status latch_reserve(latch_context* ctx, int64_t max_keypoints, int64_t max_query, int64_t max_train) {
+    if (!ctx) return fail(ctx, LATCH_EINVAL, "NULL context");
+    if (max_keypoints < 0 || max_query < 0 || max_train < 0) return fail(ctx, LATCH_EINVAL, "negative size");
+    LATCH_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    void* p = nullptr;
+    latch_image big{nullptr, 32768, 32768, 32768};
+    latch_status st = scratch_reserve(ctx, 0, extract_scratch_bytes(&big, max_keypoints), &p);
+    if (st != LATCH_OK) return st;
+    return scratch_reserve(ctx, 1, match_popc_scratch_bytes(ctx, max_query, max_train), &p);
+}
+
+latch_status latch_check(latch_context* ctx) {
+    if (!ctx) return fail(ctx, LATCH_EINVAL, "NULL context");
+    LATCH_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    LATCH_CUDA_TRY(ctx, cudaDeviceSynchronize());
+    uint32_t flags = 0;
+    LATCH_CUDA_TRY(ctx, cudaMemcpy(&flags, ctx->d_flags, sizeof(flags), cudaMemcpyDeviceToHost));
+    if (flags) {
+        LATCH_CUDA_TRY(ctx, cudaMemset(ctx->d_flags, 0, sizeof(flags)));
+        if (flags & kFlagTimeout) return fail(ctx, LATCH_ETIMEOUT, "a device-side wait timed out (flags 0x%x)", flags);
+        return fail(ctx, LATCH_EDEVICE, "a keypoint had a scale index outside the scale table (flags 0x%x)", flags);
+    }
+    return LATCH_OK;
+}
+
+latch_status latch_extract(latch_context* ctx, const latch_image* img, const latch_keypoint* d_kps, int32_t n,
+                           const latch_triplet* h_triplets, uint8_t* d_out, latch_stream_t stream) {
+    if (!ctx) return fail(ctx, LATCH_EINVAL, "NULL context");
+    if (n < 0) return fail(ctx, LATCH_EINVAL, "n = %d < 0", n);
+    if (!img) return fail(ctx, LATCH_EINVAL, "NULL image");
+    if (img->width < 1 || img->height < 1 || img->width > 32768 || img->height > 32768)
+        return fail(ctx, LATCH_EINVAL, "image size %dx%d outside [1, 32768]", img->width, img->height);
+    if (img->pitch < img->width || img->pitch % 16 != 0)
+        return fail(ctx, LATCH_EINVAL, "pitch %lld must be >= width and a multiple of 16", (long long)img->pitch);
+    if (!img->data || (reinterpret_cast<uintptr_t>(img->data) & 15))
+        return fail(ctx, LATCH_EINVAL, "image data must be non-NULL and 16-byte aligned");
+    if (n > 0 && (!d_kps || !d_out)) return fail(ctx, LATCH_EINVAL, "NULL keypoints or output");
+    if (d_out && (reinterpret_cast<uintptr_t>(d_out) & 15)) return fail(ctx, LATCH_EINVAL, "d_out not 16-byte aligned");
+    if (d_kps && (reinterpret_cast<uintptr_t>(d_kps) & 3)) return fail(ctx, LATCH_EINVAL, "d_kps not 4-byte aligned");
+    LATCH_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (h_triplets) {
+        latch_status st = load_triplets(ctx, h_triplets, s, false);
+        if (st != LATCH_OK) return st;
+    }
+    if (!ctx->has_trip) return fail(ctx, LATCH_EINVAL, "no triplet table: pass one or call latch_set_triplets");
+    if (n == 0) return LATCH_OK;
+    void* scratch = nullptr;
+    latch_status st = scratch_reserve(ctx, 0, extract_scratch_bytes(img, n), &scratch);
+    if (st != LATCH_OK) return st;
+    return cuda_check(ctx, launch_extract(ctx, img, d_kps, n, d_out, scratch, s), "extract kernel launch");
+}
+
+latch_status hamming_match(latch_context* ctx, const uint8_t* d_query, int32_t nq, const uint8_t* d_train,
+                           int32_t nt, int32_t k, float ratio, latch_match* d_out, int32_t path,
+                           latch_stream_t stream) {
+    if (!ctx) return fail(ctx, LATCH_EINVAL, "NULL context");
+    if (nq < 0 || nt < 0) return fail(ctx, LATCH_EINVAL, "negative size");
+    if (k != 1 && k != 2) return fail(ctx, LATCH_EINVAL, "k = %d must be 1 or 2", k);
+    if (!(ratio >= 0.0f && ratio <= 1.0f)) return fail(ctx, LATCH_EINVAL, "ratio %g not in [0, 1]", ratio);
+    if (path != LATCH_PATH_AUTO && path != LATCH_PATH_POPC && path != LATCH_PATH_TENSOR)
+        return fail(ctx, LATCH_EINVAL, "unknown path %d", path);
+    if (nq > 0 && (!d_query || !d_out)) return fail(ctx, LATCH_EINVAL, "NULL query or output");
+    if (nq > 0 && nt > 0 && !d_train) return fail(ctx, LATCH_EINVAL, "NULL train");
+    if ((reinterpret_cast<uintptr_t>(d_query) | reinterpret_cast<uintptr_t>(d_train) |
+         reinterpret_cast<uintptr_t>(d_out)) & 15)
+        return fail(ctx, LATCH_EINVAL, "descriptor and output pointers must be 16-byte aligned");
+    if (path == LATCH_PATH_TENSOR) return fail(ctx, LATCH_EUNSUPPORTED, "tensor-core path not built yet");
+    if (nq == 0) return LATCH_OK;
+    LATCH_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    const int32_t r_milli = static_cast<int32_t>(std::round(static_cast<double>(ratio) * 1000.0));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void* scratch = nullptr;
+    latch_status st = scratch_reserve(ctx, 1, match_popc_scratch_bytes(ctx, nq, nt), &scratch);
+    if (st != LATCH_OK) return st;
+    return cuda_check(ctx, launch_match_popc(ctx, d_query, nq, d_train, nt, k, r_milli, d_out, scratch, s),
+                      "match kernel launch");
+}
+
+}  // extern "C"

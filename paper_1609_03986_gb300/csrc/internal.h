@@ -1,0 +1,82 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+
+#include "latch.h"
+
+namespace latch {
+
+constexpr int kWin = LATCH_WINDOW;          // 48
+constexpr int kWinPix = kWin * kWin;        // 2304
+constexpr int kHalf = kWin / 2;             // 24
+constexpr int kPatchR = LATCH_PATCH / 2;    // 3
+constexpr int kBits = LATCH_TRIPLETS;       // 512
+constexpr int kDescBytes = LATCH_DESC_BYTES;
+constexpr int kDescWords = kDescBytes / 4;  // 16
+constexpr int kBins = LATCH_ANGLE_BINS;
+constexpr double kMaxScale = 2.25;
+constexpr int kMaxReach = 77;               // max |offset| at scale 2.25 (24*sqrt(2)*2.25 = 76.4)
+
+// Device-side error flags (OR-ed into ctx->d_flags).
+enum : uint32_t { kFlagBadScale = 1u, kFlagTimeout = 2u };
+
+// Host-built sample-offset tables (tables.cpp).  For each scale s and angle bin b,
+// kWinPix entries of (dx, dy) as int8 pairs, entry index v * 48 + u.
+void build_offset_tables(const double* scales, int nscales, int8_t* out /* nscales*32*2304*2 */);
+int max_reach(const double* scales, int nscales);
+
+struct Scratch {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace latch
+
+struct latch_context {
+    int device = 0;
+    int sm_count = 0;
+    int nscales = 0;
+    double scales[LATCH_MAX_SCALES] = {};
+    int reach = 0;                       // max |offset| over the scale table
+    int8_t* d_offsets = nullptr;         // nscales * 32 * 2304 * 2 bytes
+    latch_triplet h_trip[LATCH_TRIPLETS] = {};
+    bool has_trip = false;
+    uint8_t* d_trip = nullptr;           // 512 * 6 bytes
+    uint32_t* d_flags = nullptr;         // device error word
+    latch::Scratch scratch[4];           // grow-only scratch regions
+    char err[256] = {};
+};
+
+namespace latch {
+
+// Records an error message on the context and returns `st`.
+latch_status fail(latch_context* ctx, latch_status st, const char* fmt, ...);
+// Maps a CUDA error to LATCH_ECUDA (recorded on ctx) or LATCH_OK.
+latch_status cuda_check(latch_context* ctx, cudaError_t e, const char* what);
+// Ensures scratch region `slot` holds at least `bytes` (cudaMalloc, grow-only).
+latch_status scratch_reserve(latch_context* ctx, int slot, size_t bytes, void** out);
+
+// Counts kernel launches made by the library (latch_kernel_launches()).
+void note_launches(int count);
+
+// Kernel launchers (one per .cu file); return cudaGetLastError() of the launch.
+cudaError_t launch_extract(const latch_context* ctx, const latch_image* img, const latch_keypoint* d_kps, int32_t n,
+                           uint8_t* d_out, void* scratch, cudaStream_t stream);
+size_t extract_scratch_bytes(const latch_image* img, int64_t n);
+
+cudaError_t launch_match_popc(const latch_context* ctx, const uint8_t* q, int32_t nq, const uint8_t* t, int32_t nt,
+                              int32_t k, int32_t r_milli, latch_match* out, void* scratch, cudaStream_t stream);
+size_t match_popc_scratch_bytes(const latch_context* ctx, int64_t nq, int64_t nt);
+
+}  // namespace latch
+
+#define LATCH_CUDA_TRY(ctx, expr)                                         \
+    do {                                                                  \
+        cudaError_t e_ = (expr);                                          \
+        if (e_ != cudaSuccess) return latch::cuda_check((ctx), e_, #expr); \
+    } while (0)

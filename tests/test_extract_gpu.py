@@ -1,0 +1,117 @@
+"""Parity of the CUDA extraction path with the CPU oracle, bit for bit, through the
+C ABI.  Sizes span many thread blocks with ragged tails; edge cases cover empty
+input, keypoints at and beyond the border, every angle bin and scale, and a bad
+scale index."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1609_03986_gb300 as P
+from paper_1609_03986_gb300 import synth
+from conftest import to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _extract(ctx, img, w, h, kps, triplets=None):
+    out = ctx.extract(to_dev(img), w, h, to_dev(P.pack_keypoints(kps)), triplets)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("name", ["plain_640x480_2k", "oriented_scaled_1920x1080_10k"])
+def test_pair_workload_parity(gpu_ctx, triplets, name):
+    """Both images of the one-pair workloads, every keypoint (2 x 2,000 upright;
+    a 3,001-keypoint ragged prefix of the 10,000 oriented and scaled ones)."""
+    wl = synth.pair(name)
+    for img, kps in zip(wl["images"], wl["kps"]):
+        if len(kps) > 4000:
+            kps = kps[:3001]
+        got = _extract(gpu_ctx, img, wl["width"], wl["height"], kps)
+        want = oracle.extract(img, wl["width"], wl["height"], kps, triplets, synth.SCALES)
+        assert np.array_equal(got, want)
+    gpu_ctx.check()
+
+
+def test_every_bin_and_scale_near_borders(gpu_ctx, triplets):
+    """All 32 bins x 3 scales, keypoints within 5 px of the border and outside the
+    image (windows partly or wholly outside read zeros)."""
+    w, h = 333, 250
+    img = synth.image(synth.seed(11, 0, synth.KIND_IMAGE), w, h, n_ellipses=30)
+    rng = np.random.default_rng(3)
+    pts = []
+    for b in range(32):
+        for s in range(3):
+            for x, y in ((0, 0), (w - 1, h - 1), (2, h // 2), (w // 2, 4), (w - 3, 7)):
+                pts.append((x, y, b, s))
+    pts += [(-10, 40, 3, 1), (w + 5, h + 90, 9, 2), (-200, -200, 0, 0), (w // 2, h // 2, 31, 2)]
+    xs = rng.integers(-40, w + 40, 300)
+    ys = rng.integers(-40, h + 40, 300)
+    pts += [(int(x), int(y), int(rng.integers(0, 32)), int(rng.integers(0, 3))) for x, y in zip(xs, ys)]
+    kps = np.array(pts, dtype=np.int32)
+    got = _extract(gpu_ctx, img, w, h, kps)
+    want = oracle.extract(img, w, h, kps, triplets, synth.SCALES)
+    assert np.array_equal(got, want)
+    gpu_ctx.check()
+
+
+def test_bin_wraps_modulo_32(gpu_ctx, triplets):
+    w, h = 200, 200
+    img = synth.image(synth.seed(11, 1, synth.KIND_IMAGE), w, h, n_ellipses=10)
+    kps = np.array([[100, 100, b, 1] for b in range(32)], np.int32)
+    a = _extract(gpu_ctx, img, w, h, kps)
+    kps2 = kps.copy()
+    kps2[:, 2] += 32
+    assert np.array_equal(a, _extract(gpu_ctx, img, w, h, kps2))
+
+
+def test_tiny_and_odd_images(gpu_ctx, triplets):
+    for w, h in ((1, 1), (7, 3), (17, 64), (48, 48)):
+        pitch = (w + 15) // 16 * 16
+        img = synth.image(synth.seed(11, w, synth.KIND_IMAGE), w, h, pitch, n_ellipses=2)
+        kps = np.array([[0, 0, 0, 0], [w // 2, h // 2, 5, 2], [w - 1, h - 1, 20, 1]], np.int32)
+        got = _extract(gpu_ctx, img, w, h, kps)
+        assert np.array_equal(got, oracle.extract(img, w, h, kps, triplets, synth.SCALES))
+
+
+def test_empty_and_invalid_arguments(gpu_ctx, triplets):
+    img = torch.zeros((64, 64), dtype=torch.uint8, device="cuda")
+    kps = torch.zeros((0, 12), dtype=torch.uint8, device="cuda")
+    out = gpu_ctx.extract(img, 64, 64, kps)
+    assert out.shape == (0, 64)
+    bad = triplets.copy()
+    bad[7, 3] = 2
+    with pytest.raises(P.LatchError) as e:
+        gpu_ctx.extract(img, 64, 64, to_dev(P.pack_keypoints([[5, 5, 0, 0]])), bad)
+    assert e.value.status == 1
+    with pytest.raises(P.LatchError):  # pitch not a multiple of 16
+        P.latch_extract(gpu_ctx.handle, img, 60, 64, 60, 0, 0, None, 0, 0)
+    with pytest.raises(P.LatchError):
+        P.latch_extract(gpu_ctx.handle, img, 64, 64, 64, 0, -1, None, 0, 0)
+
+
+def test_bad_scale_index_flags_device_error(gpu_ctx, triplets):
+    w, h = 100, 100
+    img = synth.image(synth.seed(11, 2, synth.KIND_IMAGE), w, h, n_ellipses=5)
+    kps = np.array([[50, 50, 0, 0], [50, 50, 0, 7], [40, 40, 3, 2]], np.int32)
+    got = _extract(gpu_ctx, img, w, h, kps)
+    with pytest.raises(P.LatchError) as e:
+        gpu_ctx.check()
+    assert e.value.status == 8
+    assert not got[1].any()
+    good = kps[[0, 2]]
+    assert np.array_equal(got[[0, 2]], oracle.extract(img, w, h, good, triplets, synth.SCALES))
+    gpu_ctx.check()  # the flag was cleared
+
+
+def test_triplet_table_switch(gpu_ctx, triplets):
+    """Passing a different table per call is honoured and restored."""
+    w, h = 160, 120
+    img = synth.image(synth.seed(11, 3, synth.KIND_IMAGE), w, h, n_ellipses=8)
+    kps = synth.keypoints(synth.seed(11, 3, synth.KIND_KEYPOINTS), w, h, 50, 10, True, 3)
+    other = synth.triplets(12345)
+    got = _extract(gpu_ctx, img, w, h, kps, other)
+    assert np.array_equal(got, oracle.extract(img, w, h, kps, other, synth.SCALES))
+    got = _extract(gpu_ctx, img, w, h, kps, triplets)
+    assert np.array_equal(got, oracle.extract(img, w, h, kps, triplets, synth.SCALES))

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "liblatch.so")
 DESC_BYTES = 64
 N_TRIPLETS = 512
 PATH_AUTO, PATH_POPC, PATH_TENSOR = 0, 1, 2
-AVAILABLE_PATHS = (PATH_POPC,)
+AVAILABLE_PATHS = (PATH_POPC, PATH_TENSOR)
 STATUS = {0: "LATCH_OK", 1: "LATCH_EINVAL", 2: "LATCH_ENOMEM", 3: "LATCH_ECUDA", 4: "LATCH_EUNSUPPORTED",
           5: "LATCH_EBUSY", 6: "LATCH_ETIMEOUT", 7: "LATCH_ECANCELLED", 8: "LATCH_EDEVICE"}
 

@@ -79,6 +79,12 @@ static latch_status upload_scales(latch_context* ctx, const double* scales, int 
     return LATCH_OK;
 }
 
+// Matching path for AUTO: the tensor-core path once the pair count amortises its
+// operand expansion and merge launches.
+static int choose_match_path(const latch_context*, int64_t nq, int64_t nt) {
+    return nq * nt >= (int64_t(1) << 22) ? LATCH_PATH_TENSOR : LATCH_PATH_POPC;
+}
+
 static latch_status validate_triplets(latch_context* ctx, const latch_triplet* t) {
     for (int i = 0; i < kBits; ++i) {
         const uint8_t* c = &t[i].ax;
@@ -187,8 +193,9 @@ latch_status latch_reserve(latch_context* ctx, int64_t max_keypoints, int64_t ma
     void* p = nullptr;
     latch_image big{nullptr, 32768, 32768, 32768};
     latch_status st = scratch_reserve(ctx, 0, extract_scratch_bytes(&big, max_keypoints), &p);
-    if (st != LATCH_OK) return st;
-    return scratch_reserve(ctx, 1, match_popc_scratch_bytes(ctx, max_query, max_train), &p);
+    if (st == LATCH_OK) st = scratch_reserve(ctx, 1, match_popc_scratch_bytes(ctx, max_query, max_train), &p);
+    if (st == LATCH_OK) st = scratch_reserve(ctx, 2, match_tc_scratch_bytes(ctx, max_query, max_train), &p);
+    return st;
 }
 
 latch_status latch_check(latch_context* ctx) {
@@ -247,16 +254,22 @@ latch_status hamming_match(latch_context* ctx, const uint8_t* d_query, int32_t n
     if ((reinterpret_cast<uintptr_t>(d_query) | reinterpret_cast<uintptr_t>(d_train) |
          reinterpret_cast<uintptr_t>(d_out)) & 15)
         return fail(ctx, LATCH_EINVAL, "descriptor and output pointers must be 16-byte aligned");
-    if (path == LATCH_PATH_TENSOR) return fail(ctx, LATCH_EUNSUPPORTED, "tensor-core path not built yet");
     if (nq == 0) return LATCH_OK;
     LATCH_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     const int32_t r_milli = static_cast<int32_t>(std::round(static_cast<double>(ratio) * 1000.0));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (path == LATCH_PATH_AUTO) path = choose_match_path(ctx, nq, nt);
     void* scratch = nullptr;
+    if (path == LATCH_PATH_TENSOR) {
+        latch_status st = scratch_reserve(ctx, 2, match_tc_scratch_bytes(ctx, nq, nt), &scratch);
+        if (st != LATCH_OK) return st;
+        return cuda_check(ctx, launch_match_tc(ctx, d_query, nq, d_train, nt, k, r_milli, d_out, scratch, s),
+                          "tensor match launch");
+    }
     latch_status st = scratch_reserve(ctx, 1, match_popc_scratch_bytes(ctx, nq, nt), &scratch);
     if (st != LATCH_OK) return st;
     return cuda_check(ctx, launch_match_popc(ctx, d_query, nq, d_train, nt, k, r_milli, d_out, scratch, s),
-                      "match kernel launch");
+                      "popc match launch");
 }
 
 }  // extern "C"

@@ -73,6 +73,10 @@ cudaError_t launch_match_popc(const latch_context* ctx, const uint8_t* q, int32_
                               int32_t k, int32_t r_milli, latch_match* out, void* scratch, cudaStream_t stream);
 size_t match_popc_scratch_bytes(const latch_context* ctx, int64_t nq, int64_t nt);
 
+cudaError_t launch_match_tc(const latch_context* ctx, const uint8_t* q, int32_t nq, const uint8_t* t, int32_t nt,
+                            int32_t k, int32_t r_milli, latch_match* out, void* scratch, cudaStream_t stream);
+size_t match_tc_scratch_bytes(const latch_context* ctx, int64_t nq, int64_t nt);
+
 }  // namespace latch
 
 #define LATCH_CUDA_TRY(ctx, expr)                                         \

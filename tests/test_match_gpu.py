@@ -11,7 +11,7 @@ from paper_1609_03986_gb300 import synth
 from conftest import match_records, to_dev
 
 pytestmark = pytest.mark.gpu
-PATHS = [P.PATH_POPC, P.PATH_AUTO]
+PATHS = [P.PATH_POPC, P.PATH_TENSOR, P.PATH_AUTO]
 
 
 def _match(ctx, q, t, k=2, ratio=0.8, path=P.PATH_AUTO):
@@ -82,8 +82,9 @@ def test_pair_workload_parity(gpu_ctx, triplets):
     torch.cuda.synchronize()
     q, t = (d.cpu().numpy() for d in descs)
     assert np.array_equal(q, oracle.extract(wl["images"][0], wl["width"], wl["height"], wl["kps"][0], triplets))
-    got = match_records(gpu_ctx.match(descs[0], descs[1], 2, 0.8))
-    _same(got, oracle.match(q, t))
+    want = oracle.match(q, t)
+    for path in PATHS:
+        _same(match_records(gpu_ctx.match(descs[0], descs[1], 2, 0.8, path)), want)
 
 
 @pytest.mark.parametrize("path", PATHS)

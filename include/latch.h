@@ -162,6 +162,25 @@ latch_status hamming_match(latch_context *ctx, const uint8_t *d_query, int32_t n
                            int32_t nt, int32_t k, float ratio, latch_match *d_out, int32_t path,
                            latch_stream_t stream);
 
+/*
+ * hamming_match without any device allocation: same results as hamming_match on
+ * the tensor-core path, for callers that must not allocate device memory (for
+ * example a host application that owns all HBM through its own pool, or a
+ * latency-bound pipeline in which a cudaMalloc would synchronise the device).  The
+ * paper has no counterpart; this is an interface convenience.
+ *   Uses the current device and no context.  Scratch lives in one 16 MiB array
+ *   that the library's CUDA module reserves on every device it is loaded on until
+ *   the process exits; a request whose scratch would not fit (roughly nq + nt above
+ *   30,000 descriptors) returns LATCH_EINVAL and enqueues nothing.
+ *   The first call on a device looks up the array's device address (once per
+ *   device); make that first call before any stream capture.
+ *   All calls share the one array: calls whose work overlaps on the GPU (different
+ *   streams, or several host threads) race and must be serialised by the caller.
+ *   Errors are described by latch_last_error(NULL).
+ */
+latch_status hamming_match_noalloc(const uint8_t *d_query, int32_t nq, const uint8_t *d_train, int32_t nt, int32_t k,
+                                   float ratio, latch_match *d_out, latch_stream_t stream);
+
 /* Wait for all work on the context's device, then report (and clear) a
  * device-side input error (LATCH_EDEVICE) or an asynchronous CUDA error. */
 latch_status latch_check(latch_context *ctx);

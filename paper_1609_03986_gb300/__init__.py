@@ -61,6 +61,7 @@ EXPORTS = [
     ("hamming_match", ctypes.c_int, [_P, _P, _I32, _P, _I32, _I32, _F, _P, _I32, _P]),
     ("latch_check", ctypes.c_int, [_P]),
     ("latch_kernel_launches", ctypes.c_uint64, []),
+    ("hamming_match_noalloc", ctypes.c_int, [_P, _I32, _P, _I32, _I32, _F, _P, _P]),
 ]
 
 
@@ -149,6 +150,13 @@ def latch_extract(ctx, image, width: int, height: int, pitch: int, kps, n: int, 
 def hamming_match(ctx, query, nq: int, train, nt: int, k: int, ratio: float, out, path: int = PATH_AUTO,
                   stream: int = 0) -> None:
     _check(ctx, library().hamming_match(ctx, _ptr(query), nq, _ptr(train), nt, k, ratio, _ptr(out), path, stream))
+
+
+def hamming_match_noalloc(query, nq: int, train, nt: int, k: int, ratio: float, out, stream: int = 0) -> None:
+    """hamming_match on the current device without allocating device memory (for
+    callers that may not call cudaMalloc); scratch is the library's fixed 16 MiB
+    array, so nq + nt is limited to roughly 30,000 descriptors."""
+    _check(None, library().hamming_match_noalloc(_ptr(query), nq, _ptr(train), nt, k, ratio, _ptr(out), stream))
 
 
 def latch_check(ctx) -> None:

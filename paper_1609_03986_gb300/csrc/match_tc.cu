@@ -440,3 +440,97 @@ cudaError_t launch_match_tc(const latch_context* ctx, const uint8_t* q, int32_t 
 }
 
 }  // namespace latch
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the tensor-core matcher.
+//
+// Some callers may not allocate device memory at all: a library embedded in a host
+// application that owns every byte of HBM through its own pool (so a cudaMalloc
+// from us could fail, or steal memory the application has budgeted), or a
+// latency-bound pipeline where cudaMalloc/cudaFree would synchronise the device and
+// stall the application's other streams.  hamming_match_noalloc serves them: its
+// scratch (expanded operands, popcounts, per-block partial results, status word)
+// lives in the fixed array below, which the CUDA module reserves on every device
+// that loads this library for as long as the process lives.
+// ---------------------------------------------------------------------------
+
+namespace latch {
+
+constexpr size_t kStaticScratchBytes = size_t(16) << 20;  // 16 MiB
+constexpr size_t kStaticFlagBytes = 256;                  // status word, cleared every call
+
+}  // namespace latch
+
+static __device__ __align__(256) uint8_t g_match_static_scratch[latch::kStaticScratchBytes];
+
+#include <mutex>
+
+namespace latch {
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_ptr[kMaxDevices] = {};
+
+// Device address of g_match_static_scratch on `dev` (which must be current).  The
+// symbol's host-side name is only a stand-in, so its address is looked up once per
+// device and cached.
+latch_status static_scratch(int dev, void** out) {
+    if (dev < 0 || dev >= kMaxDevices) return fail(nullptr, LATCH_EUNSUPPORTED, "device index %d too large", dev);
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_match_static_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(nullptr, LATCH_ECUDA, "cudaGetSymbolAddress(static scratch): %s", cudaGetErrorString(e));
+        g_static_ptr[dev] = p;
+    }
+    *out = g_static_ptr[dev];
+    return LATCH_OK;
+}
+
+}  // namespace
+}  // namespace latch
+
+extern "C" latch_status hamming_match_noalloc(const uint8_t* d_query, int32_t nq, const uint8_t* d_train,
+                                              int32_t nt, int32_t k, float ratio, latch_match* d_out,
+                                              latch_stream_t stream) {
+    using namespace latch;
+    if (nq < 0 || nt < 0) return fail(nullptr, LATCH_EINVAL, "negative size");
+    if (k != 1 && k != 2) return fail(nullptr, LATCH_EINVAL, "k = %d must be 1 or 2", k);
+    if (!(ratio >= 0.0f && ratio <= 1.0f)) return fail(nullptr, LATCH_EINVAL, "ratio %g not in [0, 1]", ratio);
+    if (nq > 0 && (!d_query || !d_out)) return fail(nullptr, LATCH_EINVAL, "NULL query or output");
+    if (nq > 0 && nt > 0 && !d_train) return fail(nullptr, LATCH_EINVAL, "NULL train");
+    if ((reinterpret_cast<uintptr_t>(d_query) | reinterpret_cast<uintptr_t>(d_train) |
+         reinterpret_cast<uintptr_t>(d_out)) & 15)
+        return fail(nullptr, LATCH_EINVAL, "descriptor and output pointers must be 16-byte aligned");
+    if (nq == 0) return LATCH_OK;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return fail(nullptr, LATCH_ECUDA, "device query: %s", cudaGetErrorString(e));
+    const WorkSplit s = make_split(nq, nt, kRowsQ, kColsB, sms);
+    const size_t need = tc_layout(s, nq, nt).total + kStaticFlagBytes;
+    if (need > kStaticScratchBytes)
+        return fail(nullptr, LATCH_EINVAL,
+                    "nq = %d, nt = %d needs %zu bytes of scratch; the static scratch holds %zu (about 30,000 "
+                    "descriptors in total)",
+                    nq, nt, need, kStaticScratchBytes);
+    void* base = nullptr;
+    latch_status st = static_scratch(dev, &base);
+    if (st != LATCH_OK) return st;
+    uint8_t* bytes = static_cast<uint8_t*>(base);
+    uint32_t* flags = reinterpret_cast<uint32_t*>(bytes);
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    e = cudaMemsetAsync(flags, 0, sizeof(uint32_t), cs);
+    if (e != cudaSuccess) return fail(nullptr, LATCH_ECUDA, "clear status word: %s", cudaGetErrorString(e));
+    // launch_match_tc reads only the SM count and the status-word pointer of its context
+    latch_context shim;
+    shim.device = dev;
+    shim.sm_count = sms;
+    shim.d_flags = flags;
+    const int32_t r_milli = static_cast<int32_t>(std::round(static_cast<double>(ratio) * 1000.0));
+    e = launch_match_tc(&shim, d_query, nq, d_train, nt, k, r_milli, d_out, bytes + kStaticFlagBytes, cs);
+    if (e != cudaSuccess) return fail(nullptr, LATCH_ECUDA, "tensor match launch: %s", cudaGetErrorString(e));
+    return LATCH_OK;
+}

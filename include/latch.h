@@ -162,6 +162,10 @@ latch_status hamming_match(latch_context *ctx, const uint8_t *d_query, int32_t n
                            int32_t nt, int32_t k, float ratio, latch_match *d_out, int32_t path,
                            latch_stream_t stream);
 
+/* The path LATCH_PATH_AUTO takes for nq x nt on this context (LATCH_PATH_POPC or
+ * LATCH_PATH_TENSOR); -1 on a NULL context. */
+int32_t hamming_match_path(const latch_context *ctx, int64_t nq, int64_t nt);
+
 /*
  * hamming_match without any device allocation: same results as hamming_match on
  * the tensor-core path, for callers that must not allocate device memory (for

@@ -61,6 +61,7 @@ EXPORTS = [
     ("hamming_match", ctypes.c_int, [_P, _P, _I32, _P, _I32, _I32, _F, _P, _I32, _P]),
     ("latch_check", ctypes.c_int, [_P]),
     ("latch_kernel_launches", ctypes.c_uint64, []),
+    ("hamming_match_path", ctypes.c_int32, [_P, _I64, _I64]),
     ("hamming_match_noalloc", ctypes.c_int, [_P, _I32, _P, _I32, _I32, _F, _P, _P]),
 ]
 
@@ -161,6 +162,11 @@ def hamming_match_noalloc(query, nq: int, train, nt: int, k: int, ratio: float, 
 
 def latch_check(ctx) -> None:
     _check(ctx, library().latch_check(ctx))
+
+
+def hamming_match_path(ctx, nq: int, nt: int) -> int:
+    """The path LATCH_PATH_AUTO takes for nq x nt on this context."""
+    return int(library().hamming_match_path(ctx, nq, nt))
 
 
 def latch_kernel_launches() -> int:

@@ -55,27 +55,33 @@ latch_status scratch_reserve(latch_context* ctx, int slot, size_t bytes, void** 
 }
 
 static latch_status upload_scales(latch_context* ctx, const double* scales, int n) {
-    const size_t bytes = static_cast<size_t>(n) * kBins * kWinPix * 2;
-    int8_t* host = static_cast<int8_t*>(malloc(bytes));
-    if (!host) return fail(ctx, LATCH_ENOMEM, "host allocation of offset tables failed");
-    build_offset_tables(scales, n, host);
-    int8_t* dev = nullptr;
-    cudaError_t e = cudaMalloc(&dev, bytes);
-    if (e != cudaSuccess) {
+    const size_t entries = static_cast<size_t>(n) * kBins * kWinPix;
+    int8_t* host = static_cast<int8_t*>(malloc(entries * 2));
+    int16_t* toff = static_cast<int16_t*>(malloc((entries + 16) * sizeof(int16_t)));
+    if (!host || !toff) {
         free(host);
-        return cuda_check(ctx, e, "cudaMalloc(offset tables)");
+        free(toff);
+        return fail(ctx, LATCH_ENOMEM, "host allocation of offset tables failed");
     }
-    e = cudaMemcpy(dev, host, bytes, cudaMemcpyHostToDevice);
+    build_offset_tables(scales, n, host);
+    const int reach = max_reach(scales, n);
+    const int pitch = extract_tile_pitch(reach);
+    for (size_t i = 0; i < entries; ++i) toff[i] = static_cast<int16_t>(host[2 * i + 1] * pitch + host[2 * i]);
+    for (size_t i = entries; i < entries + 16; ++i) toff[i] = 0;
     free(host);
+    int16_t* dev = nullptr;
+    cudaError_t e = cudaMalloc(&dev, (entries + 16) * sizeof(int16_t));
+    if (e == cudaSuccess) e = cudaMemcpy(dev, toff, (entries + 16) * sizeof(int16_t), cudaMemcpyHostToDevice);
+    free(toff);
     if (e != cudaSuccess) {
-        cudaFree(dev);
-        return cuda_check(ctx, e, "cudaMemcpy(offset tables)");
+        if (dev) cudaFree(dev);
+        return cuda_check(ctx, e, "upload offset tables");
     }
-    if (ctx->d_offsets) cudaFree(ctx->d_offsets);
-    ctx->d_offsets = dev;
+    if (ctx->d_tile_offsets) cudaFree(ctx->d_tile_offsets);
+    ctx->d_tile_offsets = dev;
     ctx->nscales = n;
     for (int i = 0; i < n; ++i) ctx->scales[i] = scales[i];
-    ctx->reach = max_reach(scales, n);
+    ctx->reach = reach;
     return LATCH_OK;
 }
 
@@ -100,8 +106,12 @@ static latch_status load_triplets(latch_context* ctx, const latch_triplet* t, cu
     latch_status st = validate_triplets(ctx, t);
     if (st != LATCH_OK) return st;
     memcpy(ctx->h_trip, t, sizeof(ctx->h_trip));
-    // The copy is ordered on `stream` before any kernel that reads the table.
+    build_triplet_offsets(ctx->h_trip, ctx->h_trip_offsets);
+    // The copies are ordered on `stream` before any kernel that reads the tables.
     cudaError_t e = cudaMemcpyAsync(ctx->d_trip, ctx->h_trip, sizeof(ctx->h_trip), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->d_trip_offsets, ctx->h_trip_offsets, sizeof(ctx->h_trip_offsets),
+                            cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess && sync) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) {
         ctx->has_trip = false;
@@ -145,6 +155,8 @@ latch_status latch_context_create(int device, latch_context** out) {
     const double defaults[3] = {1.0, 1.5, 2.25};
     latch_status st = upload_scales(ctx, defaults, 3);
     if (st == LATCH_OK) st = cuda_check(ctx, cudaMalloc(&ctx->d_trip, sizeof(ctx->h_trip)), "cudaMalloc(triplets)");
+    if (st == LATCH_OK)
+        st = cuda_check(ctx, cudaMalloc(&ctx->d_trip_offsets, sizeof(ctx->h_trip_offsets)), "cudaMalloc(triplets)");
     if (st == LATCH_OK) st = cuda_check(ctx, cudaMalloc(&ctx->d_flags, 64), "cudaMalloc(flags)");
     if (st == LATCH_OK) st = cuda_check(ctx, cudaMemset(ctx->d_flags, 0, 64), "cudaMemset(flags)");
     if (st != LATCH_OK) {
@@ -160,8 +172,9 @@ latch_status latch_context_destroy(latch_context* ctx) {
     if (!ctx) return LATCH_OK;
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
-    if (ctx->d_offsets) cudaFree(ctx->d_offsets);
+    if (ctx->d_tile_offsets) cudaFree(ctx->d_tile_offsets);
     if (ctx->d_trip) cudaFree(ctx->d_trip);
+    if (ctx->d_trip_offsets) cudaFree(ctx->d_trip_offsets);
     if (ctx->d_flags) cudaFree(ctx->d_flags);
     for (auto& s : ctx->scratch)
         if (s.ptr) cudaFree(s.ptr);
@@ -196,6 +209,10 @@ latch_status latch_reserve(latch_context* ctx, int64_t max_keypoints, int64_t ma
     if (st == LATCH_OK) st = scratch_reserve(ctx, 1, match_popc_scratch_bytes(ctx, max_query, max_train), &p);
     if (st == LATCH_OK) st = scratch_reserve(ctx, 2, match_tc_scratch_bytes(ctx, max_query, max_train), &p);
     return st;
+}
+
+int32_t hamming_match_path(const latch_context* ctx, int64_t nq, int64_t nt) {
+    return ctx ? choose_match_path(ctx, nq, nt) : -1;
 }
 
 latch_status latch_check(latch_context* ctx) {

@@ -1,84 +1,468 @@
 // LATCH descriptor extraction (Sec. 3.1 Eq. 1; Sec. 3.2).
 //
-// One warp per keypoint: the lanes gather the oriented, scaled 48x48 window into
-// shared memory through the per-(scale, bin) offset table (nearest pixel; samples
-// outside the image read 0), then every lane evaluates 16 triplets
-// t = 32*w + lane, w = 0..15: D1 = ||P_A - P_1||^2, D2 = ||P_A - P_2||^2 over the
-// 7x7 patches in exact integer arithmetic, bit = D1 > D2.  __ballot_sync packs the
-// 32 bits of word w (bit i = triplet 32*w + i, i.e. bit t is bit t%8 of byte t/8),
-// and lanes 0..15 write the 16 words of the descriptor as one coalesced 64-byte row.
+// 1. bucket_kernel (one block): counting sort of the keypoints into 64x64-pixel
+//    image cells.  The cell grid reaches 128 px beyond every border; keypoints
+//    further out have windows wholly outside the image (the window reaches at most
+//    `reach` <= 78 px), whose samples all read 0, so their descriptor is all zeros
+//    and is written here directly.  Keypoints with a scale index outside the scale
+//    table also get zeros and raise the context's device flag.
+// 2. extract_cells_kernel (one block per cell, 8 warps): the image tile under the
+//    cell plus a `reach` halo is staged into shared memory by one TMA 2-D load
+//    (samples outside the image arrive as 0, the border reading).  For each
+//    keypoint of the cell in turn, the block
+//      - samples the 48x48 window through the per-(scale, bin) offset table
+//        (nearest pixel; offsets pre-multiplied into tile offsets) and stores it
+//        as 4 byte-shifted copies, so that the 8 bytes holding any 7-pixel patch
+//        row are two aligned 32-bit words;
+//      - evaluates Eq. 1 for 32 triplets per warp at a time, one triplet per lane:
+//        D1 - D2 = (sum C1^2 - sum C2^2) - 2 (sum A.C1 - sum A.C2) over the 7 rows,
+//        with __dp4a on 4 pixels at a time, all exact in 32-bit integers;
+//      - packs the 32 bits of each warp-group with __ballot_sync (bit t = bit
+//        t % 32 of word t / 32, i.e. bit t % 8 of byte t / 8) and writes the
+//        64-byte descriptor as four 128-bit stores.
+//    Windows are double-buffered so one __syncthreads per keypoint suffices.
+#include <cuda.h>
+
+#include <cmath>
 #include <cstdint>
 
 #include "internal.h"
+#include "sm103.h"
 
 namespace latch {
 
 namespace {
 
-constexpr int kWarps = 4;
-constexpr int kThreads = kWarps * 32;
+using namespace sm103;
 
-__global__ void __launch_bounds__(kThreads) extract_naive_kernel(
-    const uint8_t* __restrict__ img, int width, int height, int64_t pitch, const latch_keypoint* __restrict__ kps,
-    int n, const int8_t* __restrict__ offsets, int nscales, const uint8_t* __restrict__ trip_g,
-    uint32_t* __restrict__ out, uint32_t* __restrict__ flags) {
-    __shared__ uint8_t s_trip[kBits * 6];
-    __shared__ uint8_t s_win[kWarps][kWinPix];
-    for (int i = threadIdx.x; i < kBits * 6; i += kThreads) s_trip[i] = trip_g[i];
+constexpr int kCell = 64;
+constexpr int kMargin = 128;            // cell grid reaches this far beyond each border
+constexpr int kThreads = 256;           // 8 warps
+constexpr int kRowWords = 12;           // 48 bytes per window row
+constexpr int kCopyWords = kWin * kRowWords + 4;   // one byte-shifted copy (+4: bank offset)
+constexpr int kWinWords = 4 * kCopyWords;          // 4 copies
+constexpr int kBucketThreads = 1024;
+constexpr int kMaxSmemCells = 12288;
+constexpr int kItemKps = 16;            // keypoints per work item (block)
+
+struct CellGrid {
+    int gx, gy;  // cells in x / y (including the margins)
+    int width, height;
+};
+
+// Cell of a keypoint: >= 0, -1 (window wholly outside: zero descriptor), -2 (bad scale).
+__device__ __forceinline__ int cell_of(const latch_keypoint& kp, int nscales, const CellGrid& g) {
+    if (kp.scale_idx >= nscales) return -2;
+    const int64_t x = static_cast<int64_t>(kp.x) + kMargin, y = static_cast<int64_t>(kp.y) + kMargin;
+    if (x < 0 || y < 0 || x >= static_cast<int64_t>(g.width) + 2 * kMargin ||
+        y >= static_cast<int64_t>(g.height) + 2 * kMargin)
+        return -1;
+    return static_cast<int>(y / kCell) * g.gx + static_cast<int>(x / kCell);
+}
+
+__global__ void __launch_bounds__(kBucketThreads) bucket_kernel(const latch_keypoint* __restrict__ kps, int n,
+                                                                int nscales, CellGrid g, int* __restrict__ gcount,
+                                                                int4* __restrict__ items, int* __restrict__ n_items,
+                                                                int* __restrict__ perm, uint4* __restrict__ out,
+                                                                uint32_t* __restrict__ flags) {
+    extern __shared__ int s_cnt[];
+    __shared__ int s_part[kBucketThreads / 32];
+    __shared__ int s_ipart[kBucketThreads / 32];
+    const int ncell = g.gx * g.gy;
+    const bool in_smem = ncell <= kMaxSmemCells;
+    int* cnt = in_smem ? s_cnt : gcount;  // gcount was zeroed by the host when used
+    if (in_smem)
+        for (int c = threadIdx.x; c < ncell; c += blockDim.x) cnt[c] = 0;
     __syncthreads();
-
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    uint8_t* win = s_win[warp];
-    for (int k = blockIdx.x * kWarps + warp; k < n; k += gridDim.x * kWarps) {
-        const latch_keypoint kp = kps[k];
-        uint32_t word = 0;
-        if (kp.scale_idx < nscales) {
-            const char2* tab = reinterpret_cast<const char2*>(offsets) +
-                               (static_cast<size_t>(kp.scale_idx) * kBins + (kp.angle_bin & (kBins - 1))) * kWinPix;
-            for (int i = lane; i < kWinPix; i += 32) {
-                const char2 o = tab[i];
-                const int64_t x = static_cast<int64_t>(kp.x) + o.x;
-                const int64_t y = static_cast<int64_t>(kp.y) + o.y;
-                win[i] = (x >= 0 && x < width && y >= 0 && y < height) ? img[y * pitch + x] : 0;
-            }
-            __syncwarp();
-            for (int w = 0; w < kDescWords; ++w) {
-                const uint8_t* t = s_trip + 6 * (32 * w + lane);
-                const int ax = t[0] - kPatchR, ay = t[1] - kPatchR;
-                const int c1x = t[2] - kPatchR, c1y = t[3] - kPatchR;
-                const int c2x = t[4] - kPatchR, c2y = t[5] - kPatchR;
-                int d1 = 0, d2 = 0;  // <= 49 * 255^2 < 2^22
-                for (int i = 0; i < 2 * kPatchR + 1; ++i)
-                    for (int j = 0; j < 2 * kPatchR + 1; ++j) {
-                        const int a = win[(ay + i) * kWin + ax + j];
-                        const int p1 = win[(c1y + i) * kWin + c1x + j];
-                        const int p2 = win[(c2y + i) * kWin + c2x + j];
-                        d1 += (a - p1) * (a - p1);
-                        d2 += (a - p2) * (a - p2);
-                    }
-                const uint32_t b = __ballot_sync(0xffffffffu, d1 > d2);
-                if (lane == w) word = b;
-            }
-            __syncwarp();
-        } else if (lane == 0) {
-            atomicOr(flags, kFlagBadScale);
+    bool bad = false;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int c = cell_of(kps[i], nscales, g);
+        if (c >= 0) {
+            atomicAdd(&cnt[c], 1);
+        } else {
+            const uint4 z = make_uint4(0, 0, 0, 0);
+            uint4* d = out + static_cast<size_t>(i) * 4;
+            d[0] = z;
+            d[1] = z;
+            d[2] = z;
+            d[3] = z;
+            bad |= (c == -2);
         }
-        if (lane < kDescWords) out[static_cast<size_t>(k) * kDescWords + lane] = word;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, kFlagBadScale);
+    // exclusive scans of the counts and of the work items (chunks of at most
+    // kItemKps keypoints of one cell): each thread sums a contiguous run of cells
+    const int per = (ncell + blockDim.x - 1) / blockDim.x;
+    const int c0 = threadIdx.x * per, c1 = min(c0 + per, ncell);
+    int sum = 0, isum = 0;
+    for (int c = c0; c < c1; ++c) {
+        const int k = cnt[c];
+        sum += k;
+        isum += (k + kItemKps - 1) / kItemKps;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = sum, iincl = isum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        const int w = __shfl_up_sync(0xffffffffu, iincl, o);
+        if (lane >= o) {
+            incl += v;
+            iincl += w;
+        }
+    }
+    if (lane == 31) {
+        s_part[warp] = incl;
+        s_ipart[warp] = iincl;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        int v = lane < kBucketThreads / 32 ? s_part[lane] : 0;
+        int vi = lane < kBucketThreads / 32 ? s_ipart[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int w = __shfl_up_sync(0xffffffffu, v, o);
+            const int wi = __shfl_up_sync(0xffffffffu, vi, o);
+            if (lane >= o) {
+                v += w;
+                vi += wi;
+            }
+        }
+        if (lane < kBucketThreads / 32) {
+            s_part[lane] = v;
+            s_ipart[lane] = vi;
+        }
+    }
+    __syncthreads();
+    int run = incl - sum + (warp > 0 ? s_part[warp - 1] : 0);
+    int irun = iincl - isum + (warp > 0 ? s_ipart[warp - 1] : 0);
+    for (int c = c0; c < c1; ++c) {
+        const int k = cnt[c];
+        for (int j = 0; j < k; j += kItemKps) items[irun++] = make_int4(c, run + j, run + min(j + kItemKps, k), 0);
+        cnt[c] = run;  // becomes the insertion cursor
+        run += k;
+    }
+    if (threadIdx.x == blockDim.x - 1) *n_items = irun;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int c = cell_of(kps[i], nscales, g);
+        if (c >= 0) perm[atomicAdd(&cnt[c], 1)] = i;
+    }
+}
+
+struct TileGeom {
+    int tw, th;      // staged tile (bytes per row, rows)
+    int mx, my;      // tile origin relative to the cell origin (negative)
+};
+
+__global__ void __launch_bounds__(kThreads) extract_cells_kernel(
+    const __grid_constant__ CUtensorMap tm_img, const latch_keypoint* __restrict__ kps,
+    const int* __restrict__ perm, const int4* __restrict__ items, const int* __restrict__ n_items, CellGrid g,
+    TileGeom tg, const int16_t* __restrict__ toff, const uint2* __restrict__ trip_off, uint4* __restrict__ out,
+    uint32_t* __restrict__ flags) {
+    extern __shared__ uint8_t smem_raw[];
+    if (static_cast<int>(blockIdx.x) >= *n_items) return;
+    const int4 item = items[blockIdx.x];
+    const int cell = item.x, k0 = item.y, k1 = item.z;
+
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    uint32_t* s_win = reinterpret_cast<uint32_t*>(smem);                  // [2][kWinWords]
+    uint8_t* s_bits = reinterpret_cast<uint8_t*>(s_win + 2 * kWinWords);  // [2][512] one byte per bit
+    uint64_t* s_bar = reinterpret_cast<uint64_t*>(s_bits + 2 * kBits);
+    volatile int* s_abort = reinterpret_cast<volatile int*>(s_bar + 1);
+    uint8_t* s_tile = reinterpret_cast<uint8_t*>(s_bar + 2);
+    s_tile = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(s_tile) + 127) & ~uintptr_t(127));
+
+    const int cx = cell % g.gx, cy = cell / g.gx;
+    const int ox = cx * kCell - kMargin + tg.mx;  // tile origin in image coordinates
+    const int oy = cy * kCell - kMargin + tg.my;
+    if (threadIdx.x == 0) {
+        mbar_init(s_bar, 1);
+        *s_abort = 0;
+        fence_mbar_init();
+        prefetch_tmap(&tm_img);
+        mbar_arrive_expect_tx(s_bar, static_cast<uint32_t>(tg.tw * tg.th));
+        tma_load_2d(s_tile, &tm_img, ox, oy, s_bar);
+    }
+    __syncthreads();
+    const bool ok = mbar_wait(s_bar, 0, s_abort);
+    if (!__syncthreads_and(ok)) {
+        if (threadIdx.x == 0) {
+            atomicOr(flags, kFlagTimeout);
+            const uint64_t t0 = globaltimer();  // let the copy land before the block exits
+            while (!mbar_try_wait(s_bar, 0) && globaltimer() - t0 < 200000000ull) {
+            }
+        }
+        return;
+    }
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // this thread's window-build job: row y, pixels 12*seg .. 12*seg+14
+    const int by = threadIdx.x >> 2, bseg = threadIdx.x & 3;
+    // this lane's two triplets (slots 64*warp + lane and +32 of the bank-conflict
+    // minimising order): patch word offsets and the triplet's bit position
+    const uint2 to0 = trip_off[64 * warp + lane];
+    const uint2 to1 = trip_off[64 * warp + 32 + lane];
+
+    for (int k = k0; k <= k1; ++k) {
+        const int buf = k & 1;
+        if (k < k1 && threadIdx.x < 192) {
+            // ---- sample the window of keypoint k into 4 byte-shifted copies ----
+            const latch_keypoint kp = kps[perm[k]];
+            const int base = (kp.y - oy) * tg.tw + (kp.x - ox);
+            const int16_t* tab = toff + (static_cast<size_t>(kp.scale_idx) * kBins + (kp.angle_bin & (kBins - 1))) *
+                                            kWinPix +
+                                 by * kWin + 12 * bseg;
+            // entries 0..15 of this row segment, as four 8-byte loads (the segment starts
+            // 24*bseg bytes into a 96-byte row: 8-byte aligned)
+            const int2* t2 = reinterpret_cast<const int2*>(tab);
+            const int2 ta = t2[0], tb = t2[1], tc = t2[2], td = t2[3];
+            const int32_t tw[8] = {ta.x, ta.y, tb.x, tb.y, tc.x, tc.y, td.x, td.y};
+            uint32_t p[4] = {0, 0, 0, 0};
+#pragma unroll
+            for (int u = 0; u < 15; ++u) {
+                if (12 * bseg + u < kWin) {
+                    const int16_t o = static_cast<int16_t>((tw[u >> 1] >> (16 * (u & 1))) & 0xffff);
+                    p[u >> 2] |= static_cast<uint32_t>(s_tile[base + o]) << (8 * (u & 3));
+                }
+            }
+            uint32_t* w = s_win + buf * kWinWords + by * kRowWords + 3 * bseg;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                w[j] = p[j];
+                w[kCopyWords + j] = __funnelshift_r(p[j], p[j + 1], 8);
+                w[2 * kCopyWords + j] = __funnelshift_r(p[j], p[j + 1], 16);
+                w[3 * kCopyWords + j] = __funnelshift_r(p[j], p[j + 1], 24);
+            }
+        }
+        __syncthreads();
+        if (k > k0 && warp == 0) {
+            // ---- pack and store the descriptor of keypoint k-1 (all its bits were
+            // written before the barrier above): word w collects bits 32w..32w+31 ----
+            const uint8_t* b = s_bits + ((k - 1) & 1) * kBits;
+            uint32_t mine = 0;  // lane w < 16 keeps word w
+#pragma unroll
+            for (int w = 0; w < kDescWords; ++w) {
+                const uint32_t word = __ballot_sync(0xffffffffu, b[32 * w + lane] != 0);
+                if (lane == w) mine = word;
+            }
+            const int src = (4 * lane) & 31;
+            const uint32_t x = __shfl_sync(0xffffffffu, mine, src);
+            const uint32_t y = __shfl_sync(0xffffffffu, mine, src + 1);
+            const uint32_t z = __shfl_sync(0xffffffffu, mine, src + 2);
+            const uint32_t v = __shfl_sync(0xffffffffu, mine, src + 3);
+            if (lane < 4) out[static_cast<size_t>(perm[k - 1]) * 4 + lane] = make_uint4(x, y, z, v);
+        }
+        if (k == k1) break;
+        // ---- Eq. 1 for this lane's two triplets ----
+        const uint32_t* wb = s_win + buf * kWinWords;
+        uint8_t* bits = s_bits + buf * kBits;
+#pragma unroll
+        for (int gi = 0; gi < 2; ++gi) {
+            const uint2 to = gi == 0 ? to0 : to1;
+            const uint32_t* pa = wb + (to.x & 0xffffu);
+            const uint32_t* p1 = wb + (to.x >> 16);
+            const uint32_t* p2 = wb + (to.y & 0xffffu);
+            uint32_t sa1 = 0, sa2 = 0, s11 = 0, s22 = 0;
+#pragma unroll
+            for (int i = 0; i < 2 * kPatchR + 1; ++i) {
+                const uint32_t a0 = pa[i * kRowWords], a1 = pa[i * kRowWords + 1];
+                const uint32_t c0 = p1[i * kRowWords], c1 = p1[i * kRowWords + 1] & 0x00ffffffu;
+                const uint32_t e0 = p2[i * kRowWords], e1 = p2[i * kRowWords + 1] & 0x00ffffffu;
+                sa1 = __dp4a(a0, c0, sa1);
+                sa1 = __dp4a(a1, c1, sa1);
+                sa2 = __dp4a(a0, e0, sa2);
+                sa2 = __dp4a(a1, e1, sa2);
+                s11 = __dp4a(c0, c0, s11);
+                s11 = __dp4a(c1, c1, s11);
+                s22 = __dp4a(e0, e0, s22);
+                s22 = __dp4a(e1, e1, s22);
+            }
+            // D1 - D2 = sum C1^2 - sum C2^2 - 2 (sum A.C1 - sum A.C2)
+            const int diff = (static_cast<int>(s11) - static_cast<int>(s22)) -
+                             2 * (static_cast<int>(sa1) - static_cast<int>(sa2));
+            bits[to.y >> 16] = diff > 0 ? 1 : 0;
+        }
     }
 }
 
 }  // namespace
 
-size_t extract_scratch_bytes(const latch_image*, int64_t) { return 0; }
+// Host-side precomputation for the cell kernel ------------------------------------
+
+static TileGeom tile_geom(int reach) {
+    TileGeom t;
+    const int rx = (reach + 15) / 16 * 16;  // x margin rounded to the 16-byte TMA granule
+    t.tw = kCell + 2 * rx;
+    t.th = kCell + 2 * reach;
+    t.mx = -rx;
+    t.my = -reach;
+    return t;
+}
+
+int extract_tile_pitch(int reach) { return tile_geom(reach).tw; }
+
+// Word offset of the top-left 8-byte run of the patch centred at (cx, cy) in the
+// 4-copy window layout.
+static uint32_t patch_word(int cx, int cy) {
+    const int x0 = cx - kPatchR, y0 = cy - kPatchR;
+    return static_cast<uint32_t>((x0 & 3) * kCopyWords + y0 * kRowWords + (x0 >> 2));
+}
+
+// Order in which the lanes evaluate the triplets.  32 lanes of a warp read the
+// same row of their patches with one shared-memory instruction; lanes whose words
+// fall in the same bank serialise.  A short deterministic annealing over swaps
+// between the 16 groups of 32 minimises the sum over groups and patch roles of the
+// squared bank occupancies.  Bits go back to their triplet positions through
+// shared memory, so the descriptor does not depend on the order.
+static void plan_triplet_order(const latch_triplet* trip, int* order) {
+    int bank[kBits][3];
+    for (int t = 0; t < kBits; ++t) {
+        const uint8_t* c = &trip[t].ax;
+        for (int p = 0; p < 3; ++p) bank[t][p] = static_cast<int>(patch_word(c[2 * p], c[2 * p + 1]) & 31);
+    }
+    constexpr int kGroups = kBits / 32;
+    int cnt[kGroups][3][32] = {};
+    for (int i = 0; i < kBits; ++i) {
+        order[i] = i;
+        for (int p = 0; p < 3; ++p) ++cnt[i / 32][p][bank[i][p]];
+    }
+    uint64_t st = 0x9E3779B97F4A7C15ull;
+    auto next = [&st]() {
+        st ^= st << 13;
+        st ^= st >> 7;
+        st ^= st << 17;
+        return st;
+    };
+    const int iters = 400000;
+    for (int it = 0; it < iters; ++it) {
+        const int s1 = static_cast<int>(next() % kBits), s2 = static_cast<int>(next() % kBits);
+        const int g1 = s1 / 32, g2 = s2 / 32;
+        if (g1 == g2) continue;
+        const int t1 = order[s1], t2 = order[s2];
+        // change of sum(count^2) when t1 moves g1 -> g2 and t2 moves g2 -> g1
+        int delta = 0;
+        for (int p = 0; p < 3; ++p) {
+            const int b1 = bank[t1][p], b2 = bank[t2][p];
+            if (b1 == b2) continue;
+            delta += 2 * (cnt[g1][p][b2] - cnt[g1][p][b1] + 1);  // g1 loses b1, gains b2
+            delta += 2 * (cnt[g2][p][b1] - cnt[g2][p][b2] + 1);  // g2 loses b2, gains b1
+        }
+        const double temp = 3.0 * (1.0 - static_cast<double>(it) / iters) + 1e-3;
+        const double u = static_cast<double>(next() >> 11) * 0x1.0p-53;
+        if (delta <= 0 || u < std::exp(-delta / temp)) {
+            for (int p = 0; p < 3; ++p) {
+                --cnt[g1][p][bank[t1][p]];
+                ++cnt[g1][p][bank[t2][p]];
+                --cnt[g2][p][bank[t2][p]];
+                ++cnt[g2][p][bank[t1][p]];
+            }
+            order[s1] = t2;
+            order[s2] = t1;
+        }
+    }
+}
+
+// Per lane slot: the three patches' word offsets and the triplet's bit position.
+void build_triplet_offsets(const latch_triplet* trip, uint32_t* out /* 2 per triplet */) {
+    int order[kBits];
+    plan_triplet_order(trip, order);
+    for (int slot = 0; slot < kBits; ++slot) {
+        const int t = order[slot];
+        const uint8_t* c = &trip[t].ax;
+        out[2 * slot] = patch_word(c[0], c[1]) | (patch_word(c[2], c[3]) << 16);
+        out[2 * slot + 1] = patch_word(c[4], c[5]) | (static_cast<uint32_t>(t) << 16);
+    }
+}
+
+static CellGrid cell_grid(const latch_image* img) {
+    CellGrid g;
+    g.width = img->width;
+    g.height = img->height;
+    g.gx = (img->width + 2 * kMargin + kCell - 1) / kCell;
+    g.gy = (img->height + 2 * kMargin + kCell - 1) / kCell;
+    return g;
+}
+
+static int64_t max_items(int64_t n, const CellGrid& g) {
+    const int64_t ncell = static_cast<int64_t>(g.gx) * g.gy;
+    return (n + kItemKps - 1) / kItemKps + (ncell < n ? ncell : n);
+}
+
+size_t extract_scratch_bytes(const latch_image* img, int64_t n) {
+    const CellGrid g = cell_grid(img);
+    const size_t ncell = static_cast<size_t>(g.gx) * g.gy;
+    return (ncell + 4 + static_cast<size_t>(n)) * sizeof(int) + static_cast<size_t>(max_items(n, g)) * sizeof(int4) +
+           256;
+}
+
+static size_t extract_smem_bytes(const TileGeom& tg) {
+    return 128 + static_cast<size_t>(2 * kWinWords) * 4 + 2 * kBits + 16 + 128 + static_cast<size_t>(tg.tw) * tg.th;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn extract_encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
 
 cudaError_t launch_extract(const latch_context* ctx, const latch_image* img, const latch_keypoint* d_kps, int32_t n,
-                           uint8_t* d_out, void*, cudaStream_t stream) {
-    const int blocks_needed = (n + kWarps - 1) / kWarps;
-    const int grid = blocks_needed < ctx->sm_count * 16 ? blocks_needed : ctx->sm_count * 16;
-    extract_naive_kernel<<<grid, kThreads, 0, stream>>>(img->data, img->width, img->height, img->pitch, d_kps, n,
-                                                        ctx->d_offsets, ctx->nscales, ctx->d_trip,
-                                                        reinterpret_cast<uint32_t*>(d_out), ctx->d_flags);
+                           uint8_t* d_out, void* scratch, cudaStream_t stream) {
+    const CellGrid g = cell_grid(img);
+    const int ncell = g.gx * g.gy;
+    const TileGeom tg = tile_geom(ctx->reach);
+    // scratch: items (int4, 16-byte aligned first), counts, item count, permutation
+    const int64_t nitem_max = max_items(n, g);
+    int4* items = static_cast<int4*>(scratch);
+    int* cell_count = reinterpret_cast<int*>(items + nitem_max);
+    int* n_items = cell_count + ncell;
+    int* perm = n_items + 4;
+    cudaError_t e;
+    if (ncell > kMaxSmemCells) {
+        e = cudaMemsetAsync(cell_count, 0, sizeof(int) * ncell, stream);
+        if (e != cudaSuccess) return e;
+    }
+    const size_t bucket_smem = ncell <= kMaxSmemCells ? sizeof(int) * ncell : 0;
+    static bool attr = false;
+    const size_t smem = extract_smem_bytes(tg);
+    if (!attr) {
+        e = cudaFuncSetAttribute(bucket_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(sizeof(int) * kMaxSmemCells));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(extract_cells_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(extract_smem_bytes(tile_geom(kMaxReach + 1))));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    bucket_kernel<<<1, kBucketThreads, bucket_smem, stream>>>(d_kps, n, ctx->nscales, g, cell_count, items, n_items,
+                                                              perm, reinterpret_cast<uint4*>(d_out), ctx->d_flags);
+    note_launches(1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+
+    EncodeTiledFn enc = extract_encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    CUtensorMap map;
+    cuuint64_t dims[2] = {static_cast<cuuint64_t>(img->width), static_cast<cuuint64_t>(img->height)};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(img->pitch)};
+    cuuint32_t box[2] = {static_cast<cuuint32_t>(tg.tw), static_cast<cuuint32_t>(tg.th)};
+    cuuint32_t estr[2] = {1, 1};
+    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(img->data), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    extract_cells_kernel<<<static_cast<unsigned>(nitem_max), kThreads, smem, stream>>>(
+        map, d_kps, perm, items, n_items, g, tg, ctx->d_tile_offsets,
+        reinterpret_cast<const uint2*>(ctx->d_trip_offsets), reinterpret_cast<uint4*>(d_out), ctx->d_flags);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -1,6 +1,6 @@
 // LATCH descriptor extraction (Sec. 3.1 Eq. 1; Sec. 3.2).
 //
-// 1. bucket_kernel (one block): counting sort of the keypoints into 64x64-pixel
+// 1. bucket_kernel (one block): counting sort of the keypoints into 32x32-pixel
 //    image cells.  The cell grid reaches 128 px beyond every border; keypoints
 //    further out have windows wholly outside the image (the window reaches at most
 //    `reach` <= 78 px), whose samples all read 0, so their descriptor is all zeros
@@ -35,11 +35,11 @@ namespace {
 
 using namespace sm103;
 
-constexpr int kCell = 64;
+constexpr int kCell = 32;
 constexpr int kMargin = 128;            // cell grid reaches this far beyond each border
 constexpr int kThreads = 256;           // 8 warps
 constexpr int kRowWords = 12;           // 48 bytes per window row
-constexpr int kCopyWords = kWin * kRowWords + 4;   // one byte-shifted copy (+4: bank offset)
+constexpr int kCopyWords = kWin * kRowWords + 4;   // one byte-shifted copy (+4: bank offset; 16-byte multiple)
 constexpr int kWinWords = 4 * kCopyWords;          // 4 copies
 constexpr int kBucketThreads = 1024;
 constexpr int kMaxSmemCells = 12288;
@@ -75,18 +75,28 @@ __global__ void __launch_bounds__(kBucketThreads) bucket_kernel(const latch_keyp
         for (int c = threadIdx.x; c < ncell; c += blockDim.x) cnt[c] = 0;
     __syncthreads();
     bool bad = false;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const int c = cell_of(kps[i], nscales, g);
-        if (c >= 0) {
-            atomicAdd(&cnt[c], 1);
-        } else {
-            const uint4 z = make_uint4(0, 0, 0, 0);
-            uint4* d = out + static_cast<size_t>(i) * 4;
-            d[0] = z;
-            d[1] = z;
-            d[2] = z;
-            d[3] = z;
-            bad |= (c == -2);
+    // 8 independent keypoint loads in flight per thread
+    for (int i0 = threadIdx.x; i0 < n; i0 += 8 * blockDim.x) {
+        int cc[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int i = i0 + j * blockDim.x;
+            cc[j] = i < n ? cell_of(kps[i], nscales, g) : -3;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int i = i0 + j * blockDim.x;
+            if (cc[j] >= 0) {
+                atomicAdd(&cnt[cc[j]], 1);
+            } else if (cc[j] > -3) {
+                const uint4 z = make_uint4(0, 0, 0, 0);
+                uint4* d = out + static_cast<size_t>(i) * 4;
+                d[0] = z;
+                d[1] = z;
+                d[2] = z;
+                d[3] = z;
+                bad |= (cc[j] == -2);
+            }
         }
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, kFlagBadScale);
@@ -142,9 +152,16 @@ __global__ void __launch_bounds__(kBucketThreads) bucket_kernel(const latch_keyp
     }
     if (threadIdx.x == blockDim.x - 1) *n_items = irun;
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const int c = cell_of(kps[i], nscales, g);
-        if (c >= 0) perm[atomicAdd(&cnt[c], 1)] = i;
+    for (int i0 = threadIdx.x; i0 < n; i0 += 8 * blockDim.x) {
+        int cc[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int i = i0 + j * blockDim.x;
+            cc[j] = i < n ? cell_of(kps[i], nscales, g) : -3;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (cc[j] >= 0) perm[atomicAdd(&cnt[cc[j]], 1)] = i0 + j * blockDim.x;
     }
 }
 
@@ -195,8 +212,8 @@ __global__ void __launch_bounds__(kThreads) extract_cells_kernel(
     }
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // this thread's window-build job: row y, pixels 12*seg .. 12*seg+14
-    const int by = threadIdx.x >> 2, bseg = threadIdx.x & 3;
+    // this thread's window-build job (threads 0..143): row by, 16-pixel segment bseg
+    const int by = threadIdx.x / 3, bseg = threadIdx.x % 3;
     // this lane's two triplets (slots 64*warp + lane and +32 of the bank-conflict
     // minimising order): patch word offsets and the triplet's bit position
     const uint2 to0 = trip_off[64 * warp + lane];
@@ -204,34 +221,35 @@ __global__ void __launch_bounds__(kThreads) extract_cells_kernel(
 
     for (int k = k0; k <= k1; ++k) {
         const int buf = k & 1;
-        if (k < k1 && threadIdx.x < 192) {
-            // ---- sample the window of keypoint k into 4 byte-shifted copies ----
+        if (k < k1 && threadIdx.x < 144) {
+            // ---- sample the window of keypoint k into 4 byte-shifted copies; this
+            // thread: row by, pixels 16*bseg .. 16*bseg+18 ----
             const latch_keypoint kp = kps[perm[k]];
             const int base = (kp.y - oy) * tg.tw + (kp.x - ox);
             const int16_t* tab = toff + (static_cast<size_t>(kp.scale_idx) * kBins + (kp.angle_bin & (kBins - 1))) *
                                             kWinPix +
-                                 by * kWin + 12 * bseg;
-            // entries 0..15 of this row segment, as four 8-byte loads (the segment starts
-            // 24*bseg bytes into a 96-byte row: 8-byte aligned)
-            const int2* t2 = reinterpret_cast<const int2*>(tab);
-            const int2 ta = t2[0], tb = t2[1], tc = t2[2], td = t2[3];
-            const int32_t tw[8] = {ta.x, ta.y, tb.x, tb.y, tc.x, tc.y, td.x, td.y};
-            uint32_t p[4] = {0, 0, 0, 0};
+                                 by * kWin + 16 * bseg;
+            // table entries 0..19 of the segment (32-byte aligned: 96*by + 32*bseg bytes)
+            const int4 ta = reinterpret_cast<const int4*>(tab)[0];
+            const int4 tb = reinterpret_cast<const int4*>(tab)[1];
+            const int2 tc = reinterpret_cast<const int2*>(tab)[4];
+            const int32_t tw[10] = {ta.x, ta.y, ta.z, ta.w, tb.x, tb.y, tb.z, tb.w, tc.x, tc.y};
+            uint32_t p[5] = {0, 0, 0, 0, 0};
 #pragma unroll
-            for (int u = 0; u < 15; ++u) {
-                if (12 * bseg + u < kWin) {
+            for (int u = 0; u < 19; ++u) {
+                if (16 * bseg + u < kWin) {
                     const int16_t o = static_cast<int16_t>((tw[u >> 1] >> (16 * (u & 1))) & 0xffff);
                     p[u >> 2] |= static_cast<uint32_t>(s_tile[base + o]) << (8 * (u & 3));
                 }
             }
-            uint32_t* w = s_win + buf * kWinWords + by * kRowWords + 3 * bseg;
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                w[j] = p[j];
-                w[kCopyWords + j] = __funnelshift_r(p[j], p[j + 1], 8);
-                w[2 * kCopyWords + j] = __funnelshift_r(p[j], p[j + 1], 16);
-                w[3 * kCopyWords + j] = __funnelshift_r(p[j], p[j + 1], 24);
-            }
+            uint4* w = reinterpret_cast<uint4*>(s_win + buf * kWinWords + by * kRowWords + 4 * bseg);
+            w[0] = make_uint4(p[0], p[1], p[2], p[3]);
+            w[kCopyWords / 4] = make_uint4(__funnelshift_r(p[0], p[1], 8), __funnelshift_r(p[1], p[2], 8),
+                                           __funnelshift_r(p[2], p[3], 8), __funnelshift_r(p[3], p[4], 8));
+            w[2 * kCopyWords / 4] = make_uint4(__funnelshift_r(p[0], p[1], 16), __funnelshift_r(p[1], p[2], 16),
+                                               __funnelshift_r(p[2], p[3], 16), __funnelshift_r(p[3], p[4], 16));
+            w[3 * kCopyWords / 4] = make_uint4(__funnelshift_r(p[0], p[1], 24), __funnelshift_r(p[1], p[2], 24),
+                                               __funnelshift_r(p[2], p[3], 24), __funnelshift_r(p[3], p[4], 24));
         }
         __syncthreads();
         if (k > k0 && warp == 0) {
@@ -440,6 +458,8 @@ cudaError_t launch_extract(const latch_context* ctx, const latch_image* img, con
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(extract_cells_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      static_cast<int>(extract_smem_bytes(tile_geom(kMaxReach + 1))));
+        if (e == cudaSuccess)  // four 56 KB blocks per SM
+            e = cudaFuncSetAttribute(extract_cells_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e != cudaSuccess) return e;
         attr = true;
     }

@@ -162,6 +162,36 @@ latch_status hamming_match(latch_context *ctx, const uint8_t *d_query, int32_t n
                            int32_t nt, int32_t k, float ratio, latch_match *d_out, int32_t path,
                            latch_stream_t stream);
 
+/* A batch of images, each matched against others (the structure-from-motion
+ * pattern of Sec. 4-5: every image against its neighbours in sequence).
+ * Keypoints and descriptors of all images are concatenated image by image: image i
+ * owns rows [o_i, o_i + h_n_kps[i]) with o_i = sum of the earlier counts.  Matches
+ * are concatenated pair by pair: pair p owns h_n_kps[query image of p] records
+ * starting at the sum of the earlier pairs' query counts; train indices in a
+ * record are relative to the train image. */
+typedef struct {
+    int32_t n_images;
+    const latch_image *h_images;     /* host array [n_images] of device images */
+    const int32_t *h_n_kps;          /* host array [n_images]: keypoints per image */
+    const latch_keypoint *d_kps;     /* device: all keypoints, image by image */
+    uint8_t *d_desc;                 /* device out: 64 bytes per keypoint, same order */
+    int32_t n_pairs;
+    const int32_t *h_pairs;          /* host array [2 * n_pairs]: (query image, train image) */
+    int32_t k;                       /* 1 or 2 */
+    float ratio;                     /* in [0, 1] */
+    latch_match *d_matches;          /* device out: see above */
+} latch_batch_desc;
+
+/* Size the context's batch scratch for `batch` (same shapes later allocate
+ * nothing; required before capturing latch_batch_run in a CUDA graph). */
+latch_status latch_reserve_batch(latch_context *ctx, const latch_batch_desc *batch);
+
+/* Extract every image's descriptors (as latch_extract, with the context's triplet
+ * and scale tables) and match every pair (as hamming_match on the tensor-core
+ * path), enqueued on `stream` as a few batched persistent launches.  Results are
+ * identical to calling latch_extract and hamming_match one by one. */
+latch_status latch_batch_run(latch_context *ctx, const latch_batch_desc *batch, latch_stream_t stream);
+
 /* The path LATCH_PATH_AUTO takes for nq x nt on this context (LATCH_PATH_POPC or
  * LATCH_PATH_TENSOR); -1 on a NULL context. */
 int32_t hamming_match_path(const latch_context *ctx, int64_t nq, int64_t nt);

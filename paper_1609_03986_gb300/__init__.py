@@ -45,6 +45,13 @@ class latch_image(ctypes.Structure):
                 ("pitch", ctypes.c_int64)]
 
 
+class latch_batch_desc(ctypes.Structure):
+    _fields_ = [("n_images", ctypes.c_int32), ("h_images", ctypes.c_void_p), ("h_n_kps", ctypes.c_void_p),
+                ("d_kps", ctypes.c_void_p), ("d_desc", ctypes.c_void_p), ("n_pairs", ctypes.c_int32),
+                ("h_pairs", ctypes.c_void_p), ("k", ctypes.c_int32), ("ratio", ctypes.c_float),
+                ("d_matches", ctypes.c_void_p)]
+
+
 _lib = None
 
 # (name, restype, argtypes) of every exported entry point
@@ -62,6 +69,8 @@ EXPORTS = [
     ("latch_check", ctypes.c_int, [_P]),
     ("latch_kernel_launches", ctypes.c_uint64, []),
     ("hamming_match_path", ctypes.c_int32, [_P, _I64, _I64]),
+    ("latch_reserve_batch", ctypes.c_int, [_P, ctypes.POINTER(latch_batch_desc)]),
+    ("latch_batch_run", ctypes.c_int, [_P, ctypes.POINTER(latch_batch_desc), _P]),
     ("hamming_match_noalloc", ctypes.c_int, [_P, _I32, _P, _I32, _I32, _F, _P, _P]),
 ]
 
@@ -162,6 +171,34 @@ def hamming_match_noalloc(query, nq: int, train, nt: int, k: int, ratio: float, 
 
 def latch_check(ctx) -> None:
     _check(ctx, library().latch_check(ctx))
+
+
+class BatchDesc:
+    """Host-side arrays of a latch_batch_desc, kept alive with the struct.
+
+    images: list of (device pointer, width, height, pitch); n_kps: list of ints;
+    pairs: list of (query image, train image)."""
+
+    def __init__(self, images, n_kps, d_kps, d_desc, pairs, k, ratio, d_matches):
+        self._imgs = (latch_image * max(1, len(images)))(*[latch_image(_ptr(p), w, h, pt) for p, w, h, pt in images])
+        self._n = np.ascontiguousarray(n_kps, dtype=np.int32)
+        self._pairs = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+        self.desc = latch_batch_desc(len(images), ctypes.addressof(self._imgs), self._n.ctypes.data, _ptr(d_kps),
+                                     _ptr(d_desc), self._pairs.shape[0], self._pairs.ctypes.data, k, ratio,
+                                     _ptr(d_matches))
+
+    def match_offsets(self):
+        """First match record of every pair."""
+        q = self._n[self._pairs[:, 0]].astype(np.int64)
+        return np.concatenate([[0], np.cumsum(q)])
+
+
+def latch_reserve_batch(ctx, batch: BatchDesc) -> None:
+    _check(ctx, library().latch_reserve_batch(ctx, ctypes.byref(batch.desc)))
+
+
+def latch_batch_run(ctx, batch: BatchDesc, stream: int = 0) -> None:
+    _check(ctx, library().latch_batch_run(ctx, ctypes.byref(batch.desc), stream))
 
 
 def hamming_match_path(ctx, nq: int, nt: int) -> int:

@@ -60,17 +60,43 @@ __device__ __forceinline__ int cell_of(const latch_keypoint& kp, int nscales, co
     return static_cast<int>(y / kCell) * g.gx + static_cast<int>(x / kCell);
 }
 
-__global__ void __launch_bounds__(kBucketThreads) bucket_kernel(const latch_keypoint* __restrict__ kps, int n,
-                                                                int nscales, CellGrid g, int* __restrict__ gcount,
-                                                                int4* __restrict__ items, int* __restrict__ n_items,
-                                                                int* __restrict__ perm, uint4* __restrict__ out,
-                                                                uint32_t* __restrict__ flags) {
+struct TileGeom {
+    int tw, th;      // staged tile (bytes per row, rows)
+    int mx, my;      // tile origin relative to the cell origin (negative)
+};
+
+// Per-launch description of a batch of images (kernel parameters).
+template <int NI>
+struct ExtractParams {
+    CUtensorMap map[NI];  // one TMA map per image
+    CellGrid grid[NI];
+    int32_t kp0[NI];      // first keypoint of image i in the concatenated keypoint array
+    int32_t n[NI];        // keypoints of image i
+    int32_t cell0[NI];    // first entry of image i in the global cell-count scratch
+    int32_t count;        // images in this launch
+    int32_t nscales;
+    TileGeom tg;
+};
+
+// One block per image: counting sort of its keypoints into cells, then its work
+// items (chunks of at most kItemKps keypoints of one cell) are appended to the
+// launch's global item list.  counters[0] = number of items (zeroed by the host).
+template <int NI>
+__global__ void __launch_bounds__(kBucketThreads) bucket_kernel(const __grid_constant__ ExtractParams<NI> prm,
+                                                                const latch_keypoint* __restrict__ kps,
+                                                                int* __restrict__ gcount, int4* __restrict__ items,
+                                                                int* __restrict__ counters, int* __restrict__ perm,
+                                                                uint4* __restrict__ out, uint32_t* __restrict__ flags) {
     extern __shared__ int s_cnt[];
     __shared__ int s_part[kBucketThreads / 32];
     __shared__ int s_ipart[kBucketThreads / 32];
+    __shared__ int s_item_base;
+    const int img = blockIdx.x;
+    const CellGrid g = prm.grid[img];
+    const int n = prm.n[img], kp0 = prm.kp0[img];
     const int ncell = g.gx * g.gy;
     const bool in_smem = ncell <= kMaxSmemCells;
-    int* cnt = in_smem ? s_cnt : gcount;  // gcount was zeroed by the host when used
+    int* cnt = in_smem ? s_cnt : gcount + prm.cell0[img];  // the global counts were zeroed by the host
     if (in_smem)
         for (int c = threadIdx.x; c < ncell; c += blockDim.x) cnt[c] = 0;
     __syncthreads();
@@ -81,7 +107,7 @@ __global__ void __launch_bounds__(kBucketThreads) bucket_kernel(const latch_keyp
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int i = i0 + j * blockDim.x;
-            cc[j] = i < n ? cell_of(kps[i], nscales, g) : -3;
+            cc[j] = i < n ? cell_of(kps[kp0 + i], prm.nscales, g) : -3;
         }
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
@@ -90,7 +116,7 @@ __global__ void __launch_bounds__(kBucketThreads) bucket_kernel(const latch_keyp
                 atomicAdd(&cnt[cc[j]], 1);
             } else if (cc[j] > -3) {
                 const uint4 z = make_uint4(0, 0, 0, 0);
-                uint4* d = out + static_cast<size_t>(i) * 4;
+                uint4* d = out + static_cast<size_t>(kp0 + i) * 4;
                 d[0] = z;
                 d[1] = z;
                 d[2] = z;
@@ -100,8 +126,8 @@ __global__ void __launch_bounds__(kBucketThreads) bucket_kernel(const latch_keyp
         }
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, kFlagBadScale);
-    // exclusive scans of the counts and of the work items (chunks of at most
-    // kItemKps keypoints of one cell): each thread sums a contiguous run of cells
+    // exclusive scans of the counts and of the work items: each thread sums a
+    // contiguous run of cells
     const int per = (ncell + blockDim.x - 1) / blockDim.x;
     const int c0 = threadIdx.x * per, c1 = min(c0 + per, ncell);
     int sum = 0, isum = 0;
@@ -140,46 +166,40 @@ __global__ void __launch_bounds__(kBucketThreads) bucket_kernel(const latch_keyp
             s_part[lane] = v;
             s_ipart[lane] = vi;
         }
+        if (lane == kBucketThreads / 32 - 1) s_item_base = atomicAdd(&counters[0], vi);
     }
     __syncthreads();
-    int run = incl - sum + (warp > 0 ? s_part[warp - 1] : 0);
-    int irun = iincl - isum + (warp > 0 ? s_ipart[warp - 1] : 0);
+    int run = kp0 + incl - sum + (warp > 0 ? s_part[warp - 1] : 0);
+    int irun = s_item_base + iincl - isum + (warp > 0 ? s_ipart[warp - 1] : 0);
     for (int c = c0; c < c1; ++c) {
         const int k = cnt[c];
-        for (int j = 0; j < k; j += kItemKps) items[irun++] = make_int4(c, run + j, run + min(j + kItemKps, k), 0);
-        cnt[c] = run;  // becomes the insertion cursor
+        for (int j = 0; j < k; j += kItemKps) items[irun++] = make_int4(img, c, run + j, run + min(j + kItemKps, k));
+        cnt[c] = run;  // becomes the insertion cursor (a position in perm)
         run += k;
     }
-    if (threadIdx.x == blockDim.x - 1) *n_items = irun;
     __syncthreads();
     for (int i0 = threadIdx.x; i0 < n; i0 += 8 * blockDim.x) {
         int cc[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int i = i0 + j * blockDim.x;
-            cc[j] = i < n ? cell_of(kps[i], nscales, g) : -3;
+            cc[j] = i < n ? cell_of(kps[kp0 + i], prm.nscales, g) : -3;
         }
 #pragma unroll
         for (int j = 0; j < 8; ++j)
-            if (cc[j] >= 0) perm[atomicAdd(&cnt[cc[j]], 1)] = i0 + j * blockDim.x;
+            if (cc[j] >= 0) perm[atomicAdd(&cnt[cc[j]], 1)] = kp0 + i0 + j * blockDim.x;
     }
 }
 
-struct TileGeom {
-    int tw, th;      // staged tile (bytes per row, rows)
-    int mx, my;      // tile origin relative to the cell origin (negative)
-};
-
+// Persistent: blocks take work items from the launch's queue (counters[1]).
+template <int NI>
 __global__ void __launch_bounds__(kThreads) extract_cells_kernel(
-    const __grid_constant__ CUtensorMap tm_img, const latch_keypoint* __restrict__ kps,
-    const int* __restrict__ perm, const int4* __restrict__ items, const int* __restrict__ n_items, CellGrid g,
-    TileGeom tg, const int16_t* __restrict__ toff, const uint2* __restrict__ trip_off, uint4* __restrict__ out,
+    const __grid_constant__ ExtractParams<NI> prm, const latch_keypoint* __restrict__ kps,
+    const int* __restrict__ perm, const int4* __restrict__ items, int* __restrict__ counters,
+    const int16_t* __restrict__ toff, const uint2* __restrict__ trip_off, uint4* __restrict__ out,
     uint32_t* __restrict__ flags) {
     extern __shared__ uint8_t smem_raw[];
-    if (static_cast<int>(blockIdx.x) >= *n_items) return;
-    const int4 item = items[blockIdx.x];
-    const int cell = item.x, k0 = item.y, k1 = item.z;
-
+    __shared__ int s_item;
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     uint32_t* s_win = reinterpret_cast<uint32_t*>(smem);                  // [2][kWinWords]
     uint8_t* s_bits = reinterpret_cast<uint8_t*>(s_win + 2 * kWinWords);  // [2][512] one byte per bit
@@ -187,30 +207,14 @@ __global__ void __launch_bounds__(kThreads) extract_cells_kernel(
     volatile int* s_abort = reinterpret_cast<volatile int*>(s_bar + 1);
     uint8_t* s_tile = reinterpret_cast<uint8_t*>(s_bar + 2);
     s_tile = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(s_tile) + 127) & ~uintptr_t(127));
+    const TileGeom tg = prm.tg;
+    const int n_items = counters[0];
 
-    const int cx = cell % g.gx, cy = cell / g.gx;
-    const int ox = cx * kCell - kMargin + tg.mx;  // tile origin in image coordinates
-    const int oy = cy * kCell - kMargin + tg.my;
     if (threadIdx.x == 0) {
         mbar_init(s_bar, 1);
         *s_abort = 0;
         fence_mbar_init();
-        prefetch_tmap(&tm_img);
-        mbar_arrive_expect_tx(s_bar, static_cast<uint32_t>(tg.tw * tg.th));
-        tma_load_2d(s_tile, &tm_img, ox, oy, s_bar);
     }
-    __syncthreads();
-    const bool ok = mbar_wait(s_bar, 0, s_abort);
-    if (!__syncthreads_and(ok)) {
-        if (threadIdx.x == 0) {
-            atomicOr(flags, kFlagTimeout);
-            const uint64_t t0 = globaltimer();  // let the copy land before the block exits
-            while (!mbar_try_wait(s_bar, 0) && globaltimer() - t0 < 200000000ull) {
-            }
-        }
-        return;
-    }
-
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // this thread's window-build job (threads 0..143): row by, 16-pixel segment bseg
     const int by = threadIdx.x / 3, bseg = threadIdx.x % 3;
@@ -219,85 +223,114 @@ __global__ void __launch_bounds__(kThreads) extract_cells_kernel(
     const uint2 to0 = trip_off[64 * warp + lane];
     const uint2 to1 = trip_off[64 * warp + 32 + lane];
 
-    for (int k = k0; k <= k1; ++k) {
-        const int buf = k & 1;
-        if (k < k1 && threadIdx.x < 144) {
-            // ---- sample the window of keypoint k into 4 byte-shifted copies; this
-            // thread: row by, pixels 16*bseg .. 16*bseg+18 ----
-            const latch_keypoint kp = kps[perm[k]];
-            const int base = (kp.y - oy) * tg.tw + (kp.x - ox);
-            const int16_t* tab = toff + (static_cast<size_t>(kp.scale_idx) * kBins + (kp.angle_bin & (kBins - 1))) *
-                                            kWinPix +
-                                 by * kWin + 16 * bseg;
-            // table entries 0..19 of the segment (32-byte aligned: 96*by + 32*bseg bytes)
-            const int4 ta = reinterpret_cast<const int4*>(tab)[0];
-            const int4 tb = reinterpret_cast<const int4*>(tab)[1];
-            const int2 tc = reinterpret_cast<const int2*>(tab)[4];
-            const int32_t tw[10] = {ta.x, ta.y, ta.z, ta.w, tb.x, tb.y, tb.z, tb.w, tc.x, tc.y};
-            uint32_t p[5] = {0, 0, 0, 0, 0};
-#pragma unroll
-            for (int u = 0; u < 19; ++u) {
-                if (16 * bseg + u < kWin) {
-                    const int16_t o = static_cast<int16_t>((tw[u >> 1] >> (16 * (u & 1))) & 0xffff);
-                    p[u >> 2] |= static_cast<uint32_t>(s_tile[base + o]) << (8 * (u & 3));
+    for (uint32_t phase = 0;; phase ^= 1) {
+        if (threadIdx.x == 0) s_item = atomicAdd(&counters[1], 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= n_items) break;
+        const int4 item = items[it];
+        const int img = item.x, cell = item.y, k0 = item.z, k1 = item.w;
+        const CellGrid g = prm.grid[img];
+        const int cx = cell % g.gx, cy = cell / g.gx;
+        const int ox = cx * kCell - kMargin + tg.mx;  // tile origin in image coordinates
+        const int oy = cy * kCell - kMargin + tg.my;
+        if (threadIdx.x == 0) {
+            mbar_arrive_expect_tx(s_bar, static_cast<uint32_t>(tg.tw * tg.th));
+            tma_load_2d(s_tile, &prm.map[img], ox, oy, s_bar);
+        }
+        const bool ok = mbar_wait(s_bar, phase, s_abort);
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0) {
+                atomicOr(flags, kFlagTimeout);
+                const uint64_t t0 = globaltimer();  // let the copy land before the block exits
+                while (!mbar_try_wait(s_bar, phase) && globaltimer() - t0 < 200000000ull) {
                 }
             }
-            uint4* w = reinterpret_cast<uint4*>(s_win + buf * kWinWords + by * kRowWords + 4 * bseg);
-            w[0] = make_uint4(p[0], p[1], p[2], p[3]);
-            w[kCopyWords / 4] = make_uint4(__funnelshift_r(p[0], p[1], 8), __funnelshift_r(p[1], p[2], 8),
-                                           __funnelshift_r(p[2], p[3], 8), __funnelshift_r(p[3], p[4], 8));
-            w[2 * kCopyWords / 4] = make_uint4(__funnelshift_r(p[0], p[1], 16), __funnelshift_r(p[1], p[2], 16),
-                                               __funnelshift_r(p[2], p[3], 16), __funnelshift_r(p[3], p[4], 16));
-            w[3 * kCopyWords / 4] = make_uint4(__funnelshift_r(p[0], p[1], 24), __funnelshift_r(p[1], p[2], 24),
-                                               __funnelshift_r(p[2], p[3], 24), __funnelshift_r(p[3], p[4], 24));
+            return;
         }
-        __syncthreads();
-        if (k > k0 && warp == 0) {
-            // ---- pack and store the descriptor of keypoint k-1 (all its bits were
-            // written before the barrier above): word w collects bits 32w..32w+31 ----
-            const uint8_t* b = s_bits + ((k - 1) & 1) * kBits;
-            uint32_t mine = 0;  // lane w < 16 keeps word w
+
+        for (int k = k0; k <= k1; ++k) {
+            const int buf = k & 1;
+            if (k < k1 && threadIdx.x < 144) {
+                // ---- sample the window of keypoint k into 4 byte-shifted copies; this
+                // thread: row by, pixels 16*bseg .. 16*bseg+18 ----
+                const latch_keypoint kp = kps[perm[k]];
+                const int base = (kp.y - oy) * tg.tw + (kp.x - ox);
+                const int16_t* tab =
+                    toff + (static_cast<size_t>(kp.scale_idx) * kBins + (kp.angle_bin & (kBins - 1))) * kWinPix +
+                    by * kWin + 16 * bseg;
+                // table entries 0..19 of the segment (32-byte aligned: 96*by + 32*bseg bytes)
+                const int4 ta = reinterpret_cast<const int4*>(tab)[0];
+                const int4 tb = reinterpret_cast<const int4*>(tab)[1];
+                const int2 tc = reinterpret_cast<const int2*>(tab)[4];
+                const int32_t tw[10] = {ta.x, ta.y, ta.z, ta.w, tb.x, tb.y, tb.z, tb.w, tc.x, tc.y};
+                uint32_t p[5] = {0, 0, 0, 0, 0};
 #pragma unroll
-            for (int w = 0; w < kDescWords; ++w) {
-                const uint32_t word = __ballot_sync(0xffffffffu, b[32 * w + lane] != 0);
-                if (lane == w) mine = word;
+                for (int u = 0; u < 19; ++u) {
+                    if (16 * bseg + u < kWin) {
+                        const int16_t o = static_cast<int16_t>((tw[u >> 1] >> (16 * (u & 1))) & 0xffff);
+                        p[u >> 2] |= static_cast<uint32_t>(s_tile[base + o]) << (8 * (u & 3));
+                    }
+                }
+                uint4* w = reinterpret_cast<uint4*>(s_win + buf * kWinWords + by * kRowWords + 4 * bseg);
+                w[0] = make_uint4(p[0], p[1], p[2], p[3]);
+                w[kCopyWords / 4] = make_uint4(__funnelshift_r(p[0], p[1], 8), __funnelshift_r(p[1], p[2], 8),
+                                               __funnelshift_r(p[2], p[3], 8), __funnelshift_r(p[3], p[4], 8));
+                w[2 * kCopyWords / 4] =
+                    make_uint4(__funnelshift_r(p[0], p[1], 16), __funnelshift_r(p[1], p[2], 16),
+                               __funnelshift_r(p[2], p[3], 16), __funnelshift_r(p[3], p[4], 16));
+                w[3 * kCopyWords / 4] =
+                    make_uint4(__funnelshift_r(p[0], p[1], 24), __funnelshift_r(p[1], p[2], 24),
+                               __funnelshift_r(p[2], p[3], 24), __funnelshift_r(p[3], p[4], 24));
             }
-            const int src = (4 * lane) & 31;
-            const uint32_t x = __shfl_sync(0xffffffffu, mine, src);
-            const uint32_t y = __shfl_sync(0xffffffffu, mine, src + 1);
-            const uint32_t z = __shfl_sync(0xffffffffu, mine, src + 2);
-            const uint32_t v = __shfl_sync(0xffffffffu, mine, src + 3);
-            if (lane < 4) out[static_cast<size_t>(perm[k - 1]) * 4 + lane] = make_uint4(x, y, z, v);
-        }
-        if (k == k1) break;
-        // ---- Eq. 1 for this lane's two triplets ----
-        const uint32_t* wb = s_win + buf * kWinWords;
-        uint8_t* bits = s_bits + buf * kBits;
+            __syncthreads();
+            if (k > k0 && warp == 0) {
+                // ---- pack and store the descriptor of keypoint k-1 (all its bits were
+                // written before the barrier above): word w collects bits 32w..32w+31 ----
+                const uint8_t* b = s_bits + ((k - 1) & 1) * kBits;
+                uint32_t mine = 0;  // lane w < 16 keeps word w
 #pragma unroll
-        for (int gi = 0; gi < 2; ++gi) {
-            const uint2 to = gi == 0 ? to0 : to1;
-            const uint32_t* pa = wb + (to.x & 0xffffu);
-            const uint32_t* p1 = wb + (to.x >> 16);
-            const uint32_t* p2 = wb + (to.y & 0xffffu);
-            uint32_t sa1 = 0, sa2 = 0, s11 = 0, s22 = 0;
-#pragma unroll
-            for (int i = 0; i < 2 * kPatchR + 1; ++i) {
-                const uint32_t a0 = pa[i * kRowWords], a1 = pa[i * kRowWords + 1];
-                const uint32_t c0 = p1[i * kRowWords], c1 = p1[i * kRowWords + 1] & 0x00ffffffu;
-                const uint32_t e0 = p2[i * kRowWords], e1 = p2[i * kRowWords + 1] & 0x00ffffffu;
-                sa1 = __dp4a(a0, c0, sa1);
-                sa1 = __dp4a(a1, c1, sa1);
-                sa2 = __dp4a(a0, e0, sa2);
-                sa2 = __dp4a(a1, e1, sa2);
-                s11 = __dp4a(c0, c0, s11);
-                s11 = __dp4a(c1, c1, s11);
-                s22 = __dp4a(e0, e0, s22);
-                s22 = __dp4a(e1, e1, s22);
+                for (int w = 0; w < kDescWords; ++w) {
+                    const uint32_t word = __ballot_sync(0xffffffffu, b[32 * w + lane] != 0);
+                    if (lane == w) mine = word;
+                }
+                const int src = (4 * lane) & 31;
+                const uint32_t x = __shfl_sync(0xffffffffu, mine, src);
+                const uint32_t y = __shfl_sync(0xffffffffu, mine, src + 1);
+                const uint32_t z = __shfl_sync(0xffffffffu, mine, src + 2);
+                const uint32_t v = __shfl_sync(0xffffffffu, mine, src + 3);
+                if (lane < 4) out[static_cast<size_t>(perm[k - 1]) * 4 + lane] = make_uint4(x, y, z, v);
             }
-            // D1 - D2 = sum C1^2 - sum C2^2 - 2 (sum A.C1 - sum A.C2)
-            const int diff = (static_cast<int>(s11) - static_cast<int>(s22)) -
-                             2 * (static_cast<int>(sa1) - static_cast<int>(sa2));
-            bits[to.y >> 16] = diff > 0 ? 1 : 0;
+            if (k == k1) break;
+            // ---- Eq. 1 for this lane's two triplets ----
+            const uint32_t* wb = s_win + buf * kWinWords;
+            uint8_t* bits = s_bits + buf * kBits;
+#pragma unroll
+            for (int gi = 0; gi < 2; ++gi) {
+                const uint2 to = gi == 0 ? to0 : to1;
+                const uint32_t* pa = wb + (to.x & 0xffffu);
+                const uint32_t* p1 = wb + (to.x >> 16);
+                const uint32_t* p2 = wb + (to.y & 0xffffu);
+                uint32_t sa1 = 0, sa2 = 0, s11 = 0, s22 = 0;
+#pragma unroll
+                for (int i = 0; i < 2 * kPatchR + 1; ++i) {
+                    const uint32_t a0 = pa[i * kRowWords], a1 = pa[i * kRowWords + 1];
+                    const uint32_t c0 = p1[i * kRowWords], c1 = p1[i * kRowWords + 1] & 0x00ffffffu;
+                    const uint32_t e0 = p2[i * kRowWords], e1 = p2[i * kRowWords + 1] & 0x00ffffffu;
+                    sa1 = __dp4a(a0, c0, sa1);
+                    sa1 = __dp4a(a1, c1, sa1);
+                    sa2 = __dp4a(a0, e0, sa2);
+                    sa2 = __dp4a(a1, e1, sa2);
+                    s11 = __dp4a(c0, c0, s11);
+                    s11 = __dp4a(c1, c1, s11);
+                    s22 = __dp4a(e0, e0, s22);
+                    s22 = __dp4a(e1, e1, s22);
+                }
+                // D1 - D2 = sum C1^2 - sum C2^2 - 2 (sum A.C1 - sum A.C2)
+                const int diff = (static_cast<int>(s11) - static_cast<int>(s22)) -
+                                 2 * (static_cast<int>(sa1) - static_cast<int>(sa2));
+                bits[to.y >> 16] = diff > 0 ? 1 : 0;
+            }
         }
     }
 }
@@ -405,13 +438,6 @@ static int64_t max_items(int64_t n, const CellGrid& g) {
     return (n + kItemKps - 1) / kItemKps + (ncell < n ? ncell : n);
 }
 
-size_t extract_scratch_bytes(const latch_image* img, int64_t n) {
-    const CellGrid g = cell_grid(img);
-    const size_t ncell = static_cast<size_t>(g.gx) * g.gy;
-    return (ncell + 4 + static_cast<size_t>(n)) * sizeof(int) + static_cast<size_t>(max_items(n, g)) * sizeof(int4) +
-           256;
-}
-
 static size_t extract_smem_bytes(const TileGeom& tg) {
     return 128 + static_cast<size_t>(2 * kWinWords) * 4 + 2 * kBits + 16 + 128 + static_cast<size_t>(tg.tw) * tg.th;
 }
@@ -433,58 +459,144 @@ static EncodeTiledFn extract_encode_fn() {
     return fn;
 }
 
-cudaError_t launch_extract(const latch_context* ctx, const latch_image* img, const latch_keypoint* d_kps, int32_t n,
-                           uint8_t* d_out, void* scratch, cudaStream_t stream) {
-    const CellGrid g = cell_grid(img);
-    const int ncell = g.gx * g.gy;
-    const TileGeom tg = tile_geom(ctx->reach);
-    // scratch: items (int4, 16-byte aligned first), counts, item count, permutation
-    const int64_t nitem_max = max_items(n, g);
-    int4* items = static_cast<int4*>(scratch);
-    int* cell_count = reinterpret_cast<int*>(items + nitem_max);
-    int* n_items = cell_count + ncell;
-    int* perm = n_items + 4;
-    cudaError_t e;
-    if (ncell > kMaxSmemCells) {
-        e = cudaMemsetAsync(cell_count, 0, sizeof(int) * ncell, stream);
-        if (e != cudaSuccess) return e;
+// Scratch of one launch over images [i0, i1): counters, cell counts, perm, items.
+struct ChunkLayout {
+    size_t counters, cells, perm, items, total;
+    int64_t ncell, nkp, nitem;
+};
+
+static ChunkLayout chunk_layout(const latch_image* imgs, const int64_t* n, int i0, int i1) {
+    ChunkLayout l;
+    l.ncell = 0;
+    l.nkp = 0;
+    l.nitem = 0;
+    for (int i = i0; i < i1; ++i) {
+        const CellGrid g = cell_grid(&imgs[i]);
+        l.ncell += static_cast<int64_t>(g.gx) * g.gy;
+        l.nkp += n[i];
+        l.nitem += max_items(n[i], g);
     }
-    const size_t bucket_smem = ncell <= kMaxSmemCells ? sizeof(int) * ncell : 0;
+    l.items = 0;  // int4, 16-byte aligned
+    l.counters = l.items + static_cast<size_t>(l.nitem) * sizeof(int4);
+    l.cells = l.counters + 16;
+    l.perm = l.cells + static_cast<size_t>(l.ncell) * sizeof(int);
+    l.total = (l.perm + static_cast<size_t>(l.nkp) * sizeof(int) + 255) / 256 * 256;
+    return l;
+}
+
+static constexpr int kBatchImages = 64;  // images per launch in the batched form
+
+size_t extract_batch_scratch_bytes(const latch_image* imgs, const int64_t* n, int count) {
+    size_t total = 0;
+    for (int i0 = 0; i0 < count; i0 += kBatchImages) {
+        const int i1 = i0 + kBatchImages < count ? i0 + kBatchImages : count;
+        total += chunk_layout(imgs, n, i0, i1).total;
+    }
+    return total;
+}
+
+size_t extract_scratch_bytes(const latch_image* img, int64_t n) { return extract_batch_scratch_bytes(img, &n, 1); }
+
+template <int NI>
+static cudaError_t launch_chunk(const latch_context* ctx, const latch_image* imgs, const int64_t* kp0,
+                                const int64_t* n, int i0, int i1, const latch_keypoint* d_kps, uint8_t* d_out,
+                                uint8_t* scratch, cudaStream_t stream) {
     static bool attr = false;
-    const size_t smem = extract_smem_bytes(tg);
+    const TileGeom tg = tile_geom(ctx->reach);
+    cudaError_t e;
     if (!attr) {
-        e = cudaFuncSetAttribute(bucket_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(bucket_kernel<NI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(sizeof(int) * kMaxSmemCells));
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(extract_cells_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            e = cudaFuncSetAttribute(extract_cells_kernel<NI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      static_cast<int>(extract_smem_bytes(tile_geom(kMaxReach + 1))));
         if (e == cudaSuccess)  // four 56 KB blocks per SM
-            e = cudaFuncSetAttribute(extract_cells_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+            e = cudaFuncSetAttribute(extract_cells_kernel<NI>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    bucket_kernel<<<1, kBucketThreads, bucket_smem, stream>>>(d_kps, n, ctx->nscales, g, cell_count, items, n_items,
-                                                              perm, reinterpret_cast<uint4*>(d_out), ctx->d_flags);
-    note_launches(1);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-
     EncodeTiledFn enc = extract_encode_fn();
     if (!enc) return cudaErrorNotSupported;
-    CUtensorMap map;
-    cuuint64_t dims[2] = {static_cast<cuuint64_t>(img->width), static_cast<cuuint64_t>(img->height)};
-    cuuint64_t strides[1] = {static_cast<cuuint64_t>(img->pitch)};
-    cuuint32_t box[2] = {static_cast<cuuint32_t>(tg.tw), static_cast<cuuint32_t>(tg.th)};
-    cuuint32_t estr[2] = {1, 1};
-    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(img->data), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return cudaErrorInvalidValue;
-    extract_cells_kernel<<<static_cast<unsigned>(nitem_max), kThreads, smem, stream>>>(
-        map, d_kps, perm, items, n_items, g, tg, ctx->d_tile_offsets,
-        reinterpret_cast<const uint2*>(ctx->d_trip_offsets), reinterpret_cast<uint4*>(d_out), ctx->d_flags);
-    note_launches(1);
-    return cudaGetLastError();
+    const ChunkLayout l = chunk_layout(imgs, n, i0, i1);
+    int4* items = reinterpret_cast<int4*>(scratch + l.items);
+    int* counters = reinterpret_cast<int*>(scratch + l.counters);
+    int* cells = reinterpret_cast<int*>(scratch + l.cells);
+    int* perm = reinterpret_cast<int*>(scratch + l.perm);
+
+    ExtractParams<NI>* prm = new ExtractParams<NI>;
+    prm->count = i1 - i0;
+    prm->nscales = ctx->nscales;
+    prm->tg = tg;
+    bool global_cells = false;
+    int64_t cell0 = 0;
+    size_t bucket_smem = 0;
+    for (int i = i0; i < i1; ++i) {
+        const int j = i - i0;
+        const CellGrid g = cell_grid(&imgs[i]);
+        const int64_t ncell = static_cast<int64_t>(g.gx) * g.gy;
+        prm->grid[j] = g;
+        prm->kp0[j] = static_cast<int32_t>(kp0[i]);
+        prm->n[j] = static_cast<int32_t>(n[i]);
+        prm->cell0[j] = static_cast<int32_t>(cell0);
+        cell0 += ncell;
+        if (ncell > kMaxSmemCells)
+            global_cells = true;
+        else if (sizeof(int) * ncell > bucket_smem)
+            bucket_smem = sizeof(int) * ncell;
+        cuuint64_t dims[2] = {static_cast<cuuint64_t>(imgs[i].width), static_cast<cuuint64_t>(imgs[i].height)};
+        cuuint64_t strides[1] = {static_cast<cuuint64_t>(imgs[i].pitch)};
+        cuuint32_t box[2] = {static_cast<cuuint32_t>(tg.tw), static_cast<cuuint32_t>(tg.th)};
+        cuuint32_t estr[2] = {1, 1};
+        if (enc(&prm->map[j], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(imgs[i].data), dims, strides, box,
+                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+            delete prm;
+            return cudaErrorInvalidValue;
+        }
+    }
+    e = cudaMemsetAsync(counters, 0, 16, stream);
+    if (e == cudaSuccess && global_cells) e = cudaMemsetAsync(cells, 0, sizeof(int) * l.ncell, stream);
+    if (e == cudaSuccess) {
+        bucket_kernel<NI><<<i1 - i0, kBucketThreads, bucket_smem, stream>>>(
+            *prm, d_kps, cells, items, counters, perm, reinterpret_cast<uint4*>(d_out), ctx->d_flags);
+        note_launches(1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        const int64_t grid = l.nitem < 4 * ctx->sm_count ? l.nitem : 4 * ctx->sm_count;
+        extract_cells_kernel<NI><<<static_cast<unsigned>(grid), kThreads, extract_smem_bytes(tg), stream>>>(
+            *prm, d_kps, perm, items, counters, ctx->d_tile_offsets,
+            reinterpret_cast<const uint2*>(ctx->d_trip_offsets), reinterpret_cast<uint4*>(d_out), ctx->d_flags);
+        note_launches(1);
+        e = cudaGetLastError();
+    }
+    delete prm;
+    return e;
+}
+
+cudaError_t launch_extract_batch(const latch_context* ctx, const latch_image* imgs, const int64_t* kp0,
+                                 const int64_t* n, int count, const latch_keypoint* d_kps, uint8_t* d_out,
+                                 void* scratch, cudaStream_t stream) {
+    uint8_t* base = static_cast<uint8_t*>(scratch);
+    for (int i0 = 0; i0 < count; i0 += kBatchImages) {
+        const int i1 = i0 + kBatchImages < count ? i0 + kBatchImages : count;
+        int64_t nk = 0;
+        for (int i = i0; i < i1; ++i) nk += n[i];
+        if (nk > 0) {
+            const cudaError_t e =
+                (i1 - i0 == 1) ? launch_chunk<1>(ctx, imgs, kp0, n, i0, i1, d_kps, d_out, base, stream)
+                               : launch_chunk<kBatchImages>(ctx, imgs, kp0, n, i0, i1, d_kps, d_out, base, stream);
+            if (e != cudaSuccess) return e;
+        }
+        base += chunk_layout(imgs, n, i0, i1).total;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_extract(const latch_context* ctx, const latch_image* img, const latch_keypoint* d_kps, int32_t n,
+                           uint8_t* d_out, void* scratch, cudaStream_t stream) {
+    const int64_t kp0 = 0, nn = n;
+    return launch_extract_batch(ctx, img, &kp0, &nn, 1, d_kps, d_out, scratch, stream);
 }
 
 }  // namespace latch

@@ -74,6 +74,11 @@ void note_launches(int count);
 cudaError_t launch_extract(const latch_context* ctx, const latch_image* img, const latch_keypoint* d_kps, int32_t n,
                            uint8_t* d_out, void* scratch, cudaStream_t stream);
 size_t extract_scratch_bytes(const latch_image* img, int64_t n);
+// Images [0, count) with keypoints d_kps[kp0[i] .. kp0[i] + n[i]) -> d_out rows at the same positions.
+cudaError_t launch_extract_batch(const latch_context* ctx, const latch_image* imgs, const int64_t* kp0,
+                                 const int64_t* n, int count, const latch_keypoint* d_kps, uint8_t* d_out,
+                                 void* scratch, cudaStream_t stream);
+size_t extract_batch_scratch_bytes(const latch_image* imgs, const int64_t* n, int count);
 
 cudaError_t launch_match_popc(const latch_context* ctx, const uint8_t* q, int32_t nq, const uint8_t* t, int32_t nt,
                               int32_t k, int32_t r_milli, latch_match* out, void* scratch, cudaStream_t stream);

@@ -1,13 +1,14 @@
-// Work split and top-2 merge shared by the matching kernels.
+// Work split shared by the matching kernels.
 //
-// The (query tile, train tile) grid of a matching call is linearised query-tile
-// major, u = m * NT + n, and split into G contiguous ranges, range c = [start(c),
-// start(c+1)) with start(c) = floor(c * U / G).  Every block writes, for each query
-// tile it touched, the two smallest keys of each query row over its train tiles
-// ("partials", slot = c - first block of that query tile).  The merge kernel
-// combines the slots of a query row.  Keys are (distance << 32) | train index, so
-// the minimum of unique keys is the nearest train descriptor with ties resolved to
-// the lowest index (Sec. 4 matching; tie and ratio readings as in latch.h).
+// A matching launch serves a batch of problems (a query set against a train set).
+// The units of problem p -- (query tile m, train tile n), m-major -- are numbered
+// from p.unit0, and all units are split into G contiguous ranges, range c =
+// [start(c), start(c+1)) with start(c) = floor(c * U / G).  Every block writes, for
+// each query tile it touches, the two smallest keys of each query row over its
+// train tiles ("partial records", slot = tile index - first tile of the block).
+// The merge combines the records of a row.  Keys are (distance << 32) | train
+// index, so the minimum of unique keys is the nearest train descriptor with ties
+// resolved to the lowest index (Sec. 4 matching; tie and ratio readings in latch.h).
 #pragma once
 
 #include <stdint.h>
@@ -17,14 +18,23 @@
 namespace latch {
 
 constexpr uint64_t kNoKey = ~0ull;
+constexpr int kMaxProblems = 600;  // problems per launch (kernel-parameter space)
 
-struct WorkSplit {
-    int64_t mt;     // query tiles
-    int64_t nt;     // train tiles
-    int64_t units;  // mt * nt
-    int64_t grid;   // blocks
-    int64_t slots;  // max blocks touching one query tile
-    int rows;       // query rows per tile
+struct MatchProblem {
+    int64_t unit0;   // first global unit
+    int32_t q_row0;  // first row of the query set in the expanded buffer
+    int32_t t_row0;  // first row of the train set
+    int32_t nq, nt;
+    int32_t mt, ntl;  // query tiles, train tiles
+    int32_t g0;       // global index of the problem's first query tile
+    int32_t out0;     // first output record
+};
+
+struct MatchBatch {
+    int32_t count;
+    int32_t pad;
+    int64_t units, grid, smax, queries;
+    MatchProblem p[kMaxProblems];
 };
 
 __host__ __device__ __forceinline__ int64_t split_start(int64_t c, int64_t units, int64_t grid) {
@@ -39,36 +49,17 @@ __host__ __device__ __forceinline__ int64_t split_owner(int64_t u, int64_t units
     return c;
 }
 
-inline WorkSplit make_split(int64_t nq, int64_t nt, int rows, int cols, int64_t max_grid) {
-    WorkSplit s;
-    s.rows = rows;
-    s.mt = (nq + rows - 1) / rows;
-    s.nt = (nt + cols - 1) / cols;
-    s.units = s.mt * s.nt;
-    s.grid = s.units < max_grid ? s.units : max_grid;
-    s.slots = 0;
-    for (int64_t m = 0; m < s.mt && s.units > 0; ++m) {
-        const int64_t lo = split_owner(m * s.nt, s.units, s.grid);
-        const int64_t hi = split_owner((m + 1) * s.nt - 1, s.units, s.grid);
-        if (hi - lo + 1 > s.slots) s.slots = hi - lo + 1;
-    }
-    return s;
-}
-
 __device__ __forceinline__ void top2_insert_u64(uint64_t key, uint64_t& k1, uint64_t& k2) {
     const uint64_t hi = key > k1 ? key : k1;
     k1 = key < k1 ? key : k1;
     k2 = hi < k2 ? hi : k2;
 }
 
-// Partial record of (block c, query tile m, row r).
-__device__ __forceinline__ uint64_t* partial_ptr(uint64_t* partials, const WorkSplit& s, int64_t m, int64_t c,
-                                                 int r) {
-    const int64_t lo = split_owner(m * s.nt, s.units, s.grid);
-    return partials + ((m * s.slots + (c - lo)) * s.rows + r) * 2;
-}
-
-cudaError_t launch_match_merge(const uint64_t* partials, const WorkSplit& s, int32_t nq, int32_t k, int32_t r_milli,
-                               latch_match* out, cudaStream_t stream);
+void plan_match_batch(MatchBatch* b, int count, int64_t max_grid);
+size_t match_tc_batch_scratch_bytes(int64_t rows, const MatchBatch& b);
+cudaError_t launch_match_tc_batch(const MatchBatch& b, int64_t rows, void* scratch, int32_t k, int32_t r_milli,
+                                  latch_match* out, uint32_t* flags, cudaStream_t stream);
+cudaError_t launch_expand(const uint8_t* desc, int64_t n, uint8_t* out, int32_t* pop, cudaStream_t stream);
+size_t match_tc_scratch_bytes_sms(int64_t sms, int64_t nq, int64_t nt);
 
 }  // namespace latch

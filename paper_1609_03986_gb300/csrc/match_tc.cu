@@ -6,21 +6,25 @@
 // common 1-bits, and Hamming(q, t) = popc(q) + popc(t) - 2 * dot(q, t).  Products
 // are 0/1 and sums are at most 512, so fp32 accumulation is exact.
 //
-// Per block (one per SM, persistent over a contiguous range of (query tile, train
-// tile) units; see match_common.cuh):
-//   warp 0     TMA producer: a 256-query tile (two 128-row A operands, 128 KB,
-//              resident while the block stays on that query tile) and 128-row x
-//              128-byte train chunks into a 4-stage ring (16 KB each), 128-byte
-//              swizzle;
-//   warp 1     MMA issuer: for each 256 x 128 unit, 2 x 16 tcgen05.mma (M=128,
-//              N=128, K=32) into one of two double-buffered TMEM accumulators;
+// One launch serves a batch of matching problems (query set x train set pairs; a
+// single hamming_match call is a batch of one).  All descriptors live in one
+// expanded buffer with one TMA tensor map.  The units (problem, 256-query tile,
+// 128-train tile) of all problems are linearised and split into one contiguous
+// range per block (one block per SM, persistent):
+//   warp 0     TMA producer: the query tile (two 128-row A operands, 128 KB) stays
+//              resident while consecutive units share it; train chunks (128 rows x
+//              128 bytes) go through a 4-stage ring, 128-byte swizzle;
+//   warp 1     MMA issuer: per unit 2 x 16 tcgen05.mma (M=128, N=128, K=32) into one
+//              of two double-buffered TMEM accumulators;
 //   warp 2     TMEM allocator (all 512 columns);
 //   warps 4-7  epilogue: tcgen05.ld of the fp32 dot products, key =
 //              ((popc(t) - 2*dot + 512) << 8 | column) formed exactly in fp32 by
-//              one FMA, running min / second-min with FMNMX, then the two best of
-//              the tile are merged into the row's (distance << 32 | index) keys.
-// All mbarrier waits are bounded (sm103.h); on a timeout the block raises the
-// context's device flag, drains and frees TMEM.
+//              one FMA, running min / second-min with FMNMX; the tile's two best are
+//              merged into the row's (distance << 32 | index) keys, and when the
+//              block leaves a query tile the row's two keys go to a partial record.
+// match_merge_kernel combines the partial records of every query row (ties to the
+// lowest train index, ratio test).  All mbarrier waits are bounded (sm103.h); on a
+// timeout the block raises the device flag, drains its copies and MMAs, frees TMEM.
 #include <cuda.h>
 
 #include <cmath>
@@ -73,11 +77,18 @@ struct Smem {
 };
 constexpr int kSmemBytes = Smem::total + 1024;
 
-__global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_constant__ CUtensorMap tm_q,
-                                                              const __grid_constant__ CUtensorMap tm_t,
-                                                              const int32_t* __restrict__ pop_q,
-                                                              const int32_t* __restrict__ pop_t, int nq, int nt,
-                                                              WorkSplit split, uint64_t* __restrict__ partials,
+// Walks the units of a block's range in increasing order.
+struct UnitCursor {
+    int p = 0;
+    __device__ __forceinline__ void seek(const MatchBatch& b, int64_t u) {
+        while (p + 1 < b.count && b.p[p + 1].unit0 <= u) ++p;
+    }
+};
+
+__global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_constant__ CUtensorMap tm,
+                                                              const __grid_constant__ MatchBatch batch,
+                                                              const int32_t* __restrict__ pop,
+                                                              uint64_t* __restrict__ partials,
                                                               uint32_t* __restrict__ flags) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -98,8 +109,8 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int64_t c = blockIdx.x;
-    const int64_t u0 = split_start(c, split.units, split.grid);
-    const int64_t u1 = split_start(c + 1, split.units, split.grid);
+    const int64_t u0 = split_start(c, batch.units, batch.grid);
+    const int64_t u1 = split_start(c + 1, batch.units, batch.grid);
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < kStages; ++i) {
@@ -116,10 +127,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
         *abort = 0;
         fence_mbar_init();
     }
-    if (warp == 0 && lane == 0) {
-        prefetch_tmap(&tm_q);
-        prefetch_tmap(&tm_t);
-    }
+    if (warp == 0 && lane == 0) prefetch_tmap(&tm);
     if (warp == 2) {
         tmem_alloc(tmem_slot, kTmemCols);
         tc_fence_before();
@@ -131,25 +139,29 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
     if (warp == 0) {
         // ---------------- TMA producer ----------------
         if (lane == 0) {
+            UnitCursor cur;
             int stage = 0;
             uint32_t ring = 0, a_par = 0;
             uint32_t fill_par[kStages];
             bool filled[kStages];
             for (int s = 0; s < kStages; ++s) filled[s] = false, fill_par[s] = 0;
-            int64_t prev_m = -1;
+            int64_t prev_g = -1;
             for (int64_t u = u0; u < u1; ++u) {
-                const int64_t m = u / split.nt, n = u % split.nt;
-                if (m != prev_m) {
-                    if (prev_m >= 0) {
+                cur.seek(batch, u);
+                const MatchProblem& P = batch.p[cur.p];
+                const int64_t m = (u - P.unit0) / P.ntl, n = (u - P.unit0) % P.ntl;
+                const int64_t g = P.g0 + m;
+                if (g != prev_g) {
+                    if (prev_g >= 0) {
                         if (!mbar_wait(a_empty, a_par, abort)) break;
                         a_par ^= 1;
                     }
                     mbar_arrive_expect_tx(a_full, kSubA * kChunks * kTileBytes);
                     for (int a = 0; a < kSubA; ++a)
                         for (int kc = 0; kc < kChunks; ++kc)
-                            tma_load_2d(sA + (a * kChunks + kc) * kTileBytes, &tm_q, kc * kChunk,
-                                        static_cast<int32_t>(m * kRowsQ + a * kRowsA), a_full);
-                    prev_m = m;
+                            tma_load_2d(sA + (a * kChunks + kc) * kTileBytes, &tm, kc * kChunk,
+                                        static_cast<int32_t>(P.q_row0 + m * kRowsQ + a * kRowsA), a_full);
+                    prev_g = g;
                 }
                 bool ok = true;
                 for (int kc = 0; kc < kChunks; ++kc) {
@@ -158,7 +170,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                         break;
                     }
                     mbar_arrive_expect_tx(&full[stage], kTileBytes);
-                    tma_load_2d(sB + stage * kTileBytes, &tm_t, kc * kChunk, static_cast<int32_t>(n * kColsB),
+                    tma_load_2d(sB + stage * kTileBytes, &tm, kc * kChunk, static_cast<int32_t>(P.t_row0 + n * kColsB),
                                 &full[stage]);
                     filled[stage] = true;
                     fill_par[stage] = ring;
@@ -175,7 +187,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                 for (int s = 0; s < kStages; ++s)
                     while (filled[s] && !mbar_try_wait(&full[s], fill_par[s]) && globaltimer() - t0 < 200000000ull) {
                     }
-                if (prev_m >= 0)  // the last A load completes the a_full phase of parity a_par
+                if (prev_g >= 0)  // the last A load completes the a_full phase of parity a_par
                     while (!mbar_try_wait(a_full, a_par) && globaltimer() - t0 < 200000000ull) {
                     }
             }
@@ -183,18 +195,21 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
+            UnitCursor cur;
             int stage = 0;
             uint32_t ring = 0, a_par = 0;
             uint32_t acc_par[2] = {0, 0};
-            int64_t prev_m = -1;
+            int64_t prev_g = -1;
             int i = 0;
             for (int64_t u = u0; u < u1 && !*abort; ++u, ++i) {
-                const int64_t m = u / split.nt;
+                cur.seek(batch, u);
+                const MatchProblem& P = batch.p[cur.p];
+                const int64_t g = P.g0 + (u - P.unit0) / P.ntl;
                 const int buf = i & 1;
-                if (m != prev_m) {
+                if (g != prev_g) {
                     if (!mbar_wait(a_full, a_par, abort)) break;
                     a_par ^= 1;
-                    prev_m = m;
+                    prev_g = g;
                 }
                 if (!mbar_wait(&acc_empty[buf], acc_par[buf] ^ 1, abort)) break;
                 acc_par[buf] ^= 1;
@@ -224,8 +239,14 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                 }
                 if (!ok) break;
                 mma_commit(&acc_full[buf]);
-                const int64_t next_m = (u + 1 < u1) ? (u + 1) / split.nt : -1;
-                if (next_m != m) mma_commit(a_empty);
+                bool last_of_tile = (u + 1 >= u1);
+                if (!last_of_tile) {
+                    UnitCursor nx = cur;
+                    nx.seek(batch, u + 1);
+                    const MatchProblem& Q = batch.p[nx.p];
+                    last_of_tile = (Q.g0 + (u + 1 - Q.unit0) / Q.ntl) != g;
+                }
+                if (last_of_tile) mma_commit(a_empty);
             }
             // every issued MMA has finished before TMEM is released
             mma_commit(mma_done);
@@ -237,27 +258,32 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
         // ---------------- epilogue ----------------
         const int et = threadIdx.x - 128;  // 0..127: TMEM lane / column index
         const int quarter = warp & 3;
+        UnitCursor cur;
         uint32_t acc_par[2] = {0, 0};
         uint64_t k1[kSubA], k2[kSubA];
         int32_t pq[kSubA];
-        int64_t prev_m = -1;
+        int64_t prev_g = -1, g_first = -1;
         int i = 0;
         for (int64_t u = u0; u < u1; ++u, ++i) {
-            const int64_t m = u / split.nt, n = u % split.nt;
+            cur.seek(batch, u);
+            const MatchProblem& P = batch.p[cur.p];
+            const int64_t m = (u - P.unit0) / P.ntl, n = (u - P.unit0) % P.ntl;
+            const int64_t g = P.g0 + m;
             const int buf = i & 1;
-            if (m != prev_m) {
+            if (g != prev_g) {
 #pragma unroll
                 for (int a = 0; a < kSubA; ++a) {
                     const int64_t row = m * kRowsQ + a * kRowsA + quarter * 32 + lane;
-                    pq[a] = row < nq ? pop_q[row] : 0;
+                    pq[a] = row < P.nq ? pop[P.q_row0 + row] : 0;
                     k1[a] = k2[a] = kNoKey;
                 }
-                prev_m = m;
+                if (g_first < 0) g_first = g;
+                prev_g = g;
             }
             {
                 const int64_t col = n * kColsB + et;
-                sC[buf * kColsB + et] =
-                    col < nt ? static_cast<float>((pop_t[col] + 512) * 256 + et) : __int_as_float(0x7f800000);
+                sC[buf * kColsB + et] = col < P.nt ? static_cast<float>((pop[P.t_row0 + col] + 512) * 256 + et)
+                                                   : __int_as_float(0x7f800000);
             }
             // one vote of the 128 epilogue threads: also publishes sC; exits are group-uniform
             if (!group_all(mbar_wait(&acc_full[buf], acc_par[buf], abort))) break;
@@ -303,13 +329,20 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[buf]);
-            const int64_t next_m = (u + 1 < u1) ? (u + 1) / split.nt : -1;
-            if (next_m != m) {
+            bool last_of_tile = (u + 1 >= u1);
+            if (!last_of_tile) {
+                UnitCursor nx = cur;
+                nx.seek(batch, u + 1);
+                const MatchProblem& Q = batch.p[nx.p];
+                last_of_tile = (Q.g0 + (u + 1 - Q.unit0) / Q.ntl) != g;
+            }
+            if (last_of_tile) {
+                uint64_t* rec = partials + ((c * batch.smax + (g - g_first)) * kRowsQ) * 2;
 #pragma unroll
                 for (int a = 0; a < kSubA; ++a) {
-                    uint64_t* p = partial_ptr(partials, split, m, c, a * kRowsA + quarter * 32 + lane);
-                    p[0] = k1[a];
-                    p[1] = k2[a];
+                    const int r = a * kRowsA + quarter * 32 + lane;
+                    rec[2 * r] = k1[a];
+                    rec[2 * r + 1] = k2[a];
                 }
             }
         }
@@ -321,6 +354,61 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
         tc_fence_after();
         tmem_dealloc(tmem, kTmemCols);
     }
+}
+
+// Index of the problem containing global unit u (largest p with unit0 <= u).
+__device__ __forceinline__ int problem_of_unit(const MatchBatch& b, int64_t u) {
+    int lo = 0, hi = b.count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (b.p[mid].unit0 <= u) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Combine the partial records of every query row; write one latch_match per query.
+__global__ void match_merge_kernel(const __grid_constant__ MatchBatch batch, const uint64_t* __restrict__ partials,
+                                   int k, int r_milli, latch_match* __restrict__ out) {
+    const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (q >= batch.queries) return;
+    int lo = 0, hi = batch.count - 1;  // problem: largest p with out0 <= q
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (batch.p[mid].out0 <= q) lo = mid; else hi = mid - 1;
+    }
+    const MatchProblem& P = batch.p[lo];
+    const int64_t ql = q - P.out0;
+    uint64_t k1 = kNoKey, k2 = kNoKey;
+    if (P.ntl > 0) {
+        const int64_t m = ql / kRowsQ;
+        const int r = static_cast<int>(ql % kRowsQ);
+        const int64_t g = P.g0 + m;
+        const int64_t ua = P.unit0 + m * P.ntl, ub = ua + P.ntl - 1;
+        const int64_t clo = split_owner(ua, batch.units, batch.grid);
+        const int64_t chi = split_owner(ub, batch.units, batch.grid);
+        for (int64_t c = clo; c <= chi; ++c) {
+            const int64_t us = split_start(c, batch.units, batch.grid);
+            const MatchProblem& F = batch.p[problem_of_unit(batch, us)];
+            const int64_t g_first = F.g0 + (us - F.unit0) / F.ntl;
+            const uint64_t* rec = partials + ((c * batch.smax + (g - g_first)) * kRowsQ + r) * 2;
+            top2_insert_u64(rec[0], k1, k2);
+            top2_insert_u64(rec[1], k1, k2);
+        }
+    }
+    latch_match mres;
+    mres.idx1 = k1 == kNoKey ? -1 : static_cast<int32_t>(k1 & 0xffffffffu);
+    mres.dist1 = k1 == kNoKey ? 0xffff : static_cast<uint16_t>(k1 >> 32);
+    const bool has2 = k == 2 && k2 != kNoKey;
+    mres.idx2 = has2 ? static_cast<int32_t>(k2 & 0xffffffffu) : -1;
+    mres.dist2 = has2 ? static_cast<uint16_t>(k2 >> 32) : 0xffff;
+    if (k1 == kNoKey)
+        mres.accepted = 0;
+    else if (k == 1)
+        mres.accepted = 1;
+    else
+        mres.accepted = (1000ll * mres.dist1 < static_cast<long long>(r_milli) * mres.dist2) ? 1 : 0;
+    mres.pad[0] = mres.pad[1] = mres.pad[2] = 0;
+    out[q] = mres;
 }
 
 // Bits -> E4M3 0/1 bytes (bit t of a descriptor -> byte t) and per-descriptor popcount.
@@ -375,22 +463,9 @@ bool make_map(CUtensorMap* map, const void* base, int64_t rows) {
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-struct TcLayout {
-    size_t exp_q, exp_t, pop_q, pop_t, part, total;
-};
-
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-TcLayout tc_layout(const WorkSplit& s, int64_t nq, int64_t nt) {
-    TcLayout l;
-    l.exp_q = 0;
-    l.exp_t = align_up(l.exp_q + static_cast<size_t>(nq) * kKBytes, 1024);
-    l.pop_q = align_up(l.exp_t + static_cast<size_t>(nt) * kKBytes, 1024);
-    l.pop_t = align_up(l.pop_q + static_cast<size_t>(nq) * 4, 256);
-    l.part = align_up(l.pop_t + static_cast<size_t>(nt) * 4, 256);
-    l.total = align_up(l.part + static_cast<size_t>(s.mt * s.slots * s.rows) * 16, 256);
-    return l;
-}
+}  // namespace
 
 cudaError_t launch_expand(const uint8_t* desc, int64_t n, uint8_t* out, int32_t* pop, cudaStream_t stream) {
     if (n == 0) return cudaSuccess;
@@ -403,40 +478,111 @@ cudaError_t launch_expand(const uint8_t* desc, int64_t n, uint8_t* out, int32_t*
     return cudaGetLastError();
 }
 
-}  // namespace
-
-size_t match_tc_scratch_bytes(const latch_context* ctx, int64_t nq, int64_t nt) {
-    const WorkSplit s = make_split(nq, nt, kRowsQ, kColsB, ctx->sm_count);
-    return tc_layout(s, nq, nt).total;
+// Fills tiles, unit offsets, query-tile prefixes, the block split and the largest
+// number of query tiles one block touches.  problems[i] must have q_row0, t_row0,
+// nq, nt and out0 set.
+void plan_match_batch(MatchBatch* b, int count, int64_t max_grid) {
+    b->count = count;
+    int64_t units = 0, g = 0, queries = 0;
+    for (int i = 0; i < count; ++i) {
+        MatchProblem& P = b->p[i];
+        P.mt = (P.nq + kRowsQ - 1) / kRowsQ;
+        P.ntl = P.nq > 0 ? (P.nt + kColsB - 1) / kColsB : 0;
+        P.unit0 = units;
+        P.g0 = static_cast<int32_t>(g);
+        units += static_cast<int64_t>(P.mt) * P.ntl;
+        g += P.mt;
+        queries = P.out0 + P.nq > queries ? P.out0 + P.nq : queries;
+    }
+    b->units = units;
+    b->queries = queries;
+    b->grid = units < max_grid ? units : max_grid;
+    b->smax = 0;
+    auto tile_of = [b](int64_t u) {
+        int p = 0;
+        while (p + 1 < b->count && b->p[p + 1].unit0 <= u) ++p;
+        return b->p[p].g0 + (u - b->p[p].unit0) / b->p[p].ntl;
+    };
+    for (int64_t c = 0; c < b->grid; ++c) {
+        const int64_t ua = split_start(c, units, b->grid), ub = split_start(c + 1, units, b->grid) - 1;
+        const int64_t segs = tile_of(ub) - tile_of(ua) + 1;
+        if (segs > b->smax) b->smax = segs;
+    }
 }
 
-cudaError_t launch_match_tc(const latch_context* ctx, const uint8_t* q, int32_t nq, const uint8_t* t, int32_t nt,
-                            int32_t k, int32_t r_milli, latch_match* out, void* scratch, cudaStream_t stream) {
+size_t match_tc_batch_scratch_bytes(int64_t rows, const MatchBatch& b) {
+    const size_t exp_bytes = align_up(static_cast<size_t>(rows) * kKBytes, 1024);
+    const size_t pop_bytes = align_up(static_cast<size_t>(rows) * 4, 256);
+    return exp_bytes + pop_bytes + static_cast<size_t>(b.grid * b.smax * kRowsQ) * 16 + 256;
+}
+
+// Scratch: expanded rows (rows x 512 B), popcounts, partial records.  The expanded
+// rows and popcounts must already be filled (launch_expand) when `expanded` is set.
+cudaError_t launch_match_tc_batch(const MatchBatch& b, int64_t rows, void* scratch, int32_t k, int32_t r_milli,
+                                  latch_match* out, uint32_t* flags, cudaStream_t stream) {
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(match_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const WorkSplit s = make_split(nq, nt, kRowsQ, kColsB, ctx->sm_count);
-    const TcLayout l = tc_layout(s, nq, nt);
     uint8_t* base = static_cast<uint8_t*>(scratch);
-    uint64_t* partials = reinterpret_cast<uint64_t*>(base + l.part);
-    if (s.units > 0) {
-        int32_t* pq = reinterpret_cast<int32_t*>(base + l.pop_q);
-        int32_t* pt = reinterpret_cast<int32_t*>(base + l.pop_t);
-        cudaError_t e = launch_expand(q, nq, base + l.exp_q, pq, stream);
-        if (e == cudaSuccess) e = launch_expand(t, nt, base + l.exp_t, pt, stream);
-        if (e != cudaSuccess) return e;
-        CUtensorMap mq, mt;
-        if (!make_map(&mq, base + l.exp_q, nq) || !make_map(&mt, base + l.exp_t, nt)) return cudaErrorInvalidValue;
-        match_tc_kernel<<<static_cast<unsigned>(s.grid), kThreads, kSmemBytes, stream>>>(mq, mt, pq, pt, nq, nt, s,
-                                                                                          partials, ctx->d_flags);
+    const size_t exp_bytes = align_up(static_cast<size_t>(rows) * kKBytes, 1024);
+    const size_t pop_bytes = align_up(static_cast<size_t>(rows) * 4, 256);
+    int32_t* pop = reinterpret_cast<int32_t*>(base + exp_bytes);
+    uint64_t* partials = reinterpret_cast<uint64_t*>(base + exp_bytes + pop_bytes);
+    if (b.units > 0) {
+        CUtensorMap map;
+        if (!make_map(&map, base, rows)) return cudaErrorInvalidValue;
+        match_tc_kernel<<<static_cast<unsigned>(b.grid), kThreads, kSmemBytes, stream>>>(map, b, pop, partials, flags);
         note_launches(1);
-        e = cudaGetLastError();
+        cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    return launch_match_merge(partials, s, nq, k, r_milli, out, stream);
+    if (b.queries == 0) return cudaSuccess;
+    const int threads = 256;
+    const int64_t grid = (b.queries + threads - 1) / threads;
+    match_merge_kernel<<<static_cast<unsigned>(grid), threads, 0, stream>>>(b, partials, k, r_milli, out);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+static void single_problem(MatchBatch* b, int32_t nq, int32_t nt, int64_t sms) {
+    b->p[0].q_row0 = 0;
+    b->p[0].t_row0 = nq;
+    b->p[0].nq = nq;
+    b->p[0].nt = nt;
+    b->p[0].out0 = 0;
+    plan_match_batch(b, 1, sms);
+}
+
+size_t match_tc_scratch_bytes_sms(int64_t sms, int64_t nq, int64_t nt) {
+    MatchBatch* b = new MatchBatch;
+    single_problem(b, static_cast<int32_t>(nq), static_cast<int32_t>(nt), sms);
+    const size_t r = match_tc_batch_scratch_bytes(nq + nt, *b);
+    delete b;
+    return r;
+}
+
+size_t match_tc_scratch_bytes(const latch_context* ctx, int64_t nq, int64_t nt) {
+    return match_tc_scratch_bytes_sms(ctx->sm_count, nq, nt);
+}
+
+cudaError_t launch_match_tc(const latch_context* ctx, const uint8_t* q, int32_t nq, const uint8_t* t, int32_t nt,
+                            int32_t k, int32_t r_milli, latch_match* out, void* scratch, cudaStream_t stream) {
+    MatchBatch* b = new MatchBatch;
+    single_problem(b, nq, nt, ctx->sm_count);
+    uint8_t* base = static_cast<uint8_t*>(scratch);
+    const size_t exp_bytes = align_up(static_cast<size_t>(nq + nt) * kKBytes, 1024);
+    int32_t* pop = reinterpret_cast<int32_t*>(base + exp_bytes);
+    cudaError_t e = cudaSuccess;
+    if (b->units > 0) {
+        e = launch_expand(q, nq, base, pop, stream);
+        if (e == cudaSuccess) e = launch_expand(t, nt, base + static_cast<size_t>(nq) * kKBytes, pop + nq, stream);
+    }
+    if (e == cudaSuccess) e = launch_match_tc_batch(*b, nq + nt, scratch, k, r_milli, out, ctx->d_flags, stream);
+    delete b;
+    return e;
 }
 
 }  // namespace latch
@@ -509,8 +655,7 @@ extern "C" latch_status hamming_match_noalloc(const uint8_t* d_query, int32_t nq
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return fail(nullptr, LATCH_ECUDA, "device query: %s", cudaGetErrorString(e));
-    const WorkSplit s = make_split(nq, nt, kRowsQ, kColsB, sms);
-    const size_t need = tc_layout(s, nq, nt).total + kStaticFlagBytes;
+    const size_t need = match_tc_scratch_bytes_sms(sms, nq, nt) + kStaticFlagBytes;
     if (need > kStaticScratchBytes)
         return fail(nullptr, LATCH_EINVAL,
                     "nq = %d, nt = %d needs %zu bytes of scratch; the static scratch holds %zu (about 30,000 "

@@ -185,3 +185,16 @@ def batch_keypoint_counts(n_images: int = BATCH_IMAGES, lo: int = 5000, hi: int 
     tmp = np.zeros((n_images, 4), dtype=np.int32)
     _load().synth_keypoints(seed(config, 0, KIND_KEYPOINTS) ^ 0x77, hi - lo + 1, 1, n_images, 0, 0, 1, _ptr(tmp))
     return (tmp[:, 0] + lo).astype(np.int32)
+
+
+def sfm_batch(n_images: int = BATCH_IMAGES, width: int = BATCH_W, height: int = BATCH_H,
+              neighbours: int = BATCH_NEIGHBOURS, kmin: int = 5000, kmax: int = 50000, config: int = 3):
+    """The batched structure-from-motion workload: n_images grey images with
+    oriented, scaled keypoints (counts uniform in [kmin, kmax]) and the pair list of
+    every image against its next `neighbours` images."""
+    counts = batch_keypoint_counts(n_images, kmin, kmax, config)
+    imgs = [image(seed(config, i, KIND_IMAGE), width, height) for i in range(n_images)]
+    kps = [keypoints(seed(config, i, KIND_KEYPOINTS), width, height, int(counts[i]), 32, True, 3)
+           for i in range(n_images)]
+    return {"images": imgs, "kps": kps, "pairs": batch_pairs(n_images, neighbours), "width": width,
+            "height": height, "triplets": triplets(), "scales": SCALES}

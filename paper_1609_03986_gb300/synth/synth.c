@@ -120,21 +120,39 @@ int synth_image(uint64_t seed, int width, int height, int64_t pitch, uint8_t *ou
     }
     for (int k = 0; k < 2 * R + 1; ++k) taps[k] /= sum;
 
-    for (int y = 0; y < H; ++y)
+    /* horizontal pass (the same sum in the same tap order inside and near the border) */
+    for (int y = 0; y < H; ++y) {
+        const uint8_t *nr = noise + (size_t)y * W;
+        double *tr = tmp + (size_t)y * W;
         for (int x = 0; x < W; ++x) {
             double acc = 0.0;
-            for (int k = -R; k <= R; ++k) acc += taps[k + R] * noise[(size_t)y * W + reflect101(x + k, W)];
-            tmp[(size_t)y * W + x] = acc;
+            if (x >= R && x < W - R) {
+                for (int k = -R; k <= R; ++k) acc += taps[k + R] * nr[x + k];
+            } else {
+                for (int k = -R; k <= R; ++k) acc += taps[k + R] * nr[reflect101(x + k, W)];
+            }
+            tr[x] = acc;
         }
+    }
+    /* vertical pass, row by row so that the inner loop runs along x */
+    double *acc = (double *)malloc(sizeof(double) * (size_t)W);
+    if (!acc) {
+        free(tmp);
+        free(noise);
+        return -1;
+    }
     for (int y = 0; y < H; ++y) {
         uint8_t *row = out + (size_t)y * (size_t)pitch;
-        for (int x = 0; x < W; ++x) {
-            double acc = 0.0;
-            for (int k = -R; k <= R; ++k) acc += taps[k + R] * tmp[(size_t)reflect101(y + k, H) * W + x];
-            row[x] = round_clamp_u8(acc);
+        for (int x = 0; x < W; ++x) acc[x] = 0.0;
+        for (int k = -R; k <= R; ++k) {
+            const double *src = tmp + (size_t)reflect101(y + k, H) * W;
+            const double t = taps[k + R];
+            for (int x = 0; x < W; ++x) acc[x] += t * src[x];
         }
+        for (int x = 0; x < W; ++x) row[x] = round_clamp_u8(acc[x]);
         for (int64_t x = W; x < pitch; ++x) row[x] = 0;
     }
+    free(acc);
     free(tmp);
     free(noise);
 

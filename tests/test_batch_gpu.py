@@ -1,0 +1,97 @@
+"""Parity of the batched extract-then-match entry point (latch_batch_run) with the
+CPU oracle and with the one-call-per-image / per-pair entry points."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1609_03986_gb300 as P
+from paper_1609_03986_gb300 import synth
+from conftest import to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _run_batch(ctx, imgs, sizes, kps_list, pairs, k=2, ratio=0.8):
+    dev_imgs = [to_dev(im) for im in imgs]
+    n = [len(k_) for k_ in kps_list]
+    allk = np.concatenate([P.pack_keypoints(k_) for k_ in kps_list]) if sum(n) else np.zeros((0, 12), np.uint8)
+    d_kps = to_dev(allk) if sum(n) else torch.zeros((1, 12), dtype=torch.uint8, device="cuda")
+    d_desc = torch.zeros((max(1, sum(n)), 64), dtype=torch.uint8, device="cuda")
+    nout = sum(n[q] for q, _ in pairs)
+    d_m = torch.zeros((max(1, nout), 16), dtype=torch.uint8, device="cuda")
+    images = [(t, w, h, t.stride(0)) for t, (w, h) in zip(dev_imgs, sizes)]
+    b = P.BatchDesc(images, n, d_kps, d_desc, pairs, k, ratio, d_m)
+    P.latch_batch_run(ctx.handle, b, int(torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    ctx.check()
+    off = np.concatenate([[0], np.cumsum(n)]).astype(np.int64)
+    descs = [d_desc[off[i]:off[i + 1]].cpu().numpy() for i in range(len(imgs))]
+    mo = b.match_offsets()
+    recs = P.matches_from_bytes(d_m.cpu().numpy())
+    matches = [recs[mo[p]:mo[p + 1]] for p in range(len(pairs))]
+    return descs, matches
+
+
+def _same(got, want):
+    for f in ("idx1", "idx2", "dist1", "dist2", "accepted"):
+        assert np.array_equal(got[f].astype(np.int64), np.asarray(want[f]).astype(np.int64)), f
+
+
+def test_small_mixed_batch(gpu_ctx, triplets):
+    """Images of different sizes and pitches, empty and tiny keypoint sets,
+    keypoints near and beyond borders, self pairs and pairs with an empty side."""
+    sizes = [(320, 240), (641, 480), (200, 150), (1000, 700), (48, 48), (333, 333)]
+    counts = [300, 1000, 0, 2500, 7, 800]
+    imgs, kps = [], []
+    for i, ((w, h), c) in enumerate(zip(sizes, counts)):
+        imgs.append(synth.image(synth.seed(31, i, synth.KIND_IMAGE), w, h, n_ellipses=30))
+        k = synth.keypoints(synth.seed(31, i, synth.KIND_KEYPOINTS), w + 40, h + 40, c, 0, True, 3)
+        k[:, 0] -= 20
+        k[:, 1] -= 20
+        kps.append(k)
+    pairs = [(0, 1), (1, 0), (0, 0), (2, 3), (3, 2), (3, 5), (4, 4), (5, 1), (1, 3), (4, 2)]
+    descs, matches = _run_batch(gpu_ctx, imgs, sizes, kps, pairs)
+    for i in range(len(imgs)):
+        want = oracle.extract(imgs[i], sizes[i][0], sizes[i][1], kps[i], triplets, synth.SCALES)
+        assert np.array_equal(descs[i], want), i
+    for p, (q, t) in enumerate(pairs):
+        if counts[q] == 0:
+            assert len(matches[p]) == 0
+            continue
+        _same(matches[p], oracle.match(descs[q], descs[t], 2, 0.8))
+
+
+def test_batch_equals_single_calls(gpu_ctx, triplets):
+    """Same bytes as latch_extract per image and hamming_match per pair, for k = 1."""
+    sizes = [(400, 300)] * 4
+    imgs = [synth.image(synth.seed(32, i, synth.KIND_IMAGE), 400, 300, n_ellipses=20) for i in range(4)]
+    kps = [synth.keypoints(synth.seed(32, i, synth.KIND_KEYPOINTS), 400, 300, 1500 + 97 * i, 32, True, 3)
+           for i in range(4)]
+    pairs = [(0, 1), (1, 2), (2, 3), (3, 0)]
+    descs, matches = _run_batch(gpu_ctx, imgs, sizes, kps, pairs, k=1, ratio=0.7)
+    single = [gpu_ctx.extract(to_dev(im), 400, 300, to_dev(P.pack_keypoints(k))) for im, k in zip(imgs, kps)]
+    for i in range(4):
+        assert np.array_equal(descs[i], single[i].cpu().numpy())
+    for p, (q, t) in enumerate(pairs):
+        one = P.matches_from_bytes(gpu_ctx.match(single[q], single[t], 1, 0.7, P.PATH_TENSOR).cpu().numpy())
+        _same(matches[p], one)
+
+
+def test_sfm_batch_full_size_sampled(gpu_ctx, triplets):
+    """The full batched workload (64 images of 4000x3000, 5k-50k oriented and scaled
+    keypoints each, 476 neighbour pairs) in one latch_batch_run: 64 sampled
+    descriptors per image against the oracle, and 3 sampled query rows of 40 pairs
+    matched by the oracle against the whole train image."""
+    wl = synth.sfm_batch()
+    sizes = [(wl["width"], wl["height"])] * len(wl["images"])
+    descs, matches = _run_batch(gpu_ctx, wl["images"], sizes, wl["kps"], wl["pairs"])
+    rng = np.random.default_rng(7)
+    for i in range(len(wl["images"])):
+        sel = rng.choice(len(wl["kps"][i]), 64, replace=False)
+        want = oracle.extract(wl["images"][i], wl["width"], wl["height"], wl["kps"][i][sel], triplets, synth.SCALES)
+        assert np.array_equal(descs[i][sel], want), i
+    for p in rng.choice(len(wl["pairs"]), 40, replace=False):
+        q, t = wl["pairs"][p]
+        rows = rng.choice(len(wl["kps"][q]), 3, replace=False)
+        _same(matches[p][rows], oracle.match(descs[q][rows], descs[t], 2, 0.8))

@@ -38,6 +38,9 @@ def _args():
     p.add_argument("--impl", default="latch", choices=["latch", "reference"])
     p.add_argument("--path", default="auto", choices=["auto", "popc", "tensor"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", default="pair", choices=["pair", "gallery", "sfm_batch"],
+                   help="pair: the default one-pair step; gallery: 16,384 x 1,048,576 matching; "
+                        "sfm_batch: 64 images x 476 neighbour pairs, batched vs one call per image / pair")
     return p.parse_args()
 
 
@@ -323,10 +326,118 @@ def run_latch(args):
     return 0
 
 
+def _timed(fn, steps, warmup, flush=None):
+    """CUDA-event time (ms) per call of fn on the current stream, L2 flushed between calls."""
+    import torch
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        if flush is not None:
+            flush.zero_()
+        fn()
+    torch.cuda.synchronize()
+    tot = 0.0
+    for _ in range(steps):
+        if flush is not None:
+            flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        tot += a.elapsed_time(b)
+    return tot / steps
+
+
+def run_gallery(args):
+    """16,384 queries against 1,048,576 gallery descriptors, top-2 ratio 0.8."""
+    import torch
+    import paper_1609_03986_gb300 as P
+    from paper_1609_03986_gb300 import synth
+    torch.cuda.set_device(0)
+    q, g, slots, hs = synth.gallery_workload()
+    dq, dg = torch.from_numpy(q).cuda(), torch.from_numpy(g).cuda()
+    out = torch.empty((q.shape[0], 16), dtype=torch.uint8, device="cuda")
+    ctx = P.Context(0)
+    s = int(torch.cuda.current_stream().cuda_stream)
+    res = {}
+    for name, path in (("tensor", P.PATH_TENSOR), ("popc", P.PATH_POPC)):
+        if args.path != "auto" and args.path != name:
+            continue
+        fn = lambda: P.hamming_match(ctx.handle, dq, q.shape[0], dg, g.shape[0], 2, 0.8, out, path, s)
+        ms = _timed(fn, args.steps, args.warmup)
+        got = P.matches_from_bytes(out.cpu().numpy())
+        ok = bool((got["idx1"] == slots).all() and (got["dist1"].astype(np.int32) == hs).all())
+        res[name] = {"ms": ms, "gpairs_per_s": q.shape[0] * g.shape[0] / (ms / 1e3) / 1e9, "planted_ok": ok}
+    ctx.close()
+    print(json.dumps({"metric": METRIC, "workload": "gallery_16384x1048576", "unit": "Gpairs/s", "paths": res,
+                      "steps": args.steps, "warmup": args.warmup}))
+    return 0
+
+
+def run_sfm_batch(args):
+    """64 images of 4000x3000 (5k-50k keypoints) x 476 neighbour pairs: the batched
+    entry point (captured in a CUDA graph) against one call per image and per pair."""
+    import torch
+    import paper_1609_03986_gb300 as P
+    from paper_1609_03986_gb300 import synth
+    torch.cuda.set_device(0)
+    wl = synth.sfm_batch()
+    w, h = wl["width"], wl["height"]
+    n = [len(k) for k in wl["kps"]]
+    ctx = P.Context(0, triplets=wl["triplets"])
+    imgs = [torch.from_numpy(im).cuda() for im in wl["images"]]
+    d_kps = torch.from_numpy(np.concatenate([P.pack_keypoints(k) for k in wl["kps"]])).cuda()
+    d_desc = torch.zeros((sum(n), 64), dtype=torch.uint8, device="cuda")
+    pairs = wl["pairs"]
+    nout = sum(n[a] for a, _ in pairs)
+    d_m = torch.zeros((nout, 16), dtype=torch.uint8, device="cuda")
+    b = P.BatchDesc([(t, w, h, t.stride(0)) for t in imgs], n, d_kps, d_desc, pairs, 2, 0.8, d_m)
+    P.latch_reserve_batch(ctx.handle, b)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = int(stream.cuda_stream)
+        P.latch_batch_run(ctx.handle, b, s)  # warm-up outside capture
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            P.latch_batch_run(ctx.handle, b, int(torch.cuda.current_stream().cuda_stream))
+        batched_ms = _timed(lambda: graph.replay(), args.steps, args.warmup)
+        batched_ref = d_m.clone()
+        # plain form: one latch_extract per image, one hamming_match per pair
+        off = np.concatenate([[0], np.cumsum(n)])
+        mo = b.match_offsets()
+        P.latch_reserve(ctx.handle, max(n), max(n), max(n))
+
+        def plain():
+            for i in range(len(imgs)):
+                P.latch_extract(ctx.handle, imgs[i], w, h, imgs[i].stride(0), d_kps[off[i]:off[i + 1]], n[i], None,
+                                d_desc[off[i]:off[i + 1]], s)
+            for p, (qi, ti) in enumerate(pairs):
+                P.hamming_match(ctx.handle, d_desc[off[qi]:off[qi + 1]], n[qi], d_desc[off[ti]:off[ti + 1]], n[ti],
+                                2, 0.8, d_m[mo[p]:mo[p + 1]], P.PATH_TENSOR, s)
+        plain_ms = _timed(plain, max(1, args.steps // 4), 1)
+    same = bool(torch.equal(batched_ref, d_m))
+    ctx.check()
+    pairs_total = sum(n[a] * n[c] for a, c in pairs)
+    print(json.dumps({"metric": METRIC, "workload": "sfm_batch_64x4000x3000_476pairs", "unit": "descriptors/s",
+                      "batched": {"ms": batched_ms, "desc_per_s": sum(n) / (batched_ms / 1e3),
+                                  "gpairs_per_s": pairs_total / (batched_ms / 1e3) / 1e9},
+                      "plain": {"ms": plain_ms, "desc_per_s": sum(n) / (plain_ms / 1e3),
+                                "gpairs_per_s": pairs_total / (plain_ms / 1e3) / 1e9},
+                      "identical_results": same, "descriptors": sum(n), "pairs": pairs_total,
+                      "steps": args.steps, "warmup": args.warmup}))
+    return 0
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "gallery":
+        return run_gallery(args)
+    if args.workload == "sfm_batch":
+        return run_sfm_batch(args)
     return run_latch(args)
 
 

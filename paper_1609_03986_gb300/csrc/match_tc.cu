@@ -13,13 +13,14 @@
 // range per block (one block per SM, persistent):
 //   warp 0     TMA producer: the query tile (two 128-row A operands, 128 KB) stays
 //              resident while consecutive units share it; train chunks (128 rows x
-//              128 bytes) go through a 4-stage ring, 128-byte swizzle;
+//              128 bytes) go through a 5-stage ring, 128-byte swizzle;
 //   warp 1     MMA issuer: per unit 2 x 16 tcgen05.mma (M=128, N=128, K=32) into one
 //              of two double-buffered TMEM accumulators;
 //   warp 2     TMEM allocator (all 512 columns);
-//   warps 4-7  epilogue: tcgen05.ld of the fp32 dot products, key =
+//   warps 4-11 epilogue (one query row per thread): double-buffered tcgen05.ld of
+//              the fp32 dot products, key =
 //              ((popc(t) - 2*dot + 512) << 8 | column) formed exactly in fp32 by
-//              one FMA, running min / second-min with FMNMX; the tile's two best are
+//              one FMA, four interleaved min / second-min chains with FMNMX; the tile's two best are
 //              merged into the row's (distance << 32 | index) keys, and when the
 //              block leaves a query tile the row's two keys go to a partial record.
 // match_merge_kernel combines the partial records of every query row (ties to the
@@ -45,19 +46,20 @@ constexpr int kColsB = 128;             // train rows per unit (N)
 constexpr int kKBytes = 512;            // expanded descriptor: 512 x 8-bit
 constexpr int kChunk = 128;             // K bytes per swizzle atom / TMA box
 constexpr int kChunks = kKBytes / kChunk;
-constexpr int kStages = 4;
+constexpr int kStages = 5;
 constexpr int kTileBytes = kRowsA * kChunk;  // 16 KB
-constexpr int kThreads = 256;
+constexpr int kThreads = 384;   // 12 warps: producer, MMA, TMEM, idle, 8 epilogue
+constexpr int kEpiThreads = 256;
 constexpr int kTmemCols = 512;
 constexpr uint32_t kIdesc = idesc_e4m3_f32(kRowsA, kColsB);
 
-// AND of `v` over the 128 epilogue threads (named barrier 1).
+// AND of `v` over the 256 epilogue threads (named barrier 1).
 __device__ __forceinline__ bool group_all(bool v) {
     uint32_t r;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\t"
         "setp.ne.u32 q, %1, 0;\n\t"
-        "bar.red.and.pred p, 1, 128, q;\n\t"
+        "bar.red.and.pred p, 1, 256, q;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(r)
         : "r"(static_cast<uint32_t>(v))
@@ -121,7 +123,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
         mbar_init(a_empty, 1);
         for (int i = 0; i < 2; ++i) {
             mbar_init(&acc_full[i], 1);
-            mbar_init(&acc_empty[i], 4);
+            mbar_init(&acc_empty[i], kEpiThreads / 32);
         }
         mbar_init(mma_done, 1);
         *abort = 0;
@@ -255,13 +257,15 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
             }
         }
     } else if (warp >= 4) {
-        // ---------------- epilogue ----------------
-        const int et = threadIdx.x - 128;  // 0..127: TMEM lane / column index
-        const int quarter = warp & 3;
+        // ---------------- epilogue: 8 warps, thread = one query row ----------------
+        const int et = threadIdx.x - 128;  // 0..255
+        const int quarter = warp & 3;      // TMEM lane quarter this warp may access
+        const int a = (warp - 4) >> 2;     // A operand (query sub-tile) of this warp
+        const int row_in_tile = a * kRowsA + quarter * 32 + lane;
         UnitCursor cur;
         uint32_t acc_par[2] = {0, 0};
-        uint64_t k1[kSubA], k2[kSubA];
-        int32_t pq[kSubA];
+        uint64_t k1 = kNoKey, k2 = kNoKey;
+        int32_t pq = 0;
         int64_t prev_g = -1, g_first = -1;
         int i = 0;
         for (int64_t u = u0; u < u1; ++u, ++i) {
@@ -271,64 +275,72 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
             const int64_t g = P.g0 + m;
             const int buf = i & 1;
             if (g != prev_g) {
-#pragma unroll
-                for (int a = 0; a < kSubA; ++a) {
-                    const int64_t row = m * kRowsQ + a * kRowsA + quarter * 32 + lane;
-                    pq[a] = row < P.nq ? pop[P.q_row0 + row] : 0;
-                    k1[a] = k2[a] = kNoKey;
-                }
+                const int64_t row = m * kRowsQ + row_in_tile;
+                pq = row < P.nq ? pop[P.q_row0 + row] : 0;
+                k1 = k2 = kNoKey;
                 if (g_first < 0) g_first = g;
                 prev_g = g;
             }
-            {
+            if (et < kColsB) {
                 const int64_t col = n * kColsB + et;
                 sC[buf * kColsB + et] = col < P.nt ? static_cast<float>((pop[P.t_row0 + col] + 512) * 256 + et)
                                                    : __int_as_float(0x7f800000);
             }
-            // one vote of the 128 epilogue threads: also publishes sC; exits are group-uniform
+            // one vote of the 256 epilogue threads: also publishes sC; exits are group-uniform
             if (!group_all(mbar_wait(&acc_full[buf], acc_par[buf], abort))) break;
             acc_par[buf] ^= 1;
             tc_fence_after();
             const float* cv = sC + buf * kColsB;
+            const uint32_t base =
+                tmem + (static_cast<uint32_t>(quarter * 32) << 16) + static_cast<uint32_t>((a * 2 + buf) * kColsB);
+            // four independent min / second-min chains over the 128 columns
+            float m1[4], m2[4];
 #pragma unroll
-            for (int a = 0; a < kSubA; ++a) {
-                float m1 = __int_as_float(0x7f800000), m2 = m1;
-                const uint32_t base = tmem + (static_cast<uint32_t>(quarter * 32) << 16) +
-                                      static_cast<uint32_t>((a * 2 + buf) * kColsB);
-#pragma unroll 1
-                for (int ch = 0; ch < kColsB / 32; ++ch) {
-                    uint32_t v[32];
-                    tmem_ld_32x32b_x32(base + ch * 32, v);
-                    tmem_ld_wait();
+            for (int c = 0; c < 4; ++c) m1[c] = m2[c] = __int_as_float(0x7f800000);
+            uint32_t va[32], vb[32];
+            tmem_ld_32x32b_x32(base, va);
+            tmem_ld_wait();
 #pragma unroll
-                    for (int j = 0; j < 32; j += 4) {
-                        const float4 cc = *reinterpret_cast<const float4*>(cv + ch * 32 + j);
-                        const float e0 = fmaf(__uint_as_float(v[j + 0]), -512.0f, cc.x);
-                        const float e1 = fmaf(__uint_as_float(v[j + 1]), -512.0f, cc.y);
-                        const float e2 = fmaf(__uint_as_float(v[j + 2]), -512.0f, cc.z);
-                        const float e3 = fmaf(__uint_as_float(v[j + 3]), -512.0f, cc.w);
-                        float h;
-                        h = fmaxf(m1, e0); m1 = fminf(m1, e0); m2 = fminf(m2, h);
-                        h = fmaxf(m1, e1); m1 = fminf(m1, e1); m2 = fminf(m2, h);
-                        h = fmaxf(m1, e2); m1 = fminf(m1, e2); m2 = fminf(m2, h);
-                        h = fmaxf(m1, e3); m1 = fminf(m1, e3); m2 = fminf(m2, h);
+            for (int ch = 0; ch < kColsB / 32; ++ch) {
+                uint32_t* cur_v = (ch & 1) ? vb : va;
+                if (ch + 1 < kColsB / 32) tmem_ld_32x32b_x32(base + (ch + 1) * 32, (ch & 1) ? va : vb);
+#pragma unroll
+                for (int j = 0; j < 32; j += 4) {
+                    const float4 cc = *reinterpret_cast<const float4*>(cv + ch * 32 + j);
+                    const float e[4] = {fmaf(__uint_as_float(cur_v[j + 0]), -512.0f, cc.x),
+                                        fmaf(__uint_as_float(cur_v[j + 1]), -512.0f, cc.y),
+                                        fmaf(__uint_as_float(cur_v[j + 2]), -512.0f, cc.z),
+                                        fmaf(__uint_as_float(cur_v[j + 3]), -512.0f, cc.w)};
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const float h = fmaxf(m1[c], e[c]);
+                        m1[c] = fminf(m1[c], e[c]);
+                        m2[c] = fminf(m2[c], h);
                     }
                 }
-                // the tile's two best (exact integers below 2^19) -> global keys
+                if (ch + 1 < kColsB / 32) tmem_ld_wait();
+            }
+            // combine the chains (keys are unique): (a1,a2) + (b1,b2) -> (min, second min)
 #pragma unroll
-                for (int b = 0; b < 2; ++b) {
-                    const float mk = b == 0 ? m1 : m2;
-                    if (mk < 1.0e30f) {
-                        const uint32_t kk = static_cast<uint32_t>(mk);
-                        const int32_t d = pq[a] + static_cast<int32_t>(kk >> 8) - 512;
-                        const uint64_t idx = static_cast<uint64_t>(n * kColsB + (kk & 255u));
-                        top2_insert_u64((static_cast<uint64_t>(d) << 32) | idx, k1[a], k2[a]);
-                    }
-                }
+            for (int c = 1; c < 4; ++c) {
+                const float lo = fminf(m1[0], m1[c]), hi = fmaxf(m1[0], m1[c]);
+                m2[0] = fminf(hi, fminf(m2[0], m2[c]));
+                m1[0] = lo;
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[buf]);
+            // the tile's two best (exact integers below 2^19) -> (distance << 32 | index) keys
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const float mk = b == 0 ? m1[0] : m2[0];
+                if (mk < 1.0e30f) {
+                    const uint32_t kk = static_cast<uint32_t>(mk);
+                    const int32_t d = pq + static_cast<int32_t>(kk >> 8) - 512;
+                    const uint64_t idx = static_cast<uint64_t>(n * kColsB + (kk & 255u));
+                    top2_insert_u64((static_cast<uint64_t>(d) << 32) | idx, k1, k2);
+                }
+            }
             bool last_of_tile = (u + 1 >= u1);
             if (!last_of_tile) {
                 UnitCursor nx = cur;
@@ -337,13 +349,9 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                 last_of_tile = (Q.g0 + (u + 1 - Q.unit0) / Q.ntl) != g;
             }
             if (last_of_tile) {
-                uint64_t* rec = partials + ((c * batch.smax + (g - g_first)) * kRowsQ) * 2;
-#pragma unroll
-                for (int a = 0; a < kSubA; ++a) {
-                    const int r = a * kRowsA + quarter * 32 + lane;
-                    rec[2 * r] = k1[a];
-                    rec[2 * r + 1] = k2[a];
-                }
+                uint64_t* rec = partials + ((c * batch.smax + (g - g_first)) * kRowsQ + row_in_tile) * 2;
+                rec[0] = k1;
+                rec[1] = k2;
             }
         }
     }

@@ -38,7 +38,9 @@ def _args():
     p.add_argument("--impl", default="latch", choices=["latch", "reference"])
     p.add_argument("--path", default="auto", choices=["auto", "popc", "tensor"])
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="pair", choices=["pair", "gallery", "sfm_batch"],
+    p.add_argument("--rate", type=float, default=200.0, help="serve: Poisson arrivals per second")
+    p.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
+    p.add_argument("--workload", default="pair", choices=["pair", "gallery", "sfm_batch", "serve"],
                    help="pair: the default one-pair step; gallery: 16,384 x 1,048,576 matching; "
                         "sfm_batch: 64 images x 476 neighbour pairs, batched vs one call per image / pair")
     return p.parse_args()
@@ -430,8 +432,80 @@ def run_sfm_batch(args):
     return 0
 
 
+def run_serve(args):
+    """Poisson stream of extract-and-match requests (images from 640x480 to
+    4000x3000, 1k-64k oriented keypoints) against 32 resident galleries of 10k-200k
+    descriptors, through the session API (continuous batching)."""
+    import threading
+    import queue as _q
+    import torch
+    import paper_1609_03986_gb300 as P
+    from paper_1609_03986_gb300 import synth
+    torch.cuda.set_device(0)
+    sizes = [(640, 480), (1280, 720), (1920, 1080), (2560, 1440), (4000, 3000)]
+    per_size = 4
+    pool = {}
+    for si, (w, h) in enumerate(sizes):
+        for j in range(per_size):
+            im = P.pinned_copy(synth.image(synth.seed(5, si * per_size + j, synth.KIND_IMAGE), w, h))
+            kp = synth.keypoints(synth.seed(5, si * per_size + j, synth.KIND_KEYPOINTS), w, h, 64000, 32, True, 3)
+            pool[(si, j)] = (im, w, h, P.pinned_copy(P.pack_keypoints(kp)))
+    gal_n = synth.batch_keypoint_counts(32, 10000, 200000, config=5)
+    gals = [synth.random_descriptors(synth.seed(5, 1000 + g, synth.KIND_GALLERY), int(n)) for g, n in enumerate(gal_n)]
+    t_arr, size_i, kps_n, gal_i = synth.arrivals(synth.seed(5, 0, synth.KIND_ARRIVALS), args.rate, args.duration,
+                                                 len(sizes), 1000, 64000, 32)
+    sess = P.Session(synth.triplets(), hbm_budget=12 << 30, max_gallery_rows=int(gal_n.sum()) + 1, max_batch=16,
+                     max_batch_kps=1 << 18)
+    for g in gals:
+        sess.add_gallery(g)
+    # warm-up
+    for i in range(8):
+        im, w, h, kp = pool[(i % len(sizes), 0)]
+        sess.wait(sess.submit(im, w, h, kp[:4000], i % 32))
+    tickets = _q.Queue()
+    n_req = len(t_arr)
+
+    def submitter():
+        t0 = time.perf_counter()
+        for i in range(n_req):
+            dt = t_arr[i] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            im, w, h, kp = pool[(int(size_i[i]), i % per_size)]
+            tickets.put((sess.submit(im, w, h, kp[:int(kps_n[i])], int(gal_i[i])), int(kps_n[i])))
+
+    th = threading.Thread(target=submitter)
+    wall0 = time.perf_counter()
+    th.start()
+    lat, first, last, ndesc, bsz = [], None, None, 0, []
+    for _ in range(n_req):
+        t, n = tickets.get()
+        r, m, _ = sess.wait(t)
+        lat.append((r.done_s - r.submit_s) * 1e3)
+        first = r.submit_s if first is None else min(first, r.submit_s)
+        last = r.done_s if last is None else max(last, r.done_s)
+        ndesc += n
+        bsz.append(r.batch_size)
+    th.join()
+    wall = time.perf_counter() - wall0
+    st = sess.stats()
+    sess.close()
+    lat = np.array(lat)
+    pairs = float(sum(int(kps_n[i]) * int(gal_n[gal_i[i]]) for i in range(n_req)))
+    print(json.dumps({"metric": METRIC, "workload": f"serve_poisson_{args.rate:g}rps_{args.duration:g}s",
+                      "requests": n_req, "offered_rps": args.rate,
+                      "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                                     "max": float(lat.max()), "mean": float(lat.mean())},
+                      "sustained_desc_per_s": ndesc / (last - first), "sustained_gpairs_per_s": pairs / (last - first) / 1e9,
+                      "achieved_rps": n_req / (last - first), "mean_batch": float(np.mean(bsz)),
+                      "max_batch": int(np.max(bsz)), "wall_s": wall, "stats": st}))
+    return 0
+
+
 def main():
     args = _args()
+    if args.workload == "serve":
+        return run_serve(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "gallery":

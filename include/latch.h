@@ -192,6 +192,64 @@ latch_status latch_reserve_batch(latch_context *ctx, const latch_batch_desc *bat
  * identical to calling latch_extract and hamming_match one by one. */
 latch_status latch_batch_run(latch_context *ctx, const latch_batch_desc *batch, latch_stream_t stream);
 
+/* ---- Serving session: extract-and-match requests against resident galleries ----
+ *
+ * A session owns a context, an HBM budget and a host scheduler thread.  Galleries
+ * (descriptor sets) are copied in once and stay on the device, pre-expanded for
+ * the tensor-core matcher.  Requests are queued by latch_submit and run with
+ * continuous batching: whenever one of the session's two lanes is free, the
+ * requests at the head of the queue that fit the lane (count, keypoints and the
+ * lane's share of the HBM budget) are admitted together and run as one batched
+ * extraction and one batched match; the two lanes run concurrently on their own
+ * streams.  Each result is bit-identical to latch_extract + hamming_match on that
+ * request alone.  All session calls are thread-safe. */
+typedef struct latch_session latch_session;
+
+typedef struct {
+    const uint8_t *h_image;          /* host image, row pitch `pitch` bytes (any pitch >= width) */
+    int32_t width, height;
+    int64_t pitch;
+    const latch_keypoint *h_kps;     /* host keypoints */
+    int32_t n;
+    int32_t gallery_id;              /* from latch_gallery_add */
+    int32_t k;                       /* 1 or 2 */
+    float ratio;                     /* in [0, 1] */
+    latch_match *h_matches;          /* host out: n records */
+    uint8_t *h_desc;                 /* host out: n * 64 bytes, or NULL */
+} latch_request;                     /* all host buffers must stay valid until latch_wait returns */
+
+typedef struct {
+    latch_status status;
+    int32_t n;
+    int32_t batch_size;              /* requests in the micro-batch this one ran in */
+    double submit_s, start_s, done_s;  /* seconds on the session clock: queued, admitted, completed */
+} latch_result;
+
+typedef struct {
+    int64_t submitted, completed, rejected, failed, batches, max_queue, queued, lane_bytes;
+} latch_session_stats;
+
+/* hbm_budget: device bytes the session may hold (arena of max_gallery_rows +
+ * 2 x max_batch_kps expanded rows, the rest split between the two lanes; each lane
+ * needs at least 64 MB).  max_batch: requests per micro-batch (1..64);
+ * max_batch_kps: keypoints per micro-batch; h_triplets: the 512-triplet table. */
+latch_status latch_session_create(int device, size_t hbm_budget, int64_t max_gallery_rows, int32_t max_batch,
+                                  int64_t max_batch_kps, const latch_triplet *h_triplets, latch_session **out);
+/* Stops the scheduler, waits for work in flight, frees everything. */
+latch_status latch_session_destroy(latch_session *s);
+/* Copy n packed descriptors (host) into a new resident gallery (synchronous). */
+latch_status latch_gallery_add(latch_session *s, const uint8_t *h_desc, int32_t n, int32_t *gallery_id);
+/* Queue a request; LATCH_ENOMEM if it can never fit a lane, LATCH_EINVAL on bad
+ * arguments or an unknown gallery.  Returns at once. */
+latch_status latch_submit(latch_session *s, const latch_request *req, uint64_t *ticket);
+/* Wait for a ticket (timeout_ms < 0: forever); LATCH_ETIMEOUT if still running.
+ * On completion the request's host outputs are filled. */
+latch_status latch_wait(latch_session *s, uint64_t ticket, int32_t timeout_ms, latch_result *out);
+/* Forget a completed ticket. */
+latch_status latch_release(latch_session *s, uint64_t ticket);
+latch_status latch_session_get_stats(latch_session *s, latch_session_stats *out);
+const char *latch_session_last_error(const latch_session *s);
+
 /* The path LATCH_PATH_AUTO takes for nq x nt on this context (LATCH_PATH_POPC or
  * LATCH_PATH_TENSOR); -1 on a NULL context. */
 int32_t hamming_match_path(const latch_context *ctx, int64_t nq, int64_t nt);

@@ -52,6 +52,23 @@ class latch_batch_desc(ctypes.Structure):
                 ("d_matches", ctypes.c_void_p)]
 
 
+class latch_request(ctypes.Structure):
+    _fields_ = [("h_image", ctypes.c_void_p), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("pitch", ctypes.c_int64), ("h_kps", ctypes.c_void_p), ("n", ctypes.c_int32),
+                ("gallery_id", ctypes.c_int32), ("k", ctypes.c_int32), ("ratio", ctypes.c_float),
+                ("h_matches", ctypes.c_void_p), ("h_desc", ctypes.c_void_p)]
+
+
+class latch_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("n", ctypes.c_int32), ("batch_size", ctypes.c_int32),
+                ("submit_s", ctypes.c_double), ("start_s", ctypes.c_double), ("done_s", ctypes.c_double)]
+
+
+class latch_session_stats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in ("submitted", "completed", "rejected", "failed", "batches", "max_queue",
+                                             "queued", "lane_bytes")]
+
+
 _lib = None
 
 # (name, restype, argtypes) of every exported entry point
@@ -71,6 +88,15 @@ EXPORTS = [
     ("hamming_match_path", ctypes.c_int32, [_P, _I64, _I64]),
     ("latch_reserve_batch", ctypes.c_int, [_P, ctypes.POINTER(latch_batch_desc)]),
     ("latch_batch_run", ctypes.c_int, [_P, ctypes.POINTER(latch_batch_desc), _P]),
+    ("latch_session_create", ctypes.c_int, [ctypes.c_int, ctypes.c_size_t, _I64, _I32, _I64, _P,
+                                            ctypes.POINTER(_P)]),
+    ("latch_session_destroy", ctypes.c_int, [_P]),
+    ("latch_gallery_add", ctypes.c_int, [_P, _P, _I32, ctypes.POINTER(_I32)]),
+    ("latch_submit", ctypes.c_int, [_P, ctypes.POINTER(latch_request), ctypes.POINTER(ctypes.c_uint64)]),
+    ("latch_wait", ctypes.c_int, [_P, ctypes.c_uint64, _I32, ctypes.POINTER(latch_result)]),
+    ("latch_release", ctypes.c_int, [_P, ctypes.c_uint64]),
+    ("latch_session_get_stats", ctypes.c_int, [_P, ctypes.POINTER(latch_session_stats)]),
+    ("latch_session_last_error", ctypes.c_char_p, [_P]),
     ("hamming_match_noalloc", ctypes.c_int, [_P, _I32, _P, _I32, _I32, _F, _P, _P]),
 ]
 
@@ -199,6 +225,127 @@ def latch_reserve_batch(ctx, batch: BatchDesc) -> None:
 
 def latch_batch_run(ctx, batch: BatchDesc, stream: int = 0) -> None:
     _check(ctx, library().latch_batch_run(ctx, ctypes.byref(batch.desc), stream))
+
+
+def _scheck(sess, status: int):
+    if status != 0:
+        msg = library().latch_session_last_error(sess)
+        raise LatchError(status, msg.decode() if msg else "")
+
+
+def latch_session_create(device: int, hbm_budget: int, max_gallery_rows: int, max_batch: int, max_batch_kps: int,
+                         triplets):
+    t = np.ascontiguousarray(triplets, dtype=np.uint8).reshape(-1)
+    h = ctypes.c_void_p()
+    st = library().latch_session_create(device, hbm_budget, max_gallery_rows, max_batch, max_batch_kps,
+                                        t.ctypes.data, ctypes.byref(h))
+    if st != 0:
+        raise LatchError(st, "latch_session_create failed")
+    return h
+
+
+def latch_session_destroy(sess) -> None:
+    library().latch_session_destroy(sess)
+
+
+def latch_gallery_add(sess, h_desc, n: int) -> int:
+    gid = ctypes.c_int32()
+    _scheck(sess, library().latch_gallery_add(sess, _ptr(h_desc), n, ctypes.byref(gid)))
+    return gid.value
+
+
+def latch_submit(sess, req: latch_request) -> int:
+    t = ctypes.c_uint64()
+    _scheck(sess, library().latch_submit(sess, ctypes.byref(req), ctypes.byref(t)))
+    return t.value
+
+
+def latch_wait(sess, ticket: int, timeout_ms: int = -1) -> latch_result:
+    r = latch_result()
+    _scheck(sess, library().latch_wait(sess, ticket, timeout_ms, ctypes.byref(r)))
+    return r
+
+
+def latch_release(sess, ticket: int) -> None:
+    _scheck(sess, library().latch_release(sess, ticket))
+
+
+def latch_session_get_stats(sess) -> dict:
+    st = latch_session_stats()
+    _scheck(sess, library().latch_session_get_stats(sess, ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in latch_session_stats._fields_}
+
+
+def latch_session_last_error(sess) -> str:
+    m = library().latch_session_last_error(sess)
+    return m.decode() if m else ""
+
+
+def _host_buffer(shape):
+    """Page-locked host array (so the session's device-to-host copies stay
+    asynchronous); plain numpy memory when torch/CUDA is not available."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.empty(shape, dtype=torch.uint8, pin_memory=True).numpy()
+    except Exception:
+        pass
+    return np.empty(shape, np.uint8)
+
+
+def pinned_copy(a: np.ndarray) -> np.ndarray:
+    """Page-locked copy of a host array (inputs that the session copies asynchronously)."""
+    b = _host_buffer(a.shape) if a.dtype == np.uint8 else np.array(a)
+    b[...] = a
+    return b
+
+
+class Session:
+    """Owner of a latch_session; requests take numpy host arrays (pinned ones keep
+    the session's host<->device copies fully asynchronous)."""
+
+    def __init__(self, triplets, device: int = 0, hbm_budget: int = 8 << 30, max_gallery_rows: int = 1 << 22,
+                 max_batch: int = 16, max_batch_kps: int = 1 << 18):
+        self.handle = latch_session_create(device, hbm_budget, max_gallery_rows, max_batch, max_batch_kps, triplets)
+        self._live = {}
+
+    def close(self):
+        if self.handle is not None:
+            latch_session_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_gallery(self, desc: np.ndarray) -> int:
+        desc = np.ascontiguousarray(desc, dtype=np.uint8).reshape(-1, DESC_BYTES)
+        return latch_gallery_add(self.handle, desc, desc.shape[0])
+
+    def submit(self, image: np.ndarray, width: int, height: int, kps_packed: np.ndarray, gallery: int, k: int = 2,
+               ratio: float = 0.8, want_desc: bool = False):
+        """image: (H, pitch) uint8; kps_packed: (n, 12) uint8.  Returns a ticket;
+        the output arrays stay referenced until wait()."""
+        n = kps_packed.shape[0]
+        matches = _host_buffer((max(n, 1), 16))
+        desc = _host_buffer((max(n, 1), DESC_BYTES)) if want_desc else None
+        req = latch_request(image.ctypes.data, width, height, image.strides[0], kps_packed.ctypes.data, n, gallery,
+                            k, ratio, matches.ctypes.data, desc.ctypes.data if desc is not None else 0)
+        t = latch_submit(self.handle, req)
+        self._live[t] = (image, kps_packed, matches, desc, n)
+        return t
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        """Returns (latch_result, match records, descriptors or None) and forgets the ticket."""
+        r = latch_wait(self.handle, ticket, timeout_ms)
+        image, kps, matches, desc, n = self._live.pop(ticket)
+        latch_release(self.handle, ticket)
+        return r, matches_from_bytes(matches[:n]), (desc[:n] if desc is not None else None)
+
+    def stats(self) -> dict:
+        return latch_session_get_stats(self.handle)
 
 
 def hamming_match_path(ctx, nq: int, nt: int) -> int:

@@ -71,6 +71,8 @@ latch_status plan_batch(latch_context* ctx, const latch_batch_desc* b, BatchPlan
             P.nq = static_cast<int32_t>(plan->n[qi]);
             P.nt = static_cast<int32_t>(plan->n[ti]);
             P.out0 = static_cast<int32_t>(plan->out0[p] - plan->out0[p0]);
+            P.k = b->k;
+            P.r_milli = 0;
         }
         plan_match_batch(mb, p1 - p0, ctx->sm_count);
         const size_t need = match_tc_batch_scratch_bytes(plan->total_kp, *mb);
@@ -136,11 +138,12 @@ extern "C" latch_status latch_batch_run(latch_context* ctx, const latch_batch_de
             P.nq = static_cast<int32_t>(plan.n[qi]);
             P.nt = static_cast<int32_t>(plan.n[ti]);
             P.out0 = static_cast<int32_t>(plan.out0[p] - plan.out0[p0]);
+            P.k = b->k;
+            P.r_milli = r_milli;
         }
         plan_match_batch(mb, p1 - p0, ctx->sm_count);
         st = cuda_check(ctx,
-                        launch_match_tc_batch(*mb, plan.total_kp, mbase, b->k, r_milli, b->d_matches + plan.out0[p0],
-                                              ctx->d_flags, s),
+                        launch_match_tc_batch(*mb, plan.total_kp, mbase, b->d_matches + plan.out0[p0], ctx->d_flags, s),
                         "batched match launch");
     }
     delete mb;

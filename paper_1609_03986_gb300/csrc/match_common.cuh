@@ -18,7 +18,7 @@
 namespace latch {
 
 constexpr uint64_t kNoKey = ~0ull;
-constexpr int kMaxProblems = 600;  // problems per launch (kernel-parameter space)
+constexpr int kMaxProblems = 512;  // problems per launch (kernel-parameter space)
 
 struct MatchProblem {
     int64_t unit0;   // first global unit
@@ -28,6 +28,8 @@ struct MatchProblem {
     int32_t mt, ntl;  // query tiles, train tiles
     int32_t g0;       // global index of the problem's first query tile
     int32_t out0;     // first output record
+    int32_t k;        // 1 or 2
+    int32_t r_milli;  // ratio test threshold, rha(1000 * ratio)
 };
 
 struct MatchBatch {
@@ -57,8 +59,14 @@ __device__ __forceinline__ void top2_insert_u64(uint64_t key, uint64_t& k1, uint
 
 void plan_match_batch(MatchBatch* b, int count, int64_t max_grid);
 size_t match_tc_batch_scratch_bytes(int64_t rows, const MatchBatch& b);
-cudaError_t launch_match_tc_batch(const MatchBatch& b, int64_t rows, void* scratch, int32_t k, int32_t r_milli,
-                                  latch_match* out, uint32_t* flags, cudaStream_t stream);
+size_t match_tc_partial_bytes(const MatchBatch& b);
+// Scratch layout [expanded rows][popcounts][partials]; the expanded rows and
+// popcounts of every problem's query and train sets must be filled already.
+cudaError_t launch_match_tc_batch(const MatchBatch& b, int64_t rows, void* scratch, latch_match* out,
+                                  uint32_t* flags, cudaStream_t stream);
+// Same with explicit buffers: `exp` holds `rows` expanded rows, `pop` their popcounts.
+cudaError_t launch_match_tc_rows(const MatchBatch& b, const uint8_t* exp, int64_t rows, const int32_t* pop,
+                                 uint64_t* partials, latch_match* out, uint32_t* flags, cudaStream_t stream);
 cudaError_t launch_expand(const uint8_t* desc, int64_t n, uint8_t* out, int32_t* pop, cudaStream_t stream);
 size_t match_tc_scratch_bytes_sms(int64_t sms, int64_t nq, int64_t nt);
 

@@ -376,7 +376,7 @@ __device__ __forceinline__ int problem_of_unit(const MatchBatch& b, int64_t u) {
 
 // Combine the partial records of every query row; write one latch_match per query.
 __global__ void match_merge_kernel(const __grid_constant__ MatchBatch batch, const uint64_t* __restrict__ partials,
-                                   int k, int r_milli, latch_match* __restrict__ out) {
+                                   latch_match* __restrict__ out) {
     const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (q >= batch.queries) return;
     int lo = 0, hi = batch.count - 1;  // problem: largest p with out0 <= q
@@ -385,6 +385,7 @@ __global__ void match_merge_kernel(const __grid_constant__ MatchBatch batch, con
         if (batch.p[mid].out0 <= q) lo = mid; else hi = mid - 1;
     }
     const MatchProblem& P = batch.p[lo];
+    const int k = P.k, r_milli = P.r_milli;
     const int64_t ql = q - P.out0;
     uint64_t k1 = kNoKey, k2 = kNoKey;
     if (P.ntl > 0) {
@@ -518,30 +519,25 @@ void plan_match_batch(MatchBatch* b, int count, int64_t max_grid) {
     }
 }
 
+size_t match_tc_partial_bytes(const MatchBatch& b) { return static_cast<size_t>(b.grid * b.smax * kRowsQ) * 16; }
+
 size_t match_tc_batch_scratch_bytes(int64_t rows, const MatchBatch& b) {
     const size_t exp_bytes = align_up(static_cast<size_t>(rows) * kKBytes, 1024);
     const size_t pop_bytes = align_up(static_cast<size_t>(rows) * 4, 256);
-    return exp_bytes + pop_bytes + static_cast<size_t>(b.grid * b.smax * kRowsQ) * 16 + 256;
+    return exp_bytes + pop_bytes + match_tc_partial_bytes(b) + 256;
 }
 
-// Scratch: expanded rows (rows x 512 B), popcounts, partial records.  The expanded
-// rows and popcounts must already be filled (launch_expand) when `expanded` is set.
-cudaError_t launch_match_tc_batch(const MatchBatch& b, int64_t rows, void* scratch, int32_t k, int32_t r_milli,
-                                  latch_match* out, uint32_t* flags, cudaStream_t stream) {
+cudaError_t launch_match_tc_rows(const MatchBatch& b, const uint8_t* exp, int64_t rows, const int32_t* pop,
+                                 uint64_t* partials, latch_match* out, uint32_t* flags, cudaStream_t stream) {
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(match_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    uint8_t* base = static_cast<uint8_t*>(scratch);
-    const size_t exp_bytes = align_up(static_cast<size_t>(rows) * kKBytes, 1024);
-    const size_t pop_bytes = align_up(static_cast<size_t>(rows) * 4, 256);
-    int32_t* pop = reinterpret_cast<int32_t*>(base + exp_bytes);
-    uint64_t* partials = reinterpret_cast<uint64_t*>(base + exp_bytes + pop_bytes);
     if (b.units > 0) {
         CUtensorMap map;
-        if (!make_map(&map, base, rows)) return cudaErrorInvalidValue;
+        if (!make_map(&map, exp, rows)) return cudaErrorInvalidValue;
         match_tc_kernel<<<static_cast<unsigned>(b.grid), kThreads, kSmemBytes, stream>>>(map, b, pop, partials, flags);
         note_launches(1);
         cudaError_t e = cudaGetLastError();
@@ -550,12 +546,25 @@ cudaError_t launch_match_tc_batch(const MatchBatch& b, int64_t rows, void* scrat
     if (b.queries == 0) return cudaSuccess;
     const int threads = 256;
     const int64_t grid = (b.queries + threads - 1) / threads;
-    match_merge_kernel<<<static_cast<unsigned>(grid), threads, 0, stream>>>(b, partials, k, r_milli, out);
+    match_merge_kernel<<<static_cast<unsigned>(grid), threads, 0, stream>>>(b, partials, out);
     note_launches(1);
     return cudaGetLastError();
 }
 
-static void single_problem(MatchBatch* b, int32_t nq, int32_t nt, int64_t sms) {
+// Scratch: expanded rows (rows x 512 B), popcounts, partial records.  The expanded
+// rows and popcounts must already be filled (launch_expand).
+cudaError_t launch_match_tc_batch(const MatchBatch& b, int64_t rows, void* scratch, latch_match* out,
+                                  uint32_t* flags, cudaStream_t stream) {
+    uint8_t* base = static_cast<uint8_t*>(scratch);
+    const size_t exp_bytes = align_up(static_cast<size_t>(rows) * kKBytes, 1024);
+    const size_t pop_bytes = align_up(static_cast<size_t>(rows) * 4, 256);
+    return launch_match_tc_rows(b, base, rows, reinterpret_cast<const int32_t*>(base + exp_bytes),
+                                reinterpret_cast<uint64_t*>(base + exp_bytes + pop_bytes), out, flags, stream);
+}
+
+static void single_problem(MatchBatch* b, int32_t nq, int32_t nt, int64_t sms, int32_t k = 2, int32_t r = 800) {
+    b->p[0].k = k;
+    b->p[0].r_milli = r;
     b->p[0].q_row0 = 0;
     b->p[0].t_row0 = nq;
     b->p[0].nq = nq;
@@ -579,7 +588,7 @@ size_t match_tc_scratch_bytes(const latch_context* ctx, int64_t nq, int64_t nt) 
 cudaError_t launch_match_tc(const latch_context* ctx, const uint8_t* q, int32_t nq, const uint8_t* t, int32_t nt,
                             int32_t k, int32_t r_milli, latch_match* out, void* scratch, cudaStream_t stream) {
     MatchBatch* b = new MatchBatch;
-    single_problem(b, nq, nt, ctx->sm_count);
+    single_problem(b, nq, nt, ctx->sm_count, k, r_milli);
     uint8_t* base = static_cast<uint8_t*>(scratch);
     const size_t exp_bytes = align_up(static_cast<size_t>(nq + nt) * kKBytes, 1024);
     int32_t* pop = reinterpret_cast<int32_t*>(base + exp_bytes);
@@ -588,7 +597,7 @@ cudaError_t launch_match_tc(const latch_context* ctx, const uint8_t* q, int32_t 
         e = launch_expand(q, nq, base, pop, stream);
         if (e == cudaSuccess) e = launch_expand(t, nt, base + static_cast<size_t>(nq) * kKBytes, pop + nq, stream);
     }
-    if (e == cudaSuccess) e = launch_match_tc_batch(*b, nq + nt, scratch, k, r_milli, out, ctx->d_flags, stream);
+    if (e == cudaSuccess) e = launch_match_tc_batch(*b, nq + nt, scratch, out, ctx->d_flags, stream);
     delete b;
     return e;
 }

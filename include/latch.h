@@ -277,6 +277,13 @@ latch_status hamming_match_noalloc(const uint8_t *d_query, int32_t nq, const uin
  * device-side input error (LATCH_EDEVICE) or an asynchronous CUDA error. */
 latch_status latch_check(latch_context *ctx);
 
+/* Failure-detection self-test (no counterpart in the paper): enqueue a kernel whose
+ * bounded device-side wait can never be satisfied, so that after limit_us
+ * microseconds (1 .. 2e6) it gives up and raises the context's timeout flag, the
+ * path every pipeline wait of the library takes.  The next latch_check returns
+ * LATCH_ETIMEOUT (and clears the flag); the context stays usable. */
+latch_status latch_selftest_wait_timeout(latch_context *ctx, int32_t limit_us, latch_stream_t stream);
+
 /* One-line description of the last error on `ctx` (or of the last failed
  * latch_context_create when ctx is NULL).  Valid until the next call. */
 const char *latch_last_error(const latch_context *ctx);

@@ -84,6 +84,7 @@ EXPORTS = [
     ("latch_extract", ctypes.c_int, [_P, ctypes.POINTER(latch_image), _P, _I32, _P, _P, _P]),
     ("hamming_match", ctypes.c_int, [_P, _P, _I32, _P, _I32, _I32, _F, _P, _I32, _P]),
     ("latch_check", ctypes.c_int, [_P]),
+    ("latch_selftest_wait_timeout", ctypes.c_int, [_P, _I32, _P]),
     ("latch_kernel_launches", ctypes.c_uint64, []),
     ("hamming_match_path", ctypes.c_int32, [_P, _I64, _I64]),
     ("latch_reserve_batch", ctypes.c_int, [_P, ctypes.POINTER(latch_batch_desc)]),
@@ -351,6 +352,10 @@ class Session:
 def hamming_match_path(ctx, nq: int, nt: int) -> int:
     """The path LATCH_PATH_AUTO takes for nq x nt on this context."""
     return int(library().hamming_match_path(ctx, nq, nt))
+
+
+def latch_selftest_wait_timeout(ctx, limit_us: int, stream: int = 0) -> None:
+    _check(ctx, library().latch_selftest_wait_timeout(ctx, limit_us, stream))
 
 
 def latch_kernel_launches() -> int:

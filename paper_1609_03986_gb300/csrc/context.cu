@@ -7,8 +7,25 @@
 #include <new>
 
 #include "internal.h"
+#include "sm103.h"
 
 namespace latch {
+
+// Failure-detection self-test: waits, with the kernels' bounded-wait routine, on an
+// mbarrier that nothing ever arrives at; when the limit runs out the block raises
+// the context's timeout flag and returns, exactly as a stalled pipeline would.
+__global__ void selftest_wait_kernel(uint64_t limit_ns, uint32_t* flags) {
+    __shared__ uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        sm103::mbar_init(&bar, 1);
+        abort_flag = 0;
+        sm103::fence_mbar_init();
+    }
+    __syncthreads();
+    const bool ok = sm103::mbar_wait(&bar, 0, &abort_flag, limit_ns);
+    if (!__syncthreads_and(ok) && threadIdx.x == 0) atomicOr(flags, kFlagTimeout);
+}
 
 static char g_create_err[256] = "";
 static std::atomic<uint64_t> g_launches{0};
@@ -213,6 +230,16 @@ latch_status latch_reserve(latch_context* ctx, int64_t max_keypoints, int64_t ma
 
 int32_t hamming_match_path(const latch_context* ctx, int64_t nq, int64_t nt) {
     return ctx ? choose_match_path(ctx, nq, nt) : -1;
+}
+
+latch_status latch_selftest_wait_timeout(latch_context* ctx, int32_t limit_us, latch_stream_t stream) {
+    if (!ctx) return fail(ctx, LATCH_EINVAL, "NULL context");
+    if (limit_us < 1 || limit_us > 2000000) return fail(ctx, LATCH_EINVAL, "limit_us must be in [1, 2e6]");
+    LATCH_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    selftest_wait_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<uint64_t>(limit_us) * 1000,
+                                                                          ctx->d_flags);
+    note_launches(1);
+    return cuda_check(ctx, cudaGetLastError(), "self-test launch");
 }
 
 latch_status latch_check(latch_context* ctx) {

@@ -191,6 +191,19 @@ __global__ void __launch_bounds__(kBucketThreads) bucket_kernel(const __grid_con
     }
 }
 
+// Offset-table entries 16*bseg .. 16*bseg+19 of window row `by` of table `tab`
+// (scale * 32 + bin): two 16-byte and one 8-byte load.
+__device__ __forceinline__ void load_table_segment(const int16_t* __restrict__ toff, int tab, int by, int bseg,
+                                                   int32_t (&tw)[10]) {
+    const int16_t* t = toff + static_cast<size_t>(tab) * kWinPix + by * kWin + 16 * bseg;
+    const int4 ta = reinterpret_cast<const int4*>(t)[0];
+    const int4 tb = reinterpret_cast<const int4*>(t)[1];
+    const int2 tc = reinterpret_cast<const int2*>(t)[4];
+    tw[0] = ta.x; tw[1] = ta.y; tw[2] = ta.z; tw[3] = ta.w;
+    tw[4] = tb.x; tw[5] = tb.y; tw[6] = tb.z; tw[7] = tb.w;
+    tw[8] = tc.x; tw[9] = tc.y;
+}
+
 // Persistent: blocks take work items from the launch's queue (counters[1]).
 template <int NI>
 __global__ void __launch_bounds__(kThreads) extract_cells_kernel(
@@ -200,6 +213,7 @@ __global__ void __launch_bounds__(kThreads) extract_cells_kernel(
     uint32_t* __restrict__ flags) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ int s_item;
+    __shared__ int4 s_kp[kItemKps];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     uint32_t* s_win = reinterpret_cast<uint32_t*>(smem);                  // [2][kWinWords]
     uint8_t* s_bits = reinterpret_cast<uint8_t*>(s_win + 2 * kWinWords);  // [2][512] one byte per bit
@@ -238,6 +252,12 @@ __global__ void __launch_bounds__(kThreads) extract_cells_kernel(
             mbar_arrive_expect_tx(s_bar, static_cast<uint32_t>(tg.tw * tg.th));
             tma_load_2d(s_tile, &prm.map[img], ox, oy, s_bar);
         }
+        // the item's keypoints, while the tile is in flight: (x, y, table, output row)
+        if (threadIdx.x < k1 - k0) {
+            const int pi = perm[k0 + threadIdx.x];
+            const latch_keypoint kp = kps[pi];
+            s_kp[threadIdx.x] = make_int4(kp.x, kp.y, kp.scale_idx * kBins + (kp.angle_bin & (kBins - 1)), pi);
+        }
         const bool ok = mbar_wait(s_bar, phase, s_abort);
         if (!__syncthreads_and(ok)) {
             if (threadIdx.x == 0) {
@@ -249,21 +269,19 @@ __global__ void __launch_bounds__(kThreads) extract_cells_kernel(
             return;
         }
 
+        // offset-table entries 0..19 of this thread's row segment for the item's first
+        // keypoint (32-byte aligned: 96*by + 32*bseg bytes); later ones are prefetched
+        // one keypoint ahead, during the previous keypoint's triplets
+        int32_t tw[10], tn[10];
+        if (threadIdx.x < 144) load_table_segment(toff, s_kp[0].z, by, bseg, tw);
+
         for (int k = k0; k <= k1; ++k) {
             const int buf = k & 1;
             if (k < k1 && threadIdx.x < 144) {
                 // ---- sample the window of keypoint k into 4 byte-shifted copies; this
                 // thread: row by, pixels 16*bseg .. 16*bseg+18 ----
-                const latch_keypoint kp = kps[perm[k]];
+                const int4 kp = s_kp[k - k0];
                 const int base = (kp.y - oy) * tg.tw + (kp.x - ox);
-                const int16_t* tab =
-                    toff + (static_cast<size_t>(kp.scale_idx) * kBins + (kp.angle_bin & (kBins - 1))) * kWinPix +
-                    by * kWin + 16 * bseg;
-                // table entries 0..19 of the segment (32-byte aligned: 96*by + 32*bseg bytes)
-                const int4 ta = reinterpret_cast<const int4*>(tab)[0];
-                const int4 tb = reinterpret_cast<const int4*>(tab)[1];
-                const int2 tc = reinterpret_cast<const int2*>(tab)[4];
-                const int32_t tw[10] = {ta.x, ta.y, ta.z, ta.w, tb.x, tb.y, tb.z, tb.w, tc.x, tc.y};
                 uint32_t p[5] = {0, 0, 0, 0, 0};
 #pragma unroll
                 for (int u = 0; u < 19; ++u) {
@@ -282,6 +300,7 @@ __global__ void __launch_bounds__(kThreads) extract_cells_kernel(
                 w[3 * kCopyWords / 4] =
                     make_uint4(__funnelshift_r(p[0], p[1], 24), __funnelshift_r(p[1], p[2], 24),
                                __funnelshift_r(p[2], p[3], 24), __funnelshift_r(p[3], p[4], 24));
+                if (k + 1 < k1) load_table_segment(toff, s_kp[k + 1 - k0].z, by, bseg, tn);
             }
             __syncthreads();
             if (k > k0 && warp == 0) {
@@ -299,9 +318,11 @@ __global__ void __launch_bounds__(kThreads) extract_cells_kernel(
                 const uint32_t y = __shfl_sync(0xffffffffu, mine, src + 1);
                 const uint32_t z = __shfl_sync(0xffffffffu, mine, src + 2);
                 const uint32_t v = __shfl_sync(0xffffffffu, mine, src + 3);
-                if (lane < 4) out[static_cast<size_t>(perm[k - 1]) * 4 + lane] = make_uint4(x, y, z, v);
+                if (lane < 4) out[static_cast<size_t>(s_kp[k - 1 - k0].w) * 4 + lane] = make_uint4(x, y, z, v);
             }
             if (k == k1) break;
+#pragma unroll
+            for (int j = 0; j < 10; ++j) tw[j] = tn[j];
             // ---- Eq. 1 for this lane's two triplets ----
             const uint32_t* wb = s_win + buf * kWinWords;
             uint8_t* bits = s_bits + buf * kBits;

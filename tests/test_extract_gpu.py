@@ -115,3 +115,17 @@ def test_triplet_table_switch(gpu_ctx, triplets):
     assert np.array_equal(got, oracle.extract(img, w, h, kps, other, synth.SCALES))
     got = _extract(gpu_ctx, img, w, h, kps, triplets)
     assert np.array_equal(got, oracle.extract(img, w, h, kps, triplets, synth.SCALES))
+
+
+def test_device_wait_timeout_is_reported(gpu_ctx, triplets):
+    """A device-side wait that can never complete gives up after its limit and the
+    host sees LATCH_ETIMEOUT; the context keeps working afterwards."""
+    P.latch_selftest_wait_timeout(gpu_ctx.handle, 20000, 0)
+    with pytest.raises(P.LatchError) as e:
+        gpu_ctx.check()
+    assert e.value.status == 6
+    gpu_ctx.check()  # the flag was cleared
+    w, h = 120, 90
+    img = synth.image(synth.seed(11, 9, synth.KIND_IMAGE), w, h, n_ellipses=5)
+    kps = np.array([[60, 45, 3, 1], [10, 10, 30, 2]], np.int32)
+    assert np.array_equal(_extract(gpu_ctx, img, w, h, kps), oracle.extract(img, w, h, kps, triplets, synth.SCALES))

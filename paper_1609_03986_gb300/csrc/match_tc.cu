@@ -8,16 +8,16 @@
 //
 // One launch serves a batch of matching problems (query set x train set pairs; a
 // single hamming_match call is a batch of one).  All descriptors live in one
-// expanded buffer with one TMA tensor map.  The units (problem, 256-query tile,
-// 128-train tile) of all problems are linearised and split into one contiguous
+// expanded buffer with one TMA tensor map.  The units (problem, 128-query tile,
+// 256-train tile) of all problems are linearised and split into one contiguous
 // range per block (one block per SM, persistent):
-//   warp 0     TMA producer: the query tile (two 128-row A operands, 128 KB) stays
-//              resident while consecutive units share it; train chunks (128 rows x
-//              128 bytes) go through a 5-stage ring, 128-byte swizzle;
-//   warp 1     MMA issuer: per unit 2 x 16 tcgen05.mma (M=128, N=128, K=32) into one
-//              of two double-buffered TMEM accumulators;
+//   warp 0     TMA producer: the query tile (128 rows x 512 B, 64 KB) stays resident
+//              while consecutive units share it; train chunks (256 rows x 128 bytes)
+//              go through a 4-stage ring, 128-byte swizzle;
+//   warp 1     MMA issuer: per unit 16 tcgen05.mma (M=128, N=256, K=32) into one of
+//              two double-buffered 256-column TMEM accumulators;
 //   warp 2     TMEM allocator (all 512 columns);
-//   warps 4-11 epilogue (one query row per thread): double-buffered tcgen05.ld of
+//   warps 4-11 epilogue (one query row and 128 columns per thread): double-buffered tcgen05.ld of
 //              the fp32 dot products, key =
 //              ((popc(t) - 2*dot + 512) << 8 | column) formed exactly in fp32 by
 //              one FMA, four interleaved min / second-min chains with FMNMX; the tile's two best are
@@ -39,18 +39,19 @@ namespace {
 
 using namespace sm103;
 
-constexpr int kRowsA = 128;             // rows per MMA (M)
-constexpr int kSubA = 2;                // A operands per query tile
-constexpr int kRowsQ = kRowsA * kSubA;  // queries per tile: 256
-constexpr int kColsB = 128;             // train rows per unit (N)
+constexpr int kRowsA = 128;             // rows per MMA (M) = query rows per tile
+constexpr int kRowsQ = kRowsA;          // queries per tile
+constexpr int kColsB = 256;             // train rows per unit (N)
+constexpr int kRowsP = 2 * kRowsQ;      // partial records per tile: (row, column half)
 constexpr int kKBytes = 512;            // expanded descriptor: 512 x 8-bit
 constexpr int kChunk = 128;             // K bytes per swizzle atom / TMA box
 constexpr int kChunks = kKBytes / kChunk;
-constexpr int kStages = 5;
-constexpr int kTileBytes = kRowsA * kChunk;  // 16 KB
+constexpr int kStages = 4;
+constexpr int kTileBytes = kRowsA * kChunk;   // 16 KB: one TMA box of 128 rows x 128 B
+constexpr int kStageBytes = kColsB * kChunk;  // 32 KB: a train chunk of 256 rows x 128 B
 constexpr int kThreads = 384;   // 12 warps: producer, MMA, TMEM, idle, 8 epilogue
 constexpr int kEpiThreads = 256;
-constexpr int kTmemCols = 512;
+constexpr int kTmemCols = 512;  // two 256-column accumulators
 constexpr uint32_t kIdesc = idesc_e4m3_f32(kRowsA, kColsB);
 
 // AND of `v` over the 256 epilogue threads (named barrier 1).
@@ -69,9 +70,9 @@ __device__ __forceinline__ bool group_all(bool v) {
 
 struct Smem {
     // offsets in the 1024-aligned dynamic buffer
-    static constexpr int a = 0;                                        // [kSubA][kChunks] tiles
-    static constexpr int b = a + kSubA * kChunks * kTileBytes;         // [kStages] tiles
-    static constexpr int cvec = b + kStages * kTileBytes;              // float [2][kColsB]
+    static constexpr int a = 0;                                        // [kChunks] tiles of 16 KB
+    static constexpr int b = a + kChunks * kTileBytes;                 // [kStages] chunks of 32 KB
+    static constexpr int cvec = b + kStages * kStageBytes;             // float [2][kColsB]
     static constexpr int bars = cvec + 2 * kColsB * 4;                 // uint64 barriers
     static constexpr int nbars = 2 * kStages + 2 + 4 + 1;
     static constexpr int misc = bars + nbars * 8;                      // tmem base, abort flag
@@ -158,11 +159,10 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                         if (!mbar_wait(a_empty, a_par, abort)) break;
                         a_par ^= 1;
                     }
-                    mbar_arrive_expect_tx(a_full, kSubA * kChunks * kTileBytes);
-                    for (int a = 0; a < kSubA; ++a)
-                        for (int kc = 0; kc < kChunks; ++kc)
-                            tma_load_2d(sA + (a * kChunks + kc) * kTileBytes, &tm, kc * kChunk,
-                                        static_cast<int32_t>(P.q_row0 + m * kRowsQ + a * kRowsA), a_full);
+                    mbar_arrive_expect_tx(a_full, kChunks * kTileBytes);
+                    for (int kc = 0; kc < kChunks; ++kc)
+                        tma_load_2d(sA + kc * kTileBytes, &tm, kc * kChunk, static_cast<int32_t>(P.q_row0 + m * kRowsQ),
+                                    a_full);
                     prev_g = g;
                 }
                 bool ok = true;
@@ -171,9 +171,10 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                         ok = false;
                         break;
                     }
-                    mbar_arrive_expect_tx(&full[stage], kTileBytes);
-                    tma_load_2d(sB + stage * kTileBytes, &tm, kc * kChunk, static_cast<int32_t>(P.t_row0 + n * kColsB),
-                                &full[stage]);
+                    mbar_arrive_expect_tx(&full[stage], kStageBytes);
+                    for (int h = 0; h < kColsB / kRowsA; ++h)  // two 128-row boxes, rows back to back
+                        tma_load_2d(sB + stage * kStageBytes + h * kTileBytes, &tm, kc * kChunk,
+                                    static_cast<int32_t>(P.t_row0 + n * kColsB + h * kRowsA), &full[stage]);
                     filled[stage] = true;
                     fill_par[stage] = ring;
                     if (++stage == kStages) {
@@ -223,16 +224,13 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t b_addr = smem_u32(sB + stage * kTileBytes);
+                    const uint32_t b_addr = smem_u32(sB + stage * kStageBytes);
+                    const uint32_t a_addr = smem_u32(sA + kc * kTileBytes);
+                    const uint32_t d = tmem + static_cast<uint32_t>(buf * kColsB);
 #pragma unroll
-                    for (int a = 0; a < kSubA; ++a) {
-                        const uint32_t a_addr = smem_u32(sA + (a * kChunks + kc) * kTileBytes);
-                        const uint32_t d = tmem + static_cast<uint32_t>((a * 2 + buf) * kColsB);
-#pragma unroll
-                        for (int ks = 0; ks < kChunk / 32; ++ks)
-                            mma_f8f6f4(d, umma_desc_sw128(a_addr + ks * 32), umma_desc_sw128(b_addr + ks * 32), kIdesc,
-                                       (kc | ks) != 0);
-                    }
+                    for (int ks = 0; ks < kChunk / 32; ++ks)
+                        mma_f8f6f4(d, umma_desc_sw128(a_addr + ks * 32), umma_desc_sw128(b_addr + ks * 32), kIdesc,
+                                   (kc | ks) != 0);
                     mma_commit(&empty[stage]);
                     if (++stage == kStages) {
                         stage = 0;
@@ -258,10 +256,11 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
         }
     } else if (warp >= 4) {
         // ---------------- epilogue: 8 warps, thread = one query row ----------------
-        const int et = threadIdx.x - 128;  // 0..255
+        const int et = threadIdx.x - 128;  // 0..255: column of sC this thread fills
         const int quarter = warp & 3;      // TMEM lane quarter this warp may access
-        const int a = (warp - 4) >> 2;     // A operand (query sub-tile) of this warp
-        const int row_in_tile = a * kRowsA + quarter * 32 + lane;
+        const int half = (warp - 4) >> 2;  // accumulator columns [128*half, 128*half + 128)
+        const int row_in_tile = quarter * 32 + lane;
+        const int prow = half * kRowsQ + row_in_tile;  // partial record of (row, half)
         UnitCursor cur;
         uint32_t acc_par[2] = {0, 0};
         uint64_t k1 = kNoKey, k2 = kNoKey;
@@ -281,7 +280,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                 if (g_first < 0) g_first = g;
                 prev_g = g;
             }
-            if (et < kColsB) {
+            {
                 const int64_t col = n * kColsB + et;
                 sC[buf * kColsB + et] = col < P.nt ? static_cast<float>((pop[P.t_row0 + col] + 512) * 256 + et)
                                                    : __int_as_float(0x7f800000);
@@ -290,9 +289,10 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
             if (!group_all(mbar_wait(&acc_full[buf], acc_par[buf], abort))) break;
             acc_par[buf] ^= 1;
             tc_fence_after();
-            const float* cv = sC + buf * kColsB;
-            const uint32_t base =
-                tmem + (static_cast<uint32_t>(quarter * 32) << 16) + static_cast<uint32_t>((a * 2 + buf) * kColsB);
+            const float* cv = sC + buf * kColsB;  // (advanced to this warp's half below)
+            const uint32_t base = tmem + (static_cast<uint32_t>(quarter * 32) << 16) +
+                                  static_cast<uint32_t>(buf * kColsB + half * 128);
+            cv += half * 128;
             // four independent min / second-min chains over the 128 columns
             float m1[4], m2[4];
 #pragma unroll
@@ -301,9 +301,9 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
             tmem_ld_32x32b_x32(base, va);
             tmem_ld_wait();
 #pragma unroll
-            for (int ch = 0; ch < kColsB / 32; ++ch) {
+            for (int ch = 0; ch < 4; ++ch) {
                 uint32_t* cur_v = (ch & 1) ? vb : va;
-                if (ch + 1 < kColsB / 32) tmem_ld_32x32b_x32(base + (ch + 1) * 32, (ch & 1) ? va : vb);
+                if (ch + 1 < 4) tmem_ld_32x32b_x32(base + (ch + 1) * 32, (ch & 1) ? va : vb);
 #pragma unroll
                 for (int j = 0; j < 32; j += 4) {
                     const float4 cc = *reinterpret_cast<const float4*>(cv + ch * 32 + j);
@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                         m2[c] = fminf(m2[c], h);
                     }
                 }
-                if (ch + 1 < kColsB / 32) tmem_ld_wait();
+                if (ch + 1 < 4) tmem_ld_wait();
             }
             // combine the chains (keys are unique): (a1,a2) + (b1,b2) -> (min, second min)
 #pragma unroll
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                 last_of_tile = (Q.g0 + (u + 1 - Q.unit0) / Q.ntl) != g;
             }
             if (last_of_tile) {
-                uint64_t* rec = partials + ((c * batch.smax + (g - g_first)) * kRowsQ + row_in_tile) * 2;
+                uint64_t* rec = partials + ((c * batch.smax + (g - g_first)) * kRowsP + prow) * 2;
                 rec[0] = k1;
                 rec[1] = k2;
             }
@@ -399,9 +399,12 @@ __global__ void match_merge_kernel(const __grid_constant__ MatchBatch batch, con
             const int64_t us = split_start(c, batch.units, batch.grid);
             const MatchProblem& F = batch.p[problem_of_unit(batch, us)];
             const int64_t g_first = F.g0 + (us - F.unit0) / F.ntl;
-            const uint64_t* rec = partials + ((c * batch.smax + (g - g_first)) * kRowsQ + r) * 2;
+            const uint64_t* rec = partials + ((c * batch.smax + (g - g_first)) * kRowsP + r) * 2;
             top2_insert_u64(rec[0], k1, k2);
             top2_insert_u64(rec[1], k1, k2);
+            const uint64_t* rec2 = rec + 2 * kRowsQ;  // the row's other column half
+            top2_insert_u64(rec2[0], k1, k2);
+            top2_insert_u64(rec2[1], k1, k2);
         }
     }
     latch_match mres;
@@ -519,7 +522,7 @@ void plan_match_batch(MatchBatch* b, int count, int64_t max_grid) {
     }
 }
 
-size_t match_tc_partial_bytes(const MatchBatch& b) { return static_cast<size_t>(b.grid * b.smax * kRowsQ) * 16; }
+size_t match_tc_partial_bytes(const MatchBatch& b) { return static_cast<size_t>(b.grid * b.smax * kRowsP) * 16; }
 
 size_t match_tc_batch_scratch_bytes(int64_t rows, const MatchBatch& b) {
     const size_t exp_bytes = align_up(static_cast<size_t>(rows) * kKBytes, 1024);

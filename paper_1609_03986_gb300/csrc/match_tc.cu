@@ -80,11 +80,37 @@ struct Smem {
 };
 constexpr int kSmemBytes = Smem::total + 1024;
 
-// Walks the units of a block's range in increasing order.
-struct UnitCursor {
-    int p = 0;
-    __device__ __forceinline__ void seek(const MatchBatch& b, int64_t u) {
-        while (p + 1 < b.count && b.p[p + 1].unit0 <= u) ++p;
+// Walks the units of a block's range in increasing order without dividing:
+// (problem p, query tile m, train tile n) of the current unit, and g = the global
+// index of its query tile.  last_of_tile(): the next unit is in another query tile
+// (or beyond the range).
+struct UnitIter {
+    int p;
+    int32_t m, n;
+    int64_t u, u_end;
+    __device__ __forceinline__ void init(const MatchBatch& b, int64_t u0, int64_t u1) {
+        p = 0;
+        while (p + 1 < b.count && b.p[p + 1].unit0 <= u0) ++p;
+        const int64_t r = u0 - b.p[p].unit0;
+        m = static_cast<int32_t>(r / b.p[p].ntl);
+        n = static_cast<int32_t>(r - static_cast<int64_t>(m) * b.p[p].ntl);
+        u = u0;
+        u_end = u1;
+    }
+    __device__ __forceinline__ int64_t g(const MatchBatch& b) const { return b.p[p].g0 + m; }
+    __device__ __forceinline__ bool last_of_tile(const MatchBatch& b) const {
+        return u + 1 >= u_end || n + 1 == b.p[p].ntl;
+    }
+    __device__ __forceinline__ void next(const MatchBatch& b) {
+        ++u;
+        if (++n == b.p[p].ntl) {
+            n = 0;
+            if (++m == b.p[p].mt) {
+                m = 0;
+                ++p;
+                while (p + 1 < b.count && b.p[p].mt * static_cast<int64_t>(b.p[p].ntl) == 0) ++p;  // skip empty
+            }
+        }
     }
 };
 
@@ -142,18 +168,18 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
     if (warp == 0) {
         // ---------------- TMA producer ----------------
         if (lane == 0) {
-            UnitCursor cur;
+            UnitIter it;
+            it.init(batch, u0, u1);
             int stage = 0;
             uint32_t ring = 0, a_par = 0;
             uint32_t fill_par[kStages];
             bool filled[kStages];
             for (int s = 0; s < kStages; ++s) filled[s] = false, fill_par[s] = 0;
             int64_t prev_g = -1;
-            for (int64_t u = u0; u < u1; ++u) {
-                cur.seek(batch, u);
-                const MatchProblem& P = batch.p[cur.p];
-                const int64_t m = (u - P.unit0) / P.ntl, n = (u - P.unit0) % P.ntl;
-                const int64_t g = P.g0 + m;
+            for (int64_t u = u0; u < u1; ++u, it.next(batch)) {
+                const MatchProblem& P = batch.p[it.p];
+                const int64_t m = it.m, n = it.n;
+                const int64_t g = it.g(batch);
                 if (g != prev_g) {
                     if (prev_g >= 0) {
                         if (!mbar_wait(a_empty, a_par, abort)) break;
@@ -198,16 +224,15 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            UnitCursor cur;
+            UnitIter it;
+            it.init(batch, u0, u1);
             int stage = 0;
             uint32_t ring = 0, a_par = 0;
             uint32_t acc_par[2] = {0, 0};
             int64_t prev_g = -1;
             int i = 0;
-            for (int64_t u = u0; u < u1 && !*abort; ++u, ++i) {
-                cur.seek(batch, u);
-                const MatchProblem& P = batch.p[cur.p];
-                const int64_t g = P.g0 + (u - P.unit0) / P.ntl;
+            for (int64_t u = u0; u < u1 && !*abort; ++u, ++i, it.next(batch)) {
+                const int64_t g = it.g(batch);
                 const int buf = i & 1;
                 if (g != prev_g) {
                     if (!mbar_wait(a_full, a_par, abort)) break;
@@ -239,14 +264,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                 }
                 if (!ok) break;
                 mma_commit(&acc_full[buf]);
-                bool last_of_tile = (u + 1 >= u1);
-                if (!last_of_tile) {
-                    UnitCursor nx = cur;
-                    nx.seek(batch, u + 1);
-                    const MatchProblem& Q = batch.p[nx.p];
-                    last_of_tile = (Q.g0 + (u + 1 - Q.unit0) / Q.ntl) != g;
-                }
-                if (last_of_tile) mma_commit(a_empty);
+                if (it.last_of_tile(batch)) mma_commit(a_empty);
             }
             // every issued MMA has finished before TMEM is released
             mma_commit(mma_done);
@@ -261,17 +279,17 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
         const int half = (warp - 4) >> 2;  // accumulator columns [128*half, 128*half + 128)
         const int row_in_tile = quarter * 32 + lane;
         const int prow = half * kRowsQ + row_in_tile;  // partial record of (row, half)
-        UnitCursor cur;
+        UnitIter it;
+        it.init(batch, u0, u1);
         uint32_t acc_par[2] = {0, 0};
         uint64_t k1 = kNoKey, k2 = kNoKey;
         int32_t pq = 0;
         int64_t prev_g = -1, g_first = -1;
         int i = 0;
-        for (int64_t u = u0; u < u1; ++u, ++i) {
-            cur.seek(batch, u);
-            const MatchProblem& P = batch.p[cur.p];
-            const int64_t m = (u - P.unit0) / P.ntl, n = (u - P.unit0) % P.ntl;
-            const int64_t g = P.g0 + m;
+        for (int64_t u = u0; u < u1; ++u, ++i, it.next(batch)) {
+            const MatchProblem& P = batch.p[it.p];
+            const int64_t m = it.m, n = it.n;
+            const int64_t g = it.g(batch);
             const int buf = i & 1;
             if (g != prev_g) {
                 const int64_t row = m * kRowsQ + row_in_tile;
@@ -341,14 +359,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                     top2_insert_u64((static_cast<uint64_t>(d) << 32) | idx, k1, k2);
                 }
             }
-            bool last_of_tile = (u + 1 >= u1);
-            if (!last_of_tile) {
-                UnitCursor nx = cur;
-                nx.seek(batch, u + 1);
-                const MatchProblem& Q = batch.p[nx.p];
-                last_of_tile = (Q.g0 + (u + 1 - Q.unit0) / Q.ntl) != g;
-            }
-            if (last_of_tile) {
+            if (it.last_of_tile(batch)) {
                 uint64_t* rec = partials + ((c * batch.smax + (g - g_first)) * kRowsP + prow) * 2;
                 rec[0] = k1;
                 rec[1] = k2;

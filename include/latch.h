@@ -250,6 +250,26 @@ latch_status latch_release(latch_session *s, uint64_t ticket);
 latch_status latch_session_get_stats(latch_session *s, latch_session_stats *out);
 const char *latch_session_last_error(const latch_session *s);
 
+/* ---- Autotuning (tile shapes and path choice, by measurement on this device) ---- */
+typedef struct {
+    int32_t item_kps;           /* extraction: keypoints per work item (block visit), 1..32 */
+    int64_t tensor_min_pairs;   /* matching: LATCH_PATH_AUTO uses the tensor cores from nq*nt >= this */
+} latch_tuning;
+
+typedef struct {
+    int32_t width, height;      /* representative image size */
+    int32_t n_keypoints;        /* keypoints per image (0: skip the extraction tuning) */
+    int32_t n_query, n_train;   /* representative matching shape (0: skip the matching tuning) */
+} latch_tune_shape;
+
+/* Measure the candidate extraction work-item sizes and the matching paths on
+ * synthetic device data of this shape and keep the fastest in the context; results
+ * do not change (all candidates compute identical outputs), only speed.  Synchronous;
+ * allocates temporary device memory.  `out` (may be NULL) receives the choice. */
+latch_status latch_autotune(latch_context *ctx, const latch_tune_shape *shape, latch_tuning *out);
+latch_status latch_get_tuning(const latch_context *ctx, latch_tuning *out);
+latch_status latch_set_tuning(latch_context *ctx, const latch_tuning *tuning);
+
 /* The path LATCH_PATH_AUTO takes for nq x nt on this context (LATCH_PATH_POPC or
  * LATCH_PATH_TENSOR); -1 on a NULL context. */
 int32_t hamming_match_path(const latch_context *ctx, int64_t nq, int64_t nt);

@@ -52,6 +52,15 @@ class latch_batch_desc(ctypes.Structure):
                 ("d_matches", ctypes.c_void_p)]
 
 
+class latch_tuning(ctypes.Structure):
+    _fields_ = [("item_kps", ctypes.c_int32), ("tensor_min_pairs", ctypes.c_int64)]
+
+
+class latch_tune_shape(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("n_keypoints", ctypes.c_int32),
+                ("n_query", ctypes.c_int32), ("n_train", ctypes.c_int32)]
+
+
 class latch_request(ctypes.Structure):
     _fields_ = [("h_image", ctypes.c_void_p), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
                 ("pitch", ctypes.c_int64), ("h_kps", ctypes.c_void_p), ("n", ctypes.c_int32),
@@ -87,6 +96,9 @@ EXPORTS = [
     ("latch_selftest_wait_timeout", ctypes.c_int, [_P, _I32, _P]),
     ("latch_kernel_launches", ctypes.c_uint64, []),
     ("hamming_match_path", ctypes.c_int32, [_P, _I64, _I64]),
+    ("latch_autotune", ctypes.c_int, [_P, ctypes.POINTER(latch_tune_shape), ctypes.POINTER(latch_tuning)]),
+    ("latch_get_tuning", ctypes.c_int, [_P, ctypes.POINTER(latch_tuning)]),
+    ("latch_set_tuning", ctypes.c_int, [_P, ctypes.POINTER(latch_tuning)]),
     ("latch_reserve_batch", ctypes.c_int, [_P, ctypes.POINTER(latch_batch_desc)]),
     ("latch_batch_run", ctypes.c_int, [_P, ctypes.POINTER(latch_batch_desc), _P]),
     ("latch_session_create", ctypes.c_int, [ctypes.c_int, ctypes.c_size_t, _I64, _I32, _I64, _P,
@@ -347,6 +359,24 @@ class Session:
 
     def stats(self) -> dict:
         return latch_session_get_stats(self.handle)
+
+
+def latch_autotune(ctx, width: int, height: int, n_keypoints: int, n_query: int, n_train: int) -> dict:
+    """Tune on this device for the given shape; returns the chosen settings."""
+    out = latch_tuning()
+    _check(ctx, library().latch_autotune(ctx, ctypes.byref(latch_tune_shape(width, height, n_keypoints, n_query,
+                                                                            n_train)), ctypes.byref(out)))
+    return {"item_kps": out.item_kps, "tensor_min_pairs": out.tensor_min_pairs}
+
+
+def latch_get_tuning(ctx) -> dict:
+    out = latch_tuning()
+    _check(ctx, library().latch_get_tuning(ctx, ctypes.byref(out)))
+    return {"item_kps": out.item_kps, "tensor_min_pairs": out.tensor_min_pairs}
+
+
+def latch_set_tuning(ctx, item_kps: int, tensor_min_pairs: int) -> None:
+    _check(ctx, library().latch_set_tuning(ctx, ctypes.byref(latch_tuning(item_kps, tensor_min_pairs))))
 
 
 def hamming_match_path(ctx, nq: int, nt: int) -> int:

@@ -103,9 +103,9 @@ static latch_status upload_scales(latch_context* ctx, const double* scales, int 
 }
 
 // Matching path for AUTO: the tensor-core path once the pair count amortises its
-// operand expansion and merge launches.
-static int choose_match_path(const latch_context*, int64_t nq, int64_t nt) {
-    return nq * nt >= (int64_t(1) << 22) ? LATCH_PATH_TENSOR : LATCH_PATH_POPC;
+// operand expansion and merge launches (threshold set by latch_autotune).
+static int choose_match_path(const latch_context* ctx, int64_t nq, int64_t nt) {
+    return nq * nt >= ctx->tensor_min_pairs ? LATCH_PATH_TENSOR : LATCH_PATH_POPC;
 }
 
 static latch_status validate_triplets(latch_context* ctx, const latch_triplet* t) {

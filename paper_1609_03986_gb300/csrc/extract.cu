@@ -43,7 +43,7 @@ constexpr int kCopyWords = kWin * kRowWords + 4;   // one byte-shifted copy (+4:
 constexpr int kWinWords = 4 * kCopyWords;          // 4 copies
 constexpr int kBucketThreads = 1024;
 constexpr int kMaxSmemCells = 12288;
-constexpr int kItemKps = 16;            // keypoints per work item (block)
+constexpr int kMaxItemKps = 32;         // largest work item (keypoints per block visit)
 
 struct CellGrid {
     int gx, gy;  // cells in x / y (including the margins)
@@ -75,11 +75,12 @@ struct ExtractParams {
     int32_t cell0[NI];    // first entry of image i in the global cell-count scratch
     int32_t count;        // images in this launch
     int32_t nscales;
+    int32_t item_kps;     // keypoints per work item (1 .. kMaxItemKps; tuned)
     TileGeom tg;
 };
 
 // One block per image: counting sort of its keypoints into cells, then its work
-// items (chunks of at most kItemKps keypoints of one cell) are appended to the
+// items (chunks of at most item_kps keypoints of one cell) are appended to the
 // launch's global item list.  counters[0] = number of items (zeroed by the host).
 template <int NI>
 __global__ void __launch_bounds__(kBucketThreads) bucket_kernel(const __grid_constant__ ExtractParams<NI> prm,
@@ -134,7 +135,7 @@ __global__ void __launch_bounds__(kBucketThreads) bucket_kernel(const __grid_con
     for (int c = c0; c < c1; ++c) {
         const int k = cnt[c];
         sum += k;
-        isum += (k + kItemKps - 1) / kItemKps;
+        isum += (k + prm.item_kps - 1) / prm.item_kps;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int incl = sum, iincl = isum;
@@ -173,7 +174,8 @@ __global__ void __launch_bounds__(kBucketThreads) bucket_kernel(const __grid_con
     int irun = s_item_base + iincl - isum + (warp > 0 ? s_ipart[warp - 1] : 0);
     for (int c = c0; c < c1; ++c) {
         const int k = cnt[c];
-        for (int j = 0; j < k; j += kItemKps) items[irun++] = make_int4(img, c, run + j, run + min(j + kItemKps, k));
+        for (int j = 0; j < k; j += prm.item_kps)
+            items[irun++] = make_int4(img, c, run + j, run + min(j + prm.item_kps, k));
         cnt[c] = run;  // becomes the insertion cursor (a position in perm)
         run += k;
     }
@@ -213,7 +215,7 @@ __global__ void __launch_bounds__(kThreads) extract_cells_kernel(
     uint32_t* __restrict__ flags) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ int s_item;
-    __shared__ int4 s_kp[kItemKps];
+    __shared__ int4 s_kp[kMaxItemKps];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     uint32_t* s_win = reinterpret_cast<uint32_t*>(smem);                  // [2][kWinWords]
     uint8_t* s_bits = reinterpret_cast<uint8_t*>(s_win + 2 * kWinWords);  // [2][512] one byte per bit
@@ -454,10 +456,8 @@ static CellGrid cell_grid(const latch_image* img) {
     return g;
 }
 
-static int64_t max_items(int64_t n, const CellGrid& g) {
-    const int64_t ncell = static_cast<int64_t>(g.gx) * g.gy;
-    return (n + kItemKps - 1) / kItemKps + (ncell < n ? ncell : n);
-}
+// Upper bound on the work items of n keypoints for any item size >= 1.
+static int64_t max_items(int64_t n, const CellGrid&) { return n; }
 
 static size_t extract_smem_bytes(const TileGeom& tg) {
     return 128 + static_cast<size_t>(2 * kWinWords) * 4 + 2 * kBits + 16 + 128 + static_cast<size_t>(tg.tw) * tg.th;
@@ -547,6 +547,7 @@ static cudaError_t launch_chunk(const latch_context* ctx, const latch_image* img
     ExtractParams<NI>* prm = new ExtractParams<NI>;
     prm->count = i1 - i0;
     prm->nscales = ctx->nscales;
+    prm->item_kps = ctx->item_kps;
     prm->tg = tg;
     bool global_cells = false;
     int64_t cell0 = 0;

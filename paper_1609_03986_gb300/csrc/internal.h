@@ -54,6 +54,8 @@ struct latch_context {
     uint8_t* d_trip = nullptr;           // 512 * 6 bytes
     uint32_t h_trip_offsets[2 * LATCH_TRIPLETS] = {};
     uint32_t* d_flags = nullptr;         // device error word
+    int32_t item_kps = 16;               // extraction: keypoints per work item (latch_autotune)
+    int64_t tensor_min_pairs = int64_t(1) << 22;  // matching: AUTO uses the tensor path from here
     latch::Scratch scratch[4];           // grow-only scratch regions
     char err[256] = {};
 };

@@ -129,3 +129,24 @@ def test_device_wait_timeout_is_reported(gpu_ctx, triplets):
     img = synth.image(synth.seed(11, 9, synth.KIND_IMAGE), w, h, n_ellipses=5)
     kps = np.array([[60, 45, 3, 1], [10, 10, 30, 2]], np.int32)
     assert np.array_equal(_extract(gpu_ctx, img, w, h, kps), oracle.extract(img, w, h, kps, triplets, synth.SCALES))
+
+
+def test_autotune_changes_speed_not_results(gpu_ctx, triplets):
+    """The autotuner picks a work-item size and a path threshold within range; every
+    item size gives the same descriptors; tuning can be saved and restored."""
+    saved = P.latch_get_tuning(gpu_ctx.handle)
+    try:
+        t = P.latch_autotune(gpu_ctx.handle, 640, 480, 3000, 2000, 2000)
+        assert 1 <= t["item_kps"] <= 32 and t["tensor_min_pairs"] >= 0
+        w, h = 640, 480
+        img = synth.image(synth.seed(11, 20, synth.KIND_IMAGE), w, h, n_ellipses=30)
+        kps = synth.keypoints(synth.seed(11, 20, synth.KIND_KEYPOINTS), w, h, 900, 8, True, 3)
+        want = oracle.extract(img, w, h, kps, triplets, synth.SCALES)
+        for item in (1, 5, 16, 32):
+            P.latch_set_tuning(gpu_ctx.handle, item, t["tensor_min_pairs"])
+            assert np.array_equal(_extract(gpu_ctx, img, w, h, kps), want), item
+        with pytest.raises(P.LatchError):
+            P.latch_set_tuning(gpu_ctx.handle, 33, 0)
+    finally:
+        P.latch_set_tuning(gpu_ctx.handle, saved["item_kps"], saved["tensor_min_pairs"])
+    gpu_ctx.check()

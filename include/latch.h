@@ -304,6 +304,15 @@ latch_status latch_check(latch_context *ctx);
  * LATCH_ETIMEOUT (and clears the flag); the context stays usable. */
 latch_status latch_selftest_wait_timeout(latch_context *ctx, int32_t limit_us, latch_stream_t stream);
 
+/* Tracing (no counterpart in the paper): with max_records > 0, each
+ * latch_batch_run on this context records CUDA events on its stream before
+ * extraction, between extraction and matching, and after matching, until
+ * max_records runs are recorded (0 disables and frees the events).  Synchronous. */
+latch_status latch_trace_enable(latch_context *ctx, int32_t max_records);
+/* Waits for the recorded runs, writes per run [extraction ms, matching ms] into
+ * out_ms (2 * capacity floats), the number of runs into *n, and starts over. */
+latch_status latch_trace_collect(latch_context *ctx, float *out_ms, int32_t capacity, int32_t *n);
+
 /* One-line description of the last error on `ctx` (or of the last failed
  * latch_context_create when ctx is NULL).  Valid until the next call. */
 const char *latch_last_error(const latch_context *ctx);

@@ -94,6 +94,8 @@ EXPORTS = [
     ("hamming_match", ctypes.c_int, [_P, _P, _I32, _P, _I32, _I32, _F, _P, _I32, _P]),
     ("latch_check", ctypes.c_int, [_P]),
     ("latch_selftest_wait_timeout", ctypes.c_int, [_P, _I32, _P]),
+    ("latch_trace_enable", ctypes.c_int, [_P, _I32]),
+    ("latch_trace_collect", ctypes.c_int, [_P, _P, _I32, ctypes.POINTER(_I32)]),
     ("latch_kernel_launches", ctypes.c_uint64, []),
     ("hamming_match_path", ctypes.c_int32, [_P, _I64, _I64]),
     ("latch_autotune", ctypes.c_int, [_P, ctypes.POINTER(latch_tune_shape), ctypes.POINTER(latch_tuning)]),
@@ -386,6 +388,18 @@ def hamming_match_path(ctx, nq: int, nt: int) -> int:
 
 def latch_selftest_wait_timeout(ctx, limit_us: int, stream: int = 0) -> None:
     _check(ctx, library().latch_selftest_wait_timeout(ctx, limit_us, stream))
+
+
+def latch_trace_enable(ctx, max_records: int) -> None:
+    _check(ctx, library().latch_trace_enable(ctx, max_records))
+
+
+def latch_trace_collect(ctx, capacity: int) -> np.ndarray:
+    """(n, 2) float32 array of [extraction ms, matching ms] per traced batch run."""
+    out = np.zeros((max(capacity, 1), 2), np.float32)
+    n = ctypes.c_int32()
+    _check(ctx, library().latch_trace_collect(ctx, out.ctypes.data, capacity, ctypes.byref(n)))
+    return out[:n.value]
 
 
 def latch_kernel_launches() -> int:

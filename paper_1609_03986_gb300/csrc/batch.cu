@@ -111,6 +111,8 @@ extern "C" latch_status latch_batch_run(latch_context* ctx, const latch_batch_de
     if (st != LATCH_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     uint8_t* base = static_cast<uint8_t*>(scratch);
+    cudaEvent_t* ev = (ctx->trace_ev && ctx->trace_n < ctx->trace_cap) ? ctx->trace_ev + 3 * ctx->trace_n++ : nullptr;
+    if (ev) cudaEventRecord(ev[0], s);
     if (plan.total_kp > 0) {
         st = cuda_check(ctx,
                         launch_extract_batch(ctx, b->h_images, plan.kp0.data(), plan.n.data(), b->n_images, b->d_kps,
@@ -118,7 +120,11 @@ extern "C" latch_status latch_batch_run(latch_context* ctx, const latch_batch_de
                         "batched extraction launch");
         if (st != LATCH_OK) return st;
     }
-    if (b->n_pairs == 0 || plan.total_out == 0) return LATCH_OK;
+    if (ev) cudaEventRecord(ev[1], s);
+    if (b->n_pairs == 0 || plan.total_out == 0) {
+        if (ev) cudaEventRecord(ev[2], s);
+        return LATCH_OK;
+    }
     uint8_t* mbase = base + plan.ext_bytes;
     const size_t exp_bytes = (static_cast<size_t>(plan.total_kp) * 512 + 1023) / 1024 * 1024;
     st = cuda_check(ctx,
@@ -147,5 +153,6 @@ extern "C" latch_status latch_batch_run(latch_context* ctx, const latch_batch_de
                         "batched match launch");
     }
     delete mb;
+    if (ev) cudaEventRecord(ev[2], s);
     return st;
 }

@@ -185,8 +185,51 @@ latch_status latch_context_create(int device, latch_context** out) {
     return LATCH_OK;
 }
 
+latch_status latch_trace_enable(latch_context* ctx, int32_t max_records) {
+    if (!ctx || max_records < 0 || max_records > (1 << 20)) return fail(ctx, LATCH_EINVAL, "bad trace capacity");
+    LATCH_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    if (ctx->trace_ev) {
+        cudaDeviceSynchronize();
+        for (int i = 0; i < 3 * ctx->trace_cap; ++i) cudaEventDestroy(ctx->trace_ev[i]);
+        delete[] ctx->trace_ev;
+        ctx->trace_ev = nullptr;
+        ctx->trace_cap = ctx->trace_n = 0;
+    }
+    if (max_records == 0) return LATCH_OK;
+    ctx->trace_ev = new (std::nothrow) cudaEvent_t[3 * static_cast<size_t>(max_records)];
+    if (!ctx->trace_ev) return fail(ctx, LATCH_ENOMEM, "host allocation failed");
+    for (int i = 0; i < 3 * max_records; ++i) {
+        const cudaError_t e = cudaEventCreate(&ctx->trace_ev[i]);
+        if (e != cudaSuccess) {
+            for (int j = 0; j < i; ++j) cudaEventDestroy(ctx->trace_ev[j]);
+            delete[] ctx->trace_ev;
+            ctx->trace_ev = nullptr;
+            return cuda_check(ctx, e, "cudaEventCreate");
+        }
+    }
+    ctx->trace_cap = max_records;
+    ctx->trace_n = 0;
+    return LATCH_OK;
+}
+
+latch_status latch_trace_collect(latch_context* ctx, float* out_ms, int32_t capacity, int32_t* n) {
+    if (!ctx || !n || (capacity > 0 && !out_ms)) return fail(ctx, LATCH_EINVAL, "NULL argument");
+    LATCH_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    const int32_t m = ctx->trace_n < capacity ? ctx->trace_n : capacity;
+    for (int i = 0; i < m; ++i) {
+        cudaEvent_t* ev = ctx->trace_ev + 3 * i;
+        LATCH_CUDA_TRY(ctx, cudaEventSynchronize(ev[2]));
+        LATCH_CUDA_TRY(ctx, cudaEventElapsedTime(&out_ms[2 * i], ev[0], ev[1]));
+        LATCH_CUDA_TRY(ctx, cudaEventElapsedTime(&out_ms[2 * i + 1], ev[1], ev[2]));
+    }
+    *n = m;
+    ctx->trace_n = 0;
+    return LATCH_OK;
+}
+
 latch_status latch_context_destroy(latch_context* ctx) {
     if (!ctx) return LATCH_OK;
+    latch_trace_enable(ctx, 0);
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     if (ctx->d_tile_offsets) cudaFree(ctx->d_tile_offsets);

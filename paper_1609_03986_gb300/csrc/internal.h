@@ -55,6 +55,10 @@ struct latch_context {
     uint32_t h_trip_offsets[2 * LATCH_TRIPLETS] = {};
     uint32_t* d_flags = nullptr;         // device error word
     int32_t item_kps = 16;               // extraction: keypoints per work item (latch_autotune)
+    // tracing (latch_trace_enable): per batch run, events before extraction, between
+    // extraction and matching, and after matching
+    cudaEvent_t* trace_ev = nullptr;
+    int32_t trace_cap = 0, trace_n = 0;
     int64_t tensor_min_pairs = int64_t(1) << 22;  // matching: AUTO uses the tensor path from here
     latch::Scratch scratch[4];           // grow-only scratch regions
     char err[256] = {};

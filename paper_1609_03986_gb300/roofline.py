@@ -58,27 +58,27 @@ def traffic(kernel: str, source: str):
     return None
 
 
-def report(extract_ms: float, match_ms: float, n0: int, n1: int, path: str, peaks_path: str):
+def report(extract_ms: float, n_desc: int, match_ms: float, pairs: int, path: str, peaks_path: str):
+    """Roofline of the dominant phase (the other under "other").  extract_ms: time of
+    the extraction launches over n_desc descriptors; match_ms: time of the matching
+    launches over `pairs` pairs."""
     peaks, kind = _peaks(peaks_path)
     clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    # extraction: one launch per image; average over both
-    ext_units = (n0 + n1) / 2
-    ext = {"bound": "alu", "achieved": EXTRACT_OPS_PER_DESC * ext_units / (extract_ms / 1e3) / 1e12,
+    ext = {"bound": "alu", "achieved": EXTRACT_OPS_PER_DESC * n_desc / (extract_ms / 1e3) / 1e12,
            "peak": SMS * INT_LANES_PER_SM * clk / 1e12, "unit": "Tops/s (int32)",
-           "kernel": "extract", "traffic": traffic("extract", "extract.cu")}
-    pairs = n0 * n1
+           "kernel": "extract", "units_per_launch": n_desc, "traffic": traffic("extract", "extract.cu")}
     if path == "tensor":
         mat = {"bound": "tensor", "achieved": TENSOR_FLOP_PER_PAIR * pairs / (match_ms / 1e3) / 1e12,
                "peak": 2.0 * float(peaks["bf16_tflops"]), "unit": "TFLOP/s (fp8 e4m3)", "kernel": "match_tensor",
-               "traffic": traffic("match_tensor", "match_tc.cu")}
+               "units_per_launch": pairs, "traffic": traffic("match_tensor", "match_tc.cu")}
     else:
         mat = {"bound": "alu", "achieved": POPC_PER_PAIR * pairs / (match_ms / 1e3) / 1e12,
                "peak": SMS * POPC_PER_SM * clk / 1e12, "unit": "Tpopc/s", "kernel": "match_popc",
-               "traffic": traffic("match_popc", "match_popc.cu")}
+               "units_per_launch": pairs, "traffic": traffic("match_popc", "match_popc.cu")}
     for r in (ext, mat):
         r["frac"] = r["achieved"] / r["peak"]
         r["peak_source"] = f"{kind} (MEASURED_PEAKS.json clock / bf16)" if kind == "measured" else "fallback"
-    dominant = ext if extract_ms * 2 >= match_ms else mat
+    dominant = ext if extract_ms >= match_ms else mat
     out = dict(dominant)
     out["other"] = mat if dominant is ext else ext
     return out

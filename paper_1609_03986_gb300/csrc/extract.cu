@@ -102,9 +102,11 @@ __global__ void __launch_bounds__(kBucketThreads) bucket_kernel(const __grid_con
         for (int c = threadIdx.x; c < ncell; c += blockDim.x) cnt[c] = 0;
     __syncthreads();
     bool bad = false;
-    // 8 independent keypoint loads in flight per thread
-    for (int i0 = threadIdx.x; i0 < n; i0 += 8 * blockDim.x) {
-        int cc[8];
+    // the cells of the first 16 * 1024 keypoints stay in registers for the second
+    // pass; 8 independent keypoint loads are in flight per thread
+    constexpr int kCached = 16;
+    int cached[kCached];
+    auto count_cells = [&](int* cc, int i0) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int i = i0 + j * blockDim.x;
@@ -125,6 +127,12 @@ __global__ void __launch_bounds__(kBucketThreads) bucket_kernel(const __grid_con
                 bad |= (cc[j] == -2);
             }
         }
+    };
+    count_cells(cached, threadIdx.x);
+    count_cells(cached + 8, threadIdx.x + 8 * blockDim.x);
+    for (int i0 = threadIdx.x + kCached * blockDim.x; i0 < n; i0 += 8 * blockDim.x) {
+        int cc[8];
+        count_cells(cc, i0);
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, kFlagBadScale);
     // exclusive scans of the counts and of the work items: each thread sums a
@@ -180,7 +188,10 @@ __global__ void __launch_bounds__(kBucketThreads) bucket_kernel(const __grid_con
         run += k;
     }
     __syncthreads();
-    for (int i0 = threadIdx.x; i0 < n; i0 += 8 * blockDim.x) {
+#pragma unroll
+    for (int j = 0; j < kCached; ++j)
+        if (cached[j] >= 0) perm[atomicAdd(&cnt[cached[j]], 1)] = kp0 + threadIdx.x + j * blockDim.x;
+    for (int i0 = threadIdx.x + kCached * blockDim.x; i0 < n; i0 += 8 * blockDim.x) {
         int cc[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {

@@ -257,7 +257,6 @@ def run_latch(args):
     clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
     clocks.start()
     time.sleep(0.5)  # let the sampler take its first readings
-    P.latch_trace_enable(ctx.handle, args.steps)
     launches0 = P.latch_kernel_launches()
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
     if ws > 1:
@@ -275,6 +274,15 @@ def run_latch(args):
     wall1 = time.perf_counter()
     launches = P.latch_kernel_launches() - launches0
     clk = clocks.stop()
+
+    # per-phase times from the library's own CUDA events, in a separate traced loop
+    # (an event between the extraction and the matching launch would keep the latter
+    # from starting early, so the timed loop above records none)
+    P.latch_trace_enable(ctx.handle, args.steps)
+    for i in range(args.steps):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
     phases = P.latch_trace_collect(ctx.handle, args.steps)
     P.latch_trace_enable(ctx.handle, 0)
 

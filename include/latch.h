@@ -252,7 +252,7 @@ const char *latch_session_last_error(const latch_session *s);
 
 /* ---- Autotuning (tile shapes and path choice, by measurement on this device) ---- */
 typedef struct {
-    int32_t item_kps;           /* extraction: keypoints per work item (block visit), 1..32 */
+    int32_t item_kps;           /* extraction: fewest keypoints per block (sets the grid), 1..32 */
     int64_t tensor_min_pairs;   /* matching: LATCH_PATH_AUTO uses the tensor cores from nq*nt >= this */
 } latch_tuning;
 

@@ -1,10 +1,12 @@
 // Batched extract-then-match (the structure-from-motion shape of Sec. 4-5: many
 // images, each matched against its neighbours).  Enqueues, on one stream:
-//   1. one bucket launch and one persistent extraction launch per 64 images,
-//   2. one expansion of all descriptors to 0/1 E4M3 rows (each image's set is
-//      expanded once, although it serves as query and as train in several pairs),
-//   3. one persistent tensor-core matching launch (plus its merge) per 600 pairs,
-//      whose blocks share the (pair, query tile, train tile) units of all pairs.
+//   1. one bucket launch and one persistent extraction launch per 64 images; the
+//      extraction also writes every descriptor's 0/1 E4M3 row for the tensor
+//      matcher (each image's set once, although it serves as query and as train
+//      in several pairs),
+//   2. one persistent tensor-core matching launch per 512 pairs, whose blocks share
+//      the (pair, query tile, train tile) units of all pairs and combine each query
+//      tile's partial results themselves.
 // Nothing is allocated once latch_reserve_batch has sized the scratch, and nothing
 // synchronises, so the whole sequence can be captured into a CUDA graph.
 #include <cmath>
@@ -21,6 +23,7 @@ namespace {
 struct BatchPlan {
     std::vector<int64_t> kp0, n, out0;
     int64_t total_kp = 0, total_out = 0;
+    int64_t max_tiles = 0;  // query tiles of the largest matching launch
     size_t ext_bytes = 0, match_bytes = 0;
 };
 
@@ -61,6 +64,13 @@ latch_status plan_batch(latch_context* ctx, const latch_batch_desc* b, BatchPlan
     MatchBatch* mb = new (std::nothrow) MatchBatch;
     if (!mb) return fail(ctx, LATCH_ENOMEM, "host allocation failed");
     size_t mbytes = 0;
+    // the arrival counters are sized for every launch first (they precede the records)
+    for (int p0 = 0; p0 < b->n_pairs; p0 += kMaxProblems) {
+        const int p1 = p0 + kMaxProblems < b->n_pairs ? p0 + kMaxProblems : b->n_pairs;
+        int64_t tiles = 0;
+        for (int p = p0; p < p1; ++p) tiles += (plan->n[b->h_pairs[2 * p]] + 127) / 128;
+        if (tiles > plan->max_tiles) plan->max_tiles = tiles;
+    }
     for (int p0 = 0; p0 < b->n_pairs; p0 += kMaxProblems) {
         const int p1 = p0 + kMaxProblems < b->n_pairs ? p0 + kMaxProblems : b->n_pairs;
         for (int p = p0; p < p1; ++p) {
@@ -75,7 +85,7 @@ latch_status plan_batch(latch_context* ctx, const latch_batch_desc* b, BatchPlan
             P.r_milli = 0;
         }
         plan_match_batch(mb, p1 - p0, ctx->sm_count);
-        const size_t need = match_tc_batch_scratch_bytes(plan->total_kp, *mb);
+        const size_t need = match_tc_batch_scratch_bytes(plan->total_kp, *mb, plan->max_tiles);
         if (need > mbytes) mbytes = need;
     }
     delete mb;
@@ -112,25 +122,34 @@ extern "C" latch_status latch_batch_run(latch_context* ctx, const latch_batch_de
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     uint8_t* base = static_cast<uint8_t*>(scratch);
     cudaEvent_t* ev = (ctx->trace_ev && ctx->trace_n < ctx->trace_cap) ? ctx->trace_ev + 3 * ctx->trace_n++ : nullptr;
+    // the extraction also writes the matcher's expanded rows and popcounts when
+    // there is matching to do
+    const bool matching = b->n_pairs > 0 && plan.total_out > 0;
+    uint8_t* mbase = base + plan.ext_bytes;
+    const size_t exp_bytes = (static_cast<size_t>(plan.total_kp) * 512 + 1023) / 1024 * 1024;
     if (ev) cudaEventRecord(ev[0], s);
+    if (matching) {
+        // cleared before the extraction, so that nothing sits between the extraction
+        // and the matching launch; each complete matching launch leaves them zero
+        st = cuda_check(ctx,
+                        cudaMemsetAsync(match_tc_batch_counters(mbase, plan.total_kp), 0,
+                                        match_tc_counter_bytes(plan.max_tiles), s),
+                        "clearing the arrival counters");
+        if (st != LATCH_OK) return st;
+    }
     if (plan.total_kp > 0) {
         st = cuda_check(ctx,
                         launch_extract_batch(ctx, b->h_images, plan.kp0.data(), plan.n.data(), b->n_images, b->d_kps,
-                                             b->d_desc, base, s),
+                                             b->d_desc, base, s, matching ? mbase : nullptr,
+                                             matching ? reinterpret_cast<int32_t*>(mbase + exp_bytes) : nullptr),
                         "batched extraction launch");
         if (st != LATCH_OK) return st;
     }
     if (ev) cudaEventRecord(ev[1], s);
-    if (b->n_pairs == 0 || plan.total_out == 0) {
+    if (!matching) {
         if (ev) cudaEventRecord(ev[2], s);
         return LATCH_OK;
     }
-    uint8_t* mbase = base + plan.ext_bytes;
-    const size_t exp_bytes = (static_cast<size_t>(plan.total_kp) * 512 + 1023) / 1024 * 1024;
-    st = cuda_check(ctx,
-                    launch_expand(b->d_desc, plan.total_kp, mbase, reinterpret_cast<int32_t*>(mbase + exp_bytes), s),
-                    "expansion launch");
-    if (st != LATCH_OK) return st;
     const int32_t r_milli = static_cast<int32_t>(std::round(static_cast<double>(b->ratio) * 1000.0));
     MatchBatch* mb = new (std::nothrow) MatchBatch;
     if (!mb) return fail(ctx, LATCH_ENOMEM, "host allocation failed");
@@ -149,7 +168,8 @@ extern "C" latch_status latch_batch_run(latch_context* ctx, const latch_batch_de
         }
         plan_match_batch(mb, p1 - p0, ctx->sm_count);
         st = cuda_check(ctx,
-                        launch_match_tc_batch(*mb, plan.total_kp, mbase, b->d_matches + plan.out0[p0], ctx->d_flags, s),
+                        launch_match_tc_batch(*mb, plan.total_kp, plan.max_tiles, mbase, b->d_matches + plan.out0[p0],
+                                              ctx->d_flags, s),
                         "batched match launch");
     }
     delete mb;

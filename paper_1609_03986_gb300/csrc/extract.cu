@@ -1,15 +1,18 @@
 // LATCH descriptor extraction (Sec. 3.1 Eq. 1; Sec. 3.2).
 //
-// 1. bucket_kernel (one block): counting sort of the keypoints into 32x32-pixel
-//    image cells.  The cell grid reaches 128 px beyond every border; keypoints
-//    further out have windows wholly outside the image (the window reaches at most
-//    `reach` <= 78 px), whose samples all read 0, so their descriptor is all zeros
-//    and is written here directly.  Keypoints with a scale index outside the scale
-//    table also get zeros and raise the context's device flag.
-// 2. extract_cells_kernel (one block per cell, 8 warps): the image tile under the
-//    cell plus a `reach` halo is staged into shared memory by one TMA 2-D load
-//    (samples outside the image arrive as 0, the border reading).  For each
-//    keypoint of the cell in turn, the block
+// 1. bucket_kernel (one block per image): counting sort of the keypoints into
+//    32x32-pixel image cells; the launch's record array receives one 16-byte record
+//    per keypoint (position, output row, offset table, image), cell by cell.  The
+//    cell grid reaches 128 px beyond every border; keypoints further out have
+//    windows wholly outside the image (the window reaches at most `reach` <= 78
+//    px), whose samples all read 0, so their descriptor is all zeros and is written
+//    here directly.  Keypoints with a scale index outside the scale table also get
+//    zeros and raise the context's device flag.
+// 2. extract_cells_kernel (8 warps per block, four blocks per SM): block b takes
+//    the b-th of G equal shares of the records.  The image tile under a cell plus a
+//    `reach` halo is staged into shared memory by one TMA 2-D load (samples outside
+//    the image arrive as 0, the border reading) whenever the next keypoint lies in
+//    another cell.  For each keypoint in turn, the block
 //      - samples the 48x48 window through the per-(scale, bin) offset table
 //        (nearest pixel; offsets pre-multiplied into tile offsets) and stores it
 //        as 4 byte-shifted copies, so that the 8 bytes holding any 7-pixel patch
@@ -19,7 +22,11 @@
 //        with __dp4a on 4 pixels at a time, all exact in 32-bit integers;
 //      - packs the 32 bits of each warp-group with __ballot_sync (bit t = bit
 //        t % 32 of word t / 32, i.e. bit t % 8 of byte t / 8) and writes the
-//        64-byte descriptor as four 128-bit stores.
+//        64-byte descriptor as four 128-bit stores (the last warp, which builds no
+//        window, does this); when the caller also wants the tensor matcher's
+//        input, it writes the expanded row (byte t = E4M3 1.0 or 0 for bit t) and
+//        the descriptor's popcount as well, so no separate pass over the
+//        descriptors is needed.
 //    Windows are double-buffered so one __syncthreads per keypoint suffices.
 #include <cuda.h>
 
@@ -43,7 +50,7 @@ constexpr int kCopyWords = kWin * kRowWords + 4;   // one byte-shifted copy (+4:
 constexpr int kWinWords = 4 * kCopyWords;          // 4 copies
 constexpr int kBucketThreads = 1024;
 constexpr int kMaxSmemCells = 12288;
-constexpr int kMaxItemKps = 32;         // largest work item (keypoints per block visit)
+constexpr int kRing = 64;               // keypoint records in flight per block (1 KB: four blocks still fit an SM)
 
 struct CellGrid {
     int gx, gy;  // cells in x / y (including the margins)
@@ -75,23 +82,32 @@ struct ExtractParams {
     int32_t cell0[NI];    // first entry of image i in the global cell-count scratch
     int32_t count;        // images in this launch
     int32_t nscales;
-    int32_t item_kps;     // keypoints per work item (1 .. kMaxItemKps; tuned)
     TileGeom tg;
 };
 
-// One block per image: counting sort of its keypoints into cells, then its work
-// items (chunks of at most item_kps keypoints of one cell) are appended to the
-// launch's global item list.  counters[0] = number of items (zeroed by the host).
+// Sorted keypoint record: x, y, output row (the keypoint's index), table (scale *
+// 32 + bin) | launch-local image << 16.
+__device__ __forceinline__ int4 kp_record(const latch_keypoint& kp, int row, int img) {
+    return make_int4(kp.x, kp.y, row, (kp.scale_idx * kBins + (kp.angle_bin & (kBins - 1))) | (img << 16));
+}
+
+// One block per image: counting sort of its keypoints into cells.  The image's
+// keypoints that have a cell take the positions [base, base + count) of the
+// launch's record array, cell by cell (base from an atomic on counters[0], which
+// ends as the launch's number of records; zeroed by the host).
 template <int NI>
 __global__ void __launch_bounds__(kBucketThreads) bucket_kernel(const __grid_constant__ ExtractParams<NI> prm,
                                                                 const latch_keypoint* __restrict__ kps,
-                                                                int* __restrict__ gcount, int4* __restrict__ items,
-                                                                int* __restrict__ counters, int* __restrict__ perm,
-                                                                uint4* __restrict__ out, uint32_t* __restrict__ flags) {
+                                                                int* __restrict__ gcount, int* __restrict__ counters,
+                                                                int4* __restrict__ recs, uint4* __restrict__ out,
+                                                                uint4* __restrict__ exp_out,
+                                                                int32_t* __restrict__ pop_out,
+                                                                uint32_t* __restrict__ flags) {
     extern __shared__ int s_cnt[];
     __shared__ int s_part[kBucketThreads / 32];
-    __shared__ int s_ipart[kBucketThreads / 32];
-    __shared__ int s_item_base;
+    __shared__ int s_base;
+    griddep_wait();
+    griddep_launch_dependents();
     const int img = blockIdx.x;
     const CellGrid g = prm.grid[img];
     const int n = prm.n[img], kp0 = prm.kp0[img];
@@ -102,11 +118,9 @@ __global__ void __launch_bounds__(kBucketThreads) bucket_kernel(const __grid_con
         for (int c = threadIdx.x; c < ncell; c += blockDim.x) cnt[c] = 0;
     __syncthreads();
     bool bad = false;
-    // the cells of the first 16 * 1024 keypoints stay in registers for the second
-    // pass; 8 independent keypoint loads are in flight per thread
-    constexpr int kCached = 16;
-    int cached[kCached];
-    auto count_cells = [&](int* cc, int i0) {
+    // 8 independent keypoint loads in flight per thread
+    for (int i0 = threadIdx.x; i0 < n; i0 += 8 * blockDim.x) {
+        int cc[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int i = i0 + j * blockDim.x;
@@ -124,83 +138,60 @@ __global__ void __launch_bounds__(kBucketThreads) bucket_kernel(const __grid_con
                 d[1] = z;
                 d[2] = z;
                 d[3] = z;
+                if (exp_out) {
+                    uint4* x = exp_out + static_cast<size_t>(kp0 + i) * 32;
+                    for (int q = 0; q < 32; ++q) x[q] = z;
+                    pop_out[kp0 + i] = 0;
+                }
                 bad |= (cc[j] == -2);
             }
         }
-    };
-    count_cells(cached, threadIdx.x);
-    count_cells(cached + 8, threadIdx.x + 8 * blockDim.x);
-    for (int i0 = threadIdx.x + kCached * blockDim.x; i0 < n; i0 += 8 * blockDim.x) {
-        int cc[8];
-        count_cells(cc, i0);
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, kFlagBadScale);
-    // exclusive scans of the counts and of the work items: each thread sums a
-    // contiguous run of cells
+    // exclusive scan of the counts: each thread sums a contiguous run of cells
     const int per = (ncell + blockDim.x - 1) / blockDim.x;
     const int c0 = threadIdx.x * per, c1 = min(c0 + per, ncell);
-    int sum = 0, isum = 0;
-    for (int c = c0; c < c1; ++c) {
-        const int k = cnt[c];
-        sum += k;
-        isum += (k + prm.item_kps - 1) / prm.item_kps;
-    }
+    int sum = 0;
+    for (int c = c0; c < c1; ++c) sum += cnt[c];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int incl = sum, iincl = isum;
+    int incl = sum;
     for (int o = 1; o < 32; o <<= 1) {
         const int v = __shfl_up_sync(0xffffffffu, incl, o);
-        const int w = __shfl_up_sync(0xffffffffu, iincl, o);
-        if (lane >= o) {
-            incl += v;
-            iincl += w;
-        }
+        if (lane >= o) incl += v;
     }
-    if (lane == 31) {
-        s_part[warp] = incl;
-        s_ipart[warp] = iincl;
-    }
+    if (lane == 31) s_part[warp] = incl;
     __syncthreads();
     if (warp == 0) {
         int v = lane < kBucketThreads / 32 ? s_part[lane] : 0;
-        int vi = lane < kBucketThreads / 32 ? s_ipart[lane] : 0;
         for (int o = 1; o < 32; o <<= 1) {
             const int w = __shfl_up_sync(0xffffffffu, v, o);
-            const int wi = __shfl_up_sync(0xffffffffu, vi, o);
-            if (lane >= o) {
-                v += w;
-                vi += wi;
-            }
+            if (lane >= o) v += w;
         }
-        if (lane < kBucketThreads / 32) {
-            s_part[lane] = v;
-            s_ipart[lane] = vi;
-        }
-        if (lane == kBucketThreads / 32 - 1) s_item_base = atomicAdd(&counters[0], vi);
+        if (lane < kBucketThreads / 32) s_part[lane] = v;
+        if (lane == kBucketThreads / 32 - 1) s_base = atomicAdd(&counters[0], v);
     }
     __syncthreads();
-    int run = kp0 + incl - sum + (warp > 0 ? s_part[warp - 1] : 0);
-    int irun = s_item_base + iincl - isum + (warp > 0 ? s_ipart[warp - 1] : 0);
+    int run = s_base + incl - sum + (warp > 0 ? s_part[warp - 1] : 0);
     for (int c = c0; c < c1; ++c) {
         const int k = cnt[c];
-        for (int j = 0; j < k; j += prm.item_kps)
-            items[irun++] = make_int4(img, c, run + j, run + min(j + prm.item_kps, k));
-        cnt[c] = run;  // becomes the insertion cursor (a position in perm)
+        cnt[c] = run;  // becomes the insertion cursor (a record position)
         run += k;
     }
     __syncthreads();
-#pragma unroll
-    for (int j = 0; j < kCached; ++j)
-        if (cached[j] >= 0) perm[atomicAdd(&cnt[cached[j]], 1)] = kp0 + threadIdx.x + j * blockDim.x;
-    for (int i0 = threadIdx.x + kCached * blockDim.x; i0 < n; i0 += 8 * blockDim.x) {
-        int cc[8];
+    // scatter the records (the keypoints are read again: 8 loads in flight)
+    for (int i0 = threadIdx.x; i0 < n; i0 += 8 * blockDim.x) {
+        latch_keypoint kp[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int i = i0 + j * blockDim.x;
-            cc[j] = i < n ? cell_of(kps[kp0 + i], prm.nscales, g) : -3;
+            if (i < n) kp[j] = kps[kp0 + i];
         }
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-            if (cc[j] >= 0) perm[atomicAdd(&cnt[cc[j]], 1)] = kp0 + i0 + j * blockDim.x;
+        for (int j = 0; j < 8; ++j) {
+            const int i = i0 + j * blockDim.x;
+            const int c = i < n ? cell_of(kp[j], prm.nscales, g) : -3;
+            if (c >= 0) recs[atomicAdd(&cnt[c], 1)] = kp_record(kp[j], kp0 + i, img);
+        }
     }
 }
 
@@ -217,16 +208,25 @@ __device__ __forceinline__ void load_table_segment(const int16_t* __restrict__ t
     tw[8] = tc.x; tw[9] = tc.y;
 }
 
-// Persistent: blocks take work items from the launch's queue (counters[1]).
+// Tile key of a record: launch-local image, cell row and column (the record's
+// keypoint has a cell, so x + kMargin and y + kMargin are >= 0).
+__device__ __forceinline__ int tile_key(const int4& r) {
+    return ((r.w >> 16) << 22) | (((r.y + kMargin) / kCell) << 11) | ((r.x + kMargin) / kCell);
+}
+
+// Block b extracts the records [b V / G, (b+1) V / G) of the launch's V records
+// (cell-sorted), one keypoint per step.  Records reach shared memory through a
+// ring filled 32 keypoints ahead by asynchronous copies; the tile under the next
+// keypoint's cell is requested, when the cell changes, right after the barrier of
+// the last keypoint that reads the current tile, so it lands during that
+// keypoint's triplets.
 template <int NI>
-__global__ void __launch_bounds__(kThreads) extract_cells_kernel(
-    const __grid_constant__ ExtractParams<NI> prm, const latch_keypoint* __restrict__ kps,
-    const int* __restrict__ perm, const int4* __restrict__ items, int* __restrict__ counters,
+__global__ void __launch_bounds__(kThreads, 4) extract_cells_kernel(
+    const __grid_constant__ ExtractParams<NI> prm, const int4* __restrict__ recs, const int* __restrict__ counters,
     const int16_t* __restrict__ toff, const uint2* __restrict__ trip_off, uint4* __restrict__ out,
-    uint32_t* __restrict__ flags) {
+    uint4* __restrict__ exp_out, int32_t* __restrict__ pop_out, uint32_t* __restrict__ flags) {
     extern __shared__ uint8_t smem_raw[];
-    __shared__ int s_item;
-    __shared__ int4 s_kp[kMaxItemKps];
+    __shared__ int4 s_rec[kRing];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     uint32_t* s_win = reinterpret_cast<uint32_t*>(smem);                  // [2][kWinWords]
     uint8_t* s_bits = reinterpret_cast<uint8_t*>(s_win + 2 * kWinWords);  // [2][512] one byte per bit
@@ -235,66 +235,68 @@ __global__ void __launch_bounds__(kThreads) extract_cells_kernel(
     uint8_t* s_tile = reinterpret_cast<uint8_t*>(s_bar + 2);
     s_tile = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(s_tile) + 127) & ~uintptr_t(127));
     const TileGeom tg = prm.tg;
-    const int n_items = counters[0];
+    griddep_wait();
+    griddep_launch_dependents();
+    const int nrec = counters[0];
+    const int j0 = static_cast<int>(static_cast<int64_t>(blockIdx.x) * nrec / gridDim.x);
+    const int m = static_cast<int>(static_cast<int64_t>(blockIdx.x + 1) * nrec / gridDim.x) - j0;
+    if (m <= 0) return;
+    const int4* brec = recs + j0;
 
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int kLastWarp = kThreads / 32 - 1;
     if (threadIdx.x == 0) {
         mbar_init(s_bar, 1);
         *s_abort = 0;
         fence_mbar_init();
     }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int t = threadIdx.x; t < m && t < kRing - 32; t += kThreads) s_rec[t] = brec[t];
     // this thread's window-build job (threads 0..143): row by, 16-pixel segment bseg
     const int by = threadIdx.x / 3, bseg = threadIdx.x % 3;
     // this lane's two triplets (slots 64*warp + lane and +32 of the bank-conflict
     // minimising order): patch word offsets and the triplet's bit position
     const uint2 to0 = trip_off[64 * warp + lane];
     const uint2 to1 = trip_off[64 * warp + 32 + lane];
+    __syncthreads();
 
-    for (uint32_t phase = 0;; phase ^= 1) {
-        if (threadIdx.x == 0) s_item = atomicAdd(&counters[1], 1);
-        __syncthreads();
-        const int it = s_item;
-        if (it >= n_items) break;
-        const int4 item = items[it];
-        const int img = item.x, cell = item.y, k0 = item.z, k1 = item.w;
-        const CellGrid g = prm.grid[img];
-        const int cx = cell % g.gx, cy = cell / g.gx;
-        const int ox = cx * kCell - kMargin + tg.mx;  // tile origin in image coordinates
-        const int oy = cy * kCell - kMargin + tg.my;
-        if (threadIdx.x == 0) {
-            mbar_arrive_expect_tx(s_bar, static_cast<uint32_t>(tg.tw * tg.th));
-            tma_load_2d(s_tile, &prm.map[img], ox, oy, s_bar);
-        }
-        // the item's keypoints, while the tile is in flight: (x, y, table, output row)
-        if (threadIdx.x < k1 - k0) {
-            const int pi = perm[k0 + threadIdx.x];
-            const latch_keypoint kp = kps[pi];
-            s_kp[threadIdx.x] = make_int4(kp.x, kp.y, kp.scale_idx * kBins + (kp.angle_bin & (kBins - 1)), pi);
-        }
-        const bool ok = mbar_wait(s_bar, phase, s_abort);
-        if (!__syncthreads_and(ok)) {
-            if (threadIdx.x == 0) {
-                atomicOr(flags, kFlagTimeout);
-                const uint64_t t0 = globaltimer();  // let the copy land before the block exits
-                while (!mbar_try_wait(s_bar, phase) && globaltimer() - t0 < 200000000ull) {
-                }
+    int cur_key = -1, ox = 0, oy = 0;
+    uint32_t tile_par = 0;
+    auto issue_tile = [&](const int4& r) {  // thread 0
+        const int key = tile_key(r);
+        const int img = key >> 22;
+        const int tx = (key & 2047) * kCell - kMargin + tg.mx, ty = ((key >> 11) & 2047) * kCell - kMargin + tg.my;
+        mbar_arrive_expect_tx(s_bar, static_cast<uint32_t>(tg.tw * tg.th));
+        tma_load_2d(s_tile, &prm.map[img], tx, ty, s_bar);
+    };
+    if (threadIdx.x == 0) issue_tile(s_rec[0]);
+
+    // offset-table entries 0..19 of this thread's row segment for the first keypoint
+    // (32-byte aligned: 96*by + 32*bseg bytes); later ones are prefetched one keypoint
+    // ahead, during the previous keypoint's triplets, into the other register set
+    // (the two sets swap roles every keypoint)
+    int32_t ta[10], tb[10];
+    if (threadIdx.x < 144) load_table_segment(toff, s_rec[0].w & 0xffff, by, bseg, ta);
+
+    // One step: build the window of keypoint k from `tw` (prefetching k+1's entries
+    // into `tn`), then, after the barrier, pack keypoint k-1 and evaluate keypoint k's
+    // triplets.  Returns true after the last step.
+    auto step = [&](int k, int32_t (&tw)[10], int32_t (&tn)[10]) -> bool {
+        const int buf = k & 1;
+        bool ok = true;
+        if (k < m) {
+            const int4 r = s_rec[k % kRing];
+            const int key = tile_key(r);
+            if (key != cur_key) {  // block-uniform: a new tile was requested for this keypoint
+                if (threadIdx.x < 144) ok = mbar_wait(s_bar, tile_par, s_abort);
+                tile_par ^= 1;
+                cur_key = key;
+                ox = (key & 2047) * kCell - kMargin + tg.mx;
+                oy = ((key >> 11) & 2047) * kCell - kMargin + tg.my;
             }
-            return;
-        }
-
-        // offset-table entries 0..19 of this thread's row segment for the item's first
-        // keypoint (32-byte aligned: 96*by + 32*bseg bytes); later ones are prefetched
-        // one keypoint ahead, during the previous keypoint's triplets
-        int32_t tw[10], tn[10];
-        if (threadIdx.x < 144) load_table_segment(toff, s_kp[0].z, by, bseg, tw);
-
-        for (int k = k0; k <= k1; ++k) {
-            const int buf = k & 1;
-            if (k < k1 && threadIdx.x < 144) {
+            if (threadIdx.x < 144 && ok) {
                 // ---- sample the window of keypoint k into 4 byte-shifted copies; this
                 // thread: row by, pixels 16*bseg .. 16*bseg+18 ----
-                const int4 kp = s_kp[k - k0];
-                const int base = (kp.y - oy) * tg.tw + (kp.x - ox);
+                const int base = (r.y - oy) * tg.tw + (r.x - ox);
                 uint32_t p[5] = {0, 0, 0, 0, 0};
 #pragma unroll
                 for (int u = 0; u < 19; ++u) {
@@ -313,12 +315,27 @@ __global__ void __launch_bounds__(kThreads) extract_cells_kernel(
                 w[3 * kCopyWords / 4] =
                     make_uint4(__funnelshift_r(p[0], p[1], 24), __funnelshift_r(p[1], p[2], 24),
                                __funnelshift_r(p[2], p[3], 24), __funnelshift_r(p[3], p[4], 24));
-                if (k + 1 < k1) load_table_segment(toff, s_kp[k + 1 - k0].z, by, bseg, tn);
+                if (k + 1 < m) load_table_segment(toff, s_rec[(k + 1) % kRing].w & 0xffff, by, bseg, tn);
             }
-            __syncthreads();
-            if (k > k0 && warp == 0) {
+        }
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0) {
+                atomicOr(flags, kFlagTimeout);
+                const uint64_t t0 = globaltimer();  // let the copy land before the block exits
+                while (!mbar_try_wait(s_bar, tile_par ^ 1) && globaltimer() - t0 < 200000000ull) {
+                }
+            }
+            if (warp == kLastWarp) cp_async_wait_all();
+            return true;
+        }
+        // the tile is free once keypoint k's window is built: request the next cell's
+        if (threadIdx.x == 0 && k + 1 < m && tile_key(s_rec[(k + 1) % kRing]) != cur_key)
+            issue_tile(s_rec[(k + 1) % kRing]);
+        if (warp == kLastWarp) {
+            if (k > 0) {
                 // ---- pack and store the descriptor of keypoint k-1 (all its bits were
-                // written before the barrier above): word w collects bits 32w..32w+31 ----
+                // written before the barrier above; this warp builds no window): word w
+                // collects bits 32w..32w+31 ----
                 const uint8_t* b = s_bits + ((k - 1) & 1) * kBits;
                 uint32_t mine = 0;  // lane w < 16 keeps word w
 #pragma unroll
@@ -331,41 +348,65 @@ __global__ void __launch_bounds__(kThreads) extract_cells_kernel(
                 const uint32_t y = __shfl_sync(0xffffffffu, mine, src + 1);
                 const uint32_t z = __shfl_sync(0xffffffffu, mine, src + 2);
                 const uint32_t v = __shfl_sync(0xffffffffu, mine, src + 3);
-                if (lane < 4) out[static_cast<size_t>(s_kp[k - 1 - k0].w) * 4 + lane] = make_uint4(x, y, z, v);
-            }
-            if (k == k1) break;
-#pragma unroll
-            for (int j = 0; j < 10; ++j) tw[j] = tn[j];
-            // ---- Eq. 1 for this lane's two triplets ----
-            const uint32_t* wb = s_win + buf * kWinWords;
-            uint8_t* bits = s_bits + buf * kBits;
-#pragma unroll
-            for (int gi = 0; gi < 2; ++gi) {
-                const uint2 to = gi == 0 ? to0 : to1;
-                const uint32_t* pa = wb + (to.x & 0xffffu);
-                const uint32_t* p1 = wb + (to.x >> 16);
-                const uint32_t* p2 = wb + (to.y & 0xffffu);
-                uint32_t sa1 = 0, sa2 = 0, s11 = 0, s22 = 0;
-#pragma unroll
-                for (int i = 0; i < 2 * kPatchR + 1; ++i) {
-                    const uint32_t a0 = pa[i * kRowWords], a1 = pa[i * kRowWords + 1];
-                    const uint32_t c0 = p1[i * kRowWords], c1 = p1[i * kRowWords + 1] & 0x00ffffffu;
-                    const uint32_t e0 = p2[i * kRowWords], e1 = p2[i * kRowWords + 1] & 0x00ffffffu;
-                    sa1 = __dp4a(a0, c0, sa1);
-                    sa1 = __dp4a(a1, c1, sa1);
-                    sa2 = __dp4a(a0, e0, sa2);
-                    sa2 = __dp4a(a1, e1, sa2);
-                    s11 = __dp4a(c0, c0, s11);
-                    s11 = __dp4a(c1, c1, s11);
-                    s22 = __dp4a(e0, e0, s22);
-                    s22 = __dp4a(e1, e1, s22);
+                const size_t row = static_cast<size_t>(s_rec[(k - 1) % kRing].z);
+                if (lane < 4) out[row * 4 + lane] = make_uint4(x, y, z, v);
+                if (exp_out) {
+                    // bytes 16*lane .. 16*lane+15 are 0 or 1: times 0x38 gives E4M3 0 / 1.0
+                    const uint4 e = reinterpret_cast<const uint4*>(b)[lane];
+                    exp_out[row * 32 + lane] = make_uint4(e.x * 0x38u, e.y * 0x38u, e.z * 0x38u, e.w * 0x38u);
+                    const int pc = __reduce_add_sync(0xffffffffu, static_cast<uint32_t>(__popc(mine)));
+                    if (lane == 0) pop_out[row] = pc;
                 }
-                // D1 - D2 = sum C1^2 - sum C2^2 - 2 (sum A.C1 - sum A.C2)
-                const int diff = (static_cast<int>(s11) - static_cast<int>(s22)) -
-                                 2 * (static_cast<int>(sa1) - static_cast<int>(sa2));
-                bits[to.y >> 16] = diff > 0 ? 1 : 0;
+            }
+            // ---- record ring: at steps k = 32i the records k+32 .. k+63 are requested
+            // (their slots held k-32 .. k-1, all consumed, the last by the pack above);
+            // at step k+16 this warp waits for them, so the barrier of step k+17
+            // publishes them before step k+31 first reads one
+            if ((k & 31) == 0) {
+                const int t = k + kRing - 32 + lane;
+                if (t < m) cp_async_16(&s_rec[t % kRing], brec + t);
+            } else if ((k & 31) == 16) {
+                cp_async_wait_all();
             }
         }
+        if (k == m) {
+            if (warp == kLastWarp) cp_async_wait_all();
+            return true;
+        }
+        // ---- Eq. 1 for this lane's two triplets ----
+        const uint32_t* wb = s_win + buf * kWinWords;
+        uint8_t* bits = s_bits + buf * kBits;
+#pragma unroll
+        for (int gi = 0; gi < 2; ++gi) {
+            const uint2 to = gi == 0 ? to0 : to1;
+            const uint32_t* pa = wb + (to.x & 0xffffu);
+            const uint32_t* p1 = wb + (to.x >> 16);
+            const uint32_t* p2 = wb + (to.y & 0xffffu);
+            uint32_t sa1 = 0, sa2 = 0, s11 = 0, s22 = 0;
+#pragma unroll
+            for (int i = 0; i < 2 * kPatchR + 1; ++i) {
+                const uint32_t a0 = pa[i * kRowWords], a1 = pa[i * kRowWords + 1];
+                const uint32_t c0 = p1[i * kRowWords], c1 = p1[i * kRowWords + 1] & 0x00ffffffu;
+                const uint32_t e0 = p2[i * kRowWords], e1 = p2[i * kRowWords + 1] & 0x00ffffffu;
+                sa1 = __dp4a(a0, c0, sa1);
+                sa1 = __dp4a(a1, c1, sa1);
+                sa2 = __dp4a(a0, e0, sa2);
+                sa2 = __dp4a(a1, e1, sa2);
+                s11 = __dp4a(c0, c0, s11);
+                s11 = __dp4a(c1, c1, s11);
+                s22 = __dp4a(e0, e0, s22);
+                s22 = __dp4a(e1, e1, s22);
+            }
+            // D1 - D2 = sum C1^2 - sum C2^2 - 2 (sum A.C1 - sum A.C2)
+            const int diff = (static_cast<int>(s11) - static_cast<int>(s22)) -
+                             2 * (static_cast<int>(sa1) - static_cast<int>(sa2));
+            bits[to.y >> 16] = diff > 0 ? 1 : 0;
+        }
+        return false;
+    };
+    for (int k = 0;; k += 2) {
+        if (step(k, ta, tb)) break;
+        if (step(k + 1, tb, ta)) break;
     }
 }
 
@@ -467,9 +508,6 @@ static CellGrid cell_grid(const latch_image* img) {
     return g;
 }
 
-// Upper bound on the work items of n keypoints for any item size >= 1.
-static int64_t max_items(int64_t n, const CellGrid&) { return n; }
-
 static size_t extract_smem_bytes(const TileGeom& tg) {
     return 128 + static_cast<size_t>(2 * kWinWords) * 4 + 2 * kBits + 16 + 128 + static_cast<size_t>(tg.tw) * tg.th;
 }
@@ -491,28 +529,26 @@ static EncodeTiledFn extract_encode_fn() {
     return fn;
 }
 
-// Scratch of one launch over images [i0, i1): counters, cell counts, perm, items.
+// Scratch of one launch over images [i0, i1): sorted keypoint records, counters,
+// cell counts (for grids too large for shared memory).
 struct ChunkLayout {
-    size_t counters, cells, perm, items, total;
-    int64_t ncell, nkp, nitem;
+    size_t recs, counters, cells, total;
+    int64_t ncell, nkp;
 };
 
 static ChunkLayout chunk_layout(const latch_image* imgs, const int64_t* n, int i0, int i1) {
     ChunkLayout l;
     l.ncell = 0;
     l.nkp = 0;
-    l.nitem = 0;
     for (int i = i0; i < i1; ++i) {
         const CellGrid g = cell_grid(&imgs[i]);
         l.ncell += static_cast<int64_t>(g.gx) * g.gy;
         l.nkp += n[i];
-        l.nitem += max_items(n[i], g);
     }
-    l.items = 0;  // int4, 16-byte aligned
-    l.counters = l.items + static_cast<size_t>(l.nitem) * sizeof(int4);
+    l.recs = 0;  // int4, 16-byte aligned
+    l.counters = l.recs + static_cast<size_t>(l.nkp) * sizeof(int4);
     l.cells = l.counters + 16;
-    l.perm = l.cells + static_cast<size_t>(l.ncell) * sizeof(int);
-    l.total = (l.perm + static_cast<size_t>(l.nkp) * sizeof(int) + 255) / 256 * 256;
+    l.total = (l.cells + static_cast<size_t>(l.ncell) * sizeof(int) + 255) / 256 * 256;
     return l;
 }
 
@@ -532,7 +568,7 @@ size_t extract_scratch_bytes(const latch_image* img, int64_t n) { return extract
 template <int NI>
 static cudaError_t launch_chunk(const latch_context* ctx, const latch_image* imgs, const int64_t* kp0,
                                 const int64_t* n, int i0, int i1, const latch_keypoint* d_kps, uint8_t* d_out,
-                                uint8_t* scratch, cudaStream_t stream) {
+                                uint8_t* exp_out, int32_t* pop_out, uint8_t* scratch, cudaStream_t stream) {
     static bool attr = false;
     const TileGeom tg = tile_geom(ctx->reach);
     cudaError_t e;
@@ -550,15 +586,13 @@ static cudaError_t launch_chunk(const latch_context* ctx, const latch_image* img
     EncodeTiledFn enc = extract_encode_fn();
     if (!enc) return cudaErrorNotSupported;
     const ChunkLayout l = chunk_layout(imgs, n, i0, i1);
-    int4* items = reinterpret_cast<int4*>(scratch + l.items);
+    int4* recs = reinterpret_cast<int4*>(scratch + l.recs);
     int* counters = reinterpret_cast<int*>(scratch + l.counters);
     int* cells = reinterpret_cast<int*>(scratch + l.cells);
-    int* perm = reinterpret_cast<int*>(scratch + l.perm);
 
     ExtractParams<NI>* prm = new ExtractParams<NI>;
     prm->count = i1 - i0;
     prm->nscales = ctx->nscales;
-    prm->item_kps = ctx->item_kps;
     prm->tg = tg;
     bool global_cells = false;
     int64_t cell0 = 0;
@@ -590,18 +624,19 @@ static cudaError_t launch_chunk(const latch_context* ctx, const latch_image* img
     e = cudaMemsetAsync(counters, 0, 16, stream);
     if (e == cudaSuccess && global_cells) e = cudaMemsetAsync(cells, 0, sizeof(int) * l.ncell, stream);
     if (e == cudaSuccess) {
-        bucket_kernel<NI><<<i1 - i0, kBucketThreads, bucket_smem, stream>>>(
-            *prm, d_kps, cells, items, counters, perm, reinterpret_cast<uint4*>(d_out), ctx->d_flags);
-        note_launches(1);
-        e = cudaGetLastError();
+        e = launch_chained(bucket_kernel<NI>, dim3(i1 - i0), dim3(kBucketThreads), bucket_smem, stream, *prm,
+                           d_kps, cells, counters, recs, reinterpret_cast<uint4*>(d_out),
+                           reinterpret_cast<uint4*>(exp_out), pop_out, ctx->d_flags);
     }
     if (e == cudaSuccess) {
-        const int64_t grid = l.nitem < 4 * ctx->sm_count ? l.nitem : 4 * ctx->sm_count;
-        extract_cells_kernel<NI><<<static_cast<unsigned>(grid), kThreads, extract_smem_bytes(tg), stream>>>(
-            *prm, d_kps, perm, items, counters, ctx->d_tile_offsets,
-            reinterpret_cast<const uint2*>(ctx->d_trip_offsets), reinterpret_cast<uint4*>(d_out), ctx->d_flags);
-        note_launches(1);
-        e = cudaGetLastError();
+        // the records are split evenly over the blocks, at least item_kps keypoints each
+        const int64_t want = (l.nkp + ctx->item_kps - 1) / ctx->item_kps;
+        const int64_t grid = want < 4 * ctx->sm_count ? want : 4 * ctx->sm_count;
+        e = launch_chained(extract_cells_kernel<NI>, dim3(static_cast<unsigned>(grid)), dim3(kThreads),
+                           extract_smem_bytes(tg), stream, *prm, static_cast<const int4*>(recs),
+                           static_cast<const int*>(counters), ctx->d_tile_offsets,
+                           reinterpret_cast<const uint2*>(ctx->d_trip_offsets), reinterpret_cast<uint4*>(d_out),
+                           reinterpret_cast<uint4*>(exp_out), pop_out, ctx->d_flags);
     }
     delete prm;
     return e;
@@ -609,16 +644,22 @@ static cudaError_t launch_chunk(const latch_context* ctx, const latch_image* img
 
 cudaError_t launch_extract_batch(const latch_context* ctx, const latch_image* imgs, const int64_t* kp0,
                                  const int64_t* n, int count, const latch_keypoint* d_kps, uint8_t* d_out,
-                                 void* scratch, cudaStream_t stream) {
+                                 void* scratch, cudaStream_t stream, uint8_t* exp_out, int32_t* pop_out) {
     uint8_t* base = static_cast<uint8_t*>(scratch);
     for (int i0 = 0; i0 < count; i0 += kBatchImages) {
         const int i1 = i0 + kBatchImages < count ? i0 + kBatchImages : count;
         int64_t nk = 0;
         for (int i = i0; i < i1; ++i) nk += n[i];
         if (nk > 0) {
+            // the kernel parameters hold one tensor map per image: the smallest
+            // instance that fits keeps the launch's parameter block small
+            const int ni = i1 - i0;
             const cudaError_t e =
-                (i1 - i0 == 1) ? launch_chunk<1>(ctx, imgs, kp0, n, i0, i1, d_kps, d_out, base, stream)
-                               : launch_chunk<kBatchImages>(ctx, imgs, kp0, n, i0, i1, d_kps, d_out, base, stream);
+                ni == 1    ? launch_chunk<1>(ctx, imgs, kp0, n, i0, i1, d_kps, d_out, exp_out, pop_out, base, stream)
+                : ni <= 4  ? launch_chunk<4>(ctx, imgs, kp0, n, i0, i1, d_kps, d_out, exp_out, pop_out, base, stream)
+                : ni <= 16 ? launch_chunk<16>(ctx, imgs, kp0, n, i0, i1, d_kps, d_out, exp_out, pop_out, base, stream)
+                           : launch_chunk<kBatchImages>(ctx, imgs, kp0, n, i0, i1, d_kps, d_out, exp_out, pop_out,
+                                                        base, stream);
             if (e != cudaSuccess) return e;
         }
         base += chunk_layout(imgs, n, i0, i1).total;
@@ -629,7 +670,7 @@ cudaError_t launch_extract_batch(const latch_context* ctx, const latch_image* im
 cudaError_t launch_extract(const latch_context* ctx, const latch_image* img, const latch_keypoint* d_kps, int32_t n,
                            uint8_t* d_out, void* scratch, cudaStream_t stream) {
     const int64_t kp0 = 0, nn = n;
-    return launch_extract_batch(ctx, img, &kp0, &nn, 1, d_kps, d_out, scratch, stream);
+    return launch_extract_batch(ctx, img, &kp0, &nn, 1, d_kps, d_out, scratch, stream, nullptr, nullptr);
 }
 
 }  // namespace latch

@@ -54,7 +54,7 @@ struct latch_context {
     uint8_t* d_trip = nullptr;           // 512 * 6 bytes
     uint32_t h_trip_offsets[2 * LATCH_TRIPLETS] = {};
     uint32_t* d_flags = nullptr;         // device error word
-    int32_t item_kps = 16;               // extraction: keypoints per work item (latch_autotune)
+    int32_t item_kps = 16;               // extraction: fewest keypoints per block (latch_autotune)
     // tracing (latch_trace_enable): per batch run, events before extraction, between
     // extraction and matching, and after matching
     cudaEvent_t* trace_ev = nullptr;
@@ -76,14 +76,38 @@ latch_status scratch_reserve(latch_context* ctx, int slot, size_t bytes, void** 
 // Counts kernel launches made by the library (latch_kernel_launches()).
 void note_launches(int count);
 
+// Launches `kernel` so that it may start while the previous kernel on the stream
+// is still running (programmatic dependent launch).  Every kernel launched this way
+// executes griddepcontrol.wait before it reads or writes global memory that earlier
+// work on the stream may touch, so the stream order of the results is unchanged;
+// what overlaps is the launch and the kernel's shared-memory / barrier prologue.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_chained(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                           Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    note_launches(1);
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Kernel launchers (one per .cu file); return cudaGetLastError() of the launch.
 cudaError_t launch_extract(const latch_context* ctx, const latch_image* img, const latch_keypoint* d_kps, int32_t n,
                            uint8_t* d_out, void* scratch, cudaStream_t stream);
 size_t extract_scratch_bytes(const latch_image* img, int64_t n);
 // Images [0, count) with keypoints d_kps[kp0[i] .. kp0[i] + n[i]) -> d_out rows at the same positions.
+// When exp_out is not NULL, row r of the tensor matcher's input (512 bytes, E4M3 0 / 1.0 per bit)
+// and pop_out[r] (the descriptor's popcount) are written as well.
 cudaError_t launch_extract_batch(const latch_context* ctx, const latch_image* imgs, const int64_t* kp0,
                                  const int64_t* n, int count, const latch_keypoint* d_kps, uint8_t* d_out,
-                                 void* scratch, cudaStream_t stream);
+                                 void* scratch, cudaStream_t stream, uint8_t* exp_out, int32_t* pop_out);
 size_t extract_batch_scratch_bytes(const latch_image* imgs, const int64_t* n, int count);
 
 cudaError_t launch_match_popc(const latch_context* ctx, const uint8_t* q, int32_t nq, const uint8_t* t, int32_t nt,

@@ -5,7 +5,7 @@
 // from p.unit0, and all units are split into G contiguous ranges, range c =
 // [start(c), start(c+1)) with start(c) = floor(c * U / G).  Every block writes, for
 // each query tile it touches, the two smallest keys of each query row over its
-// train tiles ("partial records", slot = tile index - first tile of the block).
+// train tiles ("partial records", slot = tile index + block index).
 // The merge combines the records of a row.  Keys are (distance << 32) | train
 // index, so the minimum of unique keys is the nearest train descriptor with ties
 // resolved to the lowest index (Sec. 4 matching; tie and ratio readings in latch.h).
@@ -32,12 +32,17 @@ struct MatchProblem {
     int32_t r_milli;  // ratio test threshold, rha(1000 * ratio)
 };
 
-struct MatchBatch {
+// A launch's problem table, passed as a kernel parameter; NP is the capacity (the
+// launcher picks the smallest instance that holds the batch, so a single problem
+// costs ~100 bytes of parameters rather than the full table).
+template <int NP>
+struct MatchBatchT {
     int32_t count;
-    int32_t pad;
-    int64_t units, grid, smax, queries;
-    MatchProblem p[kMaxProblems];
+    int32_t tiles;  // query tiles over all problems (sum of mt)
+    int64_t units, grid, queries;
+    MatchProblem p[NP];
 };
+using MatchBatch = MatchBatchT<kMaxProblems>;
 
 __host__ __device__ __forceinline__ int64_t split_start(int64_t c, int64_t units, int64_t grid) {
     return (c * units) / grid;
@@ -58,15 +63,23 @@ __device__ __forceinline__ void top2_insert_u64(uint64_t key, uint64_t& k1, uint
 }
 
 void plan_match_batch(MatchBatch* b, int count, int64_t max_grid);
-size_t match_tc_batch_scratch_bytes(int64_t rows, const MatchBatch& b);
+// Scratch of the batched layout [expanded rows][popcounts][arrival counters for
+// counter_tiles query tiles][partial records]; counter_tiles >= b.tiles.
+size_t match_tc_batch_scratch_bytes(int64_t rows, const MatchBatch& b, int64_t counter_tiles);
+int32_t* match_tc_batch_counters(void* scratch, int64_t rows);
 size_t match_tc_partial_bytes(const MatchBatch& b);
-// Scratch layout [expanded rows][popcounts][partials]; the expanded rows and
-// popcounts of every problem's query and train sets must be filled already.
-cudaError_t launch_match_tc_batch(const MatchBatch& b, int64_t rows, void* scratch, latch_match* out,
-                                  uint32_t* flags, cudaStream_t stream);
-// Same with explicit buffers: `exp` holds `rows` expanded rows, `pop` their popcounts.
+size_t match_tc_counter_bytes(int64_t tiles);
+// The batched layout: the expanded rows and popcounts of every problem's query and
+// train sets must be filled already, and the arrival counters zero (a complete
+// launch leaves them zero, so consecutive launches need one clearing).
+cudaError_t launch_match_tc_batch(const MatchBatch& b, int64_t rows, int64_t counter_tiles, void* scratch,
+                                  latch_match* out, uint32_t* flags, cudaStream_t stream);
+// Same with explicit buffers: `exp` holds `rows` expanded rows, `pop` their
+// popcounts, `partials` match_tc_partial_bytes(b) of scratch, `tile_cnt` b.tiles
+// zero counters (NULL: combine the records in a separate pass).
 cudaError_t launch_match_tc_rows(const MatchBatch& b, const uint8_t* exp, int64_t rows, const int32_t* pop,
-                                 uint64_t* partials, latch_match* out, uint32_t* flags, cudaStream_t stream);
+                                 uint64_t* partials, int32_t* tile_cnt, latch_match* out, uint32_t* flags,
+                                 cudaStream_t stream);
 cudaError_t launch_expand(const uint8_t* desc, int64_t n, uint8_t* out, int32_t* pop, cudaStream_t stream);
 size_t match_tc_scratch_bytes_sms(int64_t sms, int64_t nq, int64_t nt);
 

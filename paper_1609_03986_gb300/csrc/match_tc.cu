@@ -22,13 +22,18 @@
 //              ((popc(t) - 2*dot + 512) << 8 | column) formed exactly in fp32 by
 //              one FMA, four interleaved min / second-min chains with FMNMX; the tile's two best are
 //              merged into the row's (distance << 32 | index) keys, and when the
-//              block leaves a query tile the row's two keys go to a partial record.
-// match_merge_kernel combines the partial records of every query row (ties to the
-// lowest train index, ratio test).  All mbarrier waits are bounded (sm103.h); on a
-// timeout the block raises the device flag, drains its copies and MMAs, frees TMEM.
+//              block leaves a query tile the row's two keys go to a partial record;
+//              the last block to leave a tile (a per-tile arrival counter) combines
+//              the records of its rows and writes their matches (ties to the lowest
+//              train index, ratio test).
+// match_merge_kernel does the same combination as a separate pass; it serves the
+// batches in which some problem has queries but an empty train set (no unit, so no
+// block visits its tiles).  All mbarrier waits are bounded (sm103.h); on a timeout
+// the block raises the device flag, drains its copies and MMAs, frees TMEM.
 #include <cuda.h>
 
 #include <cmath>
+#include <new>
 
 #include "match_common.cuh"
 #include "sm103.h"
@@ -54,6 +59,9 @@ constexpr int kEpiThreads = 256;
 constexpr int kTmemCols = 512;  // two 256-column accumulators
 constexpr uint32_t kIdesc = idesc_e4m3_f32(kRowsA, kColsB);
 
+// Barrier of the 256 epilogue threads (named barrier 1).
+__device__ __forceinline__ void group_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
 // AND of `v` over the 256 epilogue threads (named barrier 1).
 __device__ __forceinline__ bool group_all(bool v) {
     uint32_t r;
@@ -75,7 +83,7 @@ struct Smem {
     static constexpr int cvec = b + kStages * kStageBytes;             // float [2][kColsB]
     static constexpr int bars = cvec + 2 * kColsB * 4;                 // uint64 barriers
     static constexpr int nbars = 2 * kStages + 2 + 4 + 1;
-    static constexpr int misc = bars + nbars * 8;                      // tmem base, abort flag
+    static constexpr int misc = bars + nbars * 8;                      // tmem base, abort flag, last-arrival flag
     static constexpr int total = misc + 16;
 };
 constexpr int kSmemBytes = Smem::total + 1024;
@@ -88,7 +96,8 @@ struct UnitIter {
     int p;
     int32_t m, n;
     int64_t u, u_end;
-    __device__ __forceinline__ void init(const MatchBatch& b, int64_t u0, int64_t u1) {
+    template <class B>
+    __device__ __forceinline__ void init(const B& b, int64_t u0, int64_t u1) {
         p = 0;
         while (p + 1 < b.count && b.p[p + 1].unit0 <= u0) ++p;
         const int64_t r = u0 - b.p[p].unit0;
@@ -97,11 +106,14 @@ struct UnitIter {
         u = u0;
         u_end = u1;
     }
-    __device__ __forceinline__ int64_t g(const MatchBatch& b) const { return b.p[p].g0 + m; }
-    __device__ __forceinline__ bool last_of_tile(const MatchBatch& b) const {
+    template <class B>
+    __device__ __forceinline__ int64_t g(const B& b) const { return b.p[p].g0 + m; }
+    template <class B>
+    __device__ __forceinline__ bool last_of_tile(const B& b) const {
         return u + 1 >= u_end || n + 1 == b.p[p].ntl;
     }
-    __device__ __forceinline__ void next(const MatchBatch& b) {
+    template <class B>
+    __device__ __forceinline__ void next(const B& b) {
         ++u;
         if (++n == b.p[p].ntl) {
             n = 0;
@@ -114,10 +126,51 @@ struct UnitIter {
     }
 };
 
+// Combines the partial records of row r of query tile (problem P, tile m, global
+// index g) over the blocks that own the tile's units.
+template <class B>
+__device__ __forceinline__ void combine_row(const B& b, const MatchProblem& P, int64_t m, int64_t g, int r,
+                                            const uint64_t* partials, uint64_t& k1, uint64_t& k2) {
+    const int64_t ua = P.unit0 + m * P.ntl, ub = ua + P.ntl - 1;
+    const int64_t clo = split_owner(ua, b.units, b.grid);
+    const int64_t chi = split_owner(ub, b.units, b.grid);
+    for (int64_t c = clo; c <= chi; ++c) {
+        const uint64_t* rec = partials + ((g + c) * kRowsP + r) * 2;
+        top2_insert_u64(__ldcg(rec), k1, k2);
+        top2_insert_u64(__ldcg(rec + 1), k1, k2);
+        const uint64_t* rec2 = rec + 2 * kRowsQ;  // the row's other column half
+        top2_insert_u64(__ldcg(rec2), k1, k2);
+        top2_insert_u64(__ldcg(rec2 + 1), k1, k2);
+    }
+}
+
+// The output record of a query from its two best keys (Sec. 4 ratio test).
+__device__ __forceinline__ latch_match final_match(uint64_t k1, uint64_t k2, int k, int r_milli) {
+    latch_match mres;
+    mres.idx1 = k1 == kNoKey ? -1 : static_cast<int32_t>(k1 & 0xffffffffu);
+    mres.dist1 = k1 == kNoKey ? 0xffff : static_cast<uint16_t>(k1 >> 32);
+    const bool has2 = k == 2 && k2 != kNoKey;
+    mres.idx2 = has2 ? static_cast<int32_t>(k2 & 0xffffffffu) : -1;
+    mres.dist2 = has2 ? static_cast<uint16_t>(k2 >> 32) : 0xffff;
+    if (k1 == kNoKey)
+        mres.accepted = 0;
+    else if (k == 1)
+        mres.accepted = 1;
+    else
+        mres.accepted = (1000ll * mres.dist1 < static_cast<long long>(r_milli) * mres.dist2) ? 1 : 0;
+    mres.pad[0] = mres.pad[1] = mres.pad[2] = 0;
+    return mres;
+}
+
+// tile_cnt: per-query-tile arrival counters, zero at launch and zero again after a
+// complete launch; NULL = leave the combination to match_merge_kernel.
+template <int NP>
 __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_constant__ CUtensorMap tm,
-                                                              const __grid_constant__ MatchBatch batch,
+                                                              const __grid_constant__ MatchBatchT<NP> batch,
                                                               const int32_t* __restrict__ pop,
                                                               uint64_t* __restrict__ partials,
+                                                              int32_t* __restrict__ tile_cnt,
+                                                              latch_match* __restrict__ out,
                                                               uint32_t* __restrict__ flags) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -134,6 +187,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
     uint64_t* mma_done = a_full + 6;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + Smem::misc);
     volatile int* abort = reinterpret_cast<volatile int*>(smem + Smem::misc + 4);
+    volatile int* last_arrival = reinterpret_cast<volatile int*>(smem + Smem::misc + 8);
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -164,6 +218,9 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    // everything above touched only this block's shared memory and TMEM
+    griddep_wait();
+    griddep_launch_dependents();
 
     if (warp == 0) {
         // ---------------- TMA producer ----------------
@@ -284,7 +341,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
         uint32_t acc_par[2] = {0, 0};
         uint64_t k1 = kNoKey, k2 = kNoKey;
         int32_t pq = 0;
-        int64_t prev_g = -1, g_first = -1;
+        int64_t prev_g = -1;
         int i = 0;
         for (int64_t u = u0; u < u1; ++u, ++i, it.next(batch)) {
             const MatchProblem& P = batch.p[it.p];
@@ -295,7 +352,6 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                 const int64_t row = m * kRowsQ + row_in_tile;
                 pq = row < P.nq ? pop[P.q_row0 + row] : 0;
                 k1 = k2 = kNoKey;
-                if (g_first < 0) g_first = g;
                 prev_g = g;
             }
             {
@@ -360,9 +416,30 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                 }
             }
             if (it.last_of_tile(batch)) {
-                uint64_t* rec = partials + ((c * batch.smax + (g - g_first)) * kRowsP + prow) * 2;
+                uint64_t* rec = partials + ((g + c) * kRowsP + prow) * 2;
                 rec[0] = k1;
                 rec[1] = k2;
+                if (tile_cnt) {
+                    // publish the records; the last owner of the tile to arrive combines them
+                    __threadfence();
+                    group_sync();
+                    if (et == 0) {
+                        const int64_t ua = P.unit0 + m * P.ntl;
+                        const int64_t owners = split_owner(ua + P.ntl - 1, batch.units, batch.grid) -
+                                               split_owner(ua, batch.units, batch.grid) + 1;
+                        const bool last = atomicAdd(&tile_cnt[g], 1) == owners - 1;
+                        if (last) tile_cnt[g] = 0;  // no other block touches it again: leave it zero
+                        *last_arrival = last;
+                    }
+                    group_sync();
+                    if (*last_arrival && half == 0) {
+                        __threadfence();
+                        const int64_t row = m * kRowsQ + row_in_tile;
+                        uint64_t f1 = kNoKey, f2 = kNoKey;
+                        combine_row(batch, P, m, g, row_in_tile, partials, f1, f2);
+                        if (row < P.nq) out[P.out0 + row] = final_match(f1, f2, P.k, P.r_milli);
+                    }
+                }
             }
         }
     }
@@ -375,19 +452,11 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
     }
 }
 
-// Index of the problem containing global unit u (largest p with unit0 <= u).
-__device__ __forceinline__ int problem_of_unit(const MatchBatch& b, int64_t u) {
-    int lo = 0, hi = b.count - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (b.p[mid].unit0 <= u) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
 // Combine the partial records of every query row; write one latch_match per query.
-__global__ void match_merge_kernel(const __grid_constant__ MatchBatch batch, const uint64_t* __restrict__ partials,
-                                   latch_match* __restrict__ out) {
+template <int NP>
+__global__ void match_merge_kernel(const __grid_constant__ MatchBatchT<NP> batch,
+                                   const uint64_t* __restrict__ partials, latch_match* __restrict__ out) {
+    griddep_wait();
     const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (q >= batch.queries) return;
     int lo = 0, hi = batch.count - 1;  // problem: largest p with out0 <= q
@@ -396,47 +465,20 @@ __global__ void match_merge_kernel(const __grid_constant__ MatchBatch batch, con
         if (batch.p[mid].out0 <= q) lo = mid; else hi = mid - 1;
     }
     const MatchProblem& P = batch.p[lo];
-    const int k = P.k, r_milli = P.r_milli;
     const int64_t ql = q - P.out0;
     uint64_t k1 = kNoKey, k2 = kNoKey;
     if (P.ntl > 0) {
         const int64_t m = ql / kRowsQ;
-        const int r = static_cast<int>(ql % kRowsQ);
-        const int64_t g = P.g0 + m;
-        const int64_t ua = P.unit0 + m * P.ntl, ub = ua + P.ntl - 1;
-        const int64_t clo = split_owner(ua, batch.units, batch.grid);
-        const int64_t chi = split_owner(ub, batch.units, batch.grid);
-        for (int64_t c = clo; c <= chi; ++c) {
-            const int64_t us = split_start(c, batch.units, batch.grid);
-            const MatchProblem& F = batch.p[problem_of_unit(batch, us)];
-            const int64_t g_first = F.g0 + (us - F.unit0) / F.ntl;
-            const uint64_t* rec = partials + ((c * batch.smax + (g - g_first)) * kRowsP + r) * 2;
-            top2_insert_u64(rec[0], k1, k2);
-            top2_insert_u64(rec[1], k1, k2);
-            const uint64_t* rec2 = rec + 2 * kRowsQ;  // the row's other column half
-            top2_insert_u64(rec2[0], k1, k2);
-            top2_insert_u64(rec2[1], k1, k2);
-        }
+        combine_row(batch, P, m, P.g0 + m, static_cast<int>(ql % kRowsQ), partials, k1, k2);
     }
-    latch_match mres;
-    mres.idx1 = k1 == kNoKey ? -1 : static_cast<int32_t>(k1 & 0xffffffffu);
-    mres.dist1 = k1 == kNoKey ? 0xffff : static_cast<uint16_t>(k1 >> 32);
-    const bool has2 = k == 2 && k2 != kNoKey;
-    mres.idx2 = has2 ? static_cast<int32_t>(k2 & 0xffffffffu) : -1;
-    mres.dist2 = has2 ? static_cast<uint16_t>(k2 >> 32) : 0xffff;
-    if (k1 == kNoKey)
-        mres.accepted = 0;
-    else if (k == 1)
-        mres.accepted = 1;
-    else
-        mres.accepted = (1000ll * mres.dist1 < static_cast<long long>(r_milli) * mres.dist2) ? 1 : 0;
-    mres.pad[0] = mres.pad[1] = mres.pad[2] = 0;
-    out[q] = mres;
+    out[q] = final_match(k1, k2, P.k, P.r_milli);
 }
 
 // Bits -> E4M3 0/1 bytes (bit t of a descriptor -> byte t) and per-descriptor popcount.
 __global__ void expand_kernel(const uint32_t* __restrict__ in, int64_t nwords, uint4* __restrict__ out,
                               int32_t* __restrict__ pop) {
+    griddep_wait();
+    griddep_launch_dependents();
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     const uint32_t w = i < nwords ? in[i] : 0u;
     uint32_t o[8];
@@ -495,15 +537,12 @@ cudaError_t launch_expand(const uint8_t* desc, int64_t n, uint8_t* out, int32_t*
     const int64_t nwords = n * 16;
     const int threads = 256;
     const int64_t grid = (nwords + threads - 1) / threads;
-    expand_kernel<<<static_cast<unsigned>(grid), threads, 0, stream>>>(reinterpret_cast<const uint32_t*>(desc), nwords,
-                                                                      reinterpret_cast<uint4*>(out), pop);
-    note_launches(1);
-    return cudaGetLastError();
+    return launch_chained(expand_kernel, dim3(static_cast<unsigned>(grid)), dim3(threads), 0, stream,
+                          reinterpret_cast<const uint32_t*>(desc), nwords, reinterpret_cast<uint4*>(out), pop);
 }
 
-// Fills tiles, unit offsets, query-tile prefixes, the block split and the largest
-// number of query tiles one block touches.  problems[i] must have q_row0, t_row0,
-// nq, nt and out0 set.
+// Fills tiles, unit offsets, query-tile prefixes and the block split.  problems[i]
+// must have q_row0, t_row0, nq, nt and out0 set.
 void plan_match_batch(MatchBatch* b, int count, int64_t max_grid) {
     b->count = count;
     int64_t units = 0, g = 0, queries = 0;
@@ -518,62 +557,102 @@ void plan_match_batch(MatchBatch* b, int count, int64_t max_grid) {
         queries = P.out0 + P.nq > queries ? P.out0 + P.nq : queries;
     }
     b->units = units;
+    b->tiles = static_cast<int32_t>(g);
     b->queries = queries;
     b->grid = units < max_grid ? units : max_grid;
-    b->smax = 0;
-    auto tile_of = [b](int64_t u) {
-        int p = 0;
-        while (p + 1 < b->count && b->p[p + 1].unit0 <= u) ++p;
-        return b->p[p].g0 + (u - b->p[p].unit0) / b->p[p].ntl;
-    };
-    for (int64_t c = 0; c < b->grid; ++c) {
-        const int64_t ua = split_start(c, units, b->grid), ub = split_start(c + 1, units, b->grid) - 1;
-        const int64_t segs = tile_of(ub) - tile_of(ua) + 1;
-        if (segs > b->smax) b->smax = segs;
-    }
 }
 
-size_t match_tc_partial_bytes(const MatchBatch& b) { return static_cast<size_t>(b.grid * b.smax * kRowsP) * 16; }
+// Block c's record of query tile g sits in slot g + c: blocks own increasing unit
+// ranges, so a later block never touches an earlier tile and the slots of
+// different (block, tile) pairs differ; tiles + grid - 1 slots suffice.
+static size_t partial_record_bytes(const MatchBatch& b) {
+    return static_cast<size_t>(b.tiles + b.grid) * kRowsP * 16;
+}
 
-size_t match_tc_batch_scratch_bytes(int64_t rows, const MatchBatch& b) {
+size_t match_tc_partial_bytes(const MatchBatch& b) { return partial_record_bytes(b); }
+
+size_t match_tc_counter_bytes(int64_t tiles) { return align_up(static_cast<size_t>(tiles) * 4, 256); }
+
+size_t match_tc_batch_scratch_bytes(int64_t rows, const MatchBatch& b, int64_t counter_tiles) {
     const size_t exp_bytes = align_up(static_cast<size_t>(rows) * kKBytes, 1024);
     const size_t pop_bytes = align_up(static_cast<size_t>(rows) * 4, 256);
-    return exp_bytes + pop_bytes + match_tc_partial_bytes(b) + 256;
+    return exp_bytes + pop_bytes + match_tc_counter_bytes(counter_tiles) + match_tc_partial_bytes(b) + 256;
 }
 
-cudaError_t launch_match_tc_rows(const MatchBatch& b, const uint8_t* exp, int64_t rows, const int32_t* pop,
-                                 uint64_t* partials, latch_match* out, uint32_t* flags, cudaStream_t stream) {
+// The batched layout's arrival counters: [expanded rows][popcounts][counters][partials].
+int32_t* match_tc_batch_counters(void* scratch, int64_t rows) {
+    const size_t exp_bytes = align_up(static_cast<size_t>(rows) * kKBytes, 1024);
+    const size_t pop_bytes = align_up(static_cast<size_t>(rows) * 4, 256);
+    return reinterpret_cast<int32_t*>(static_cast<uint8_t*>(scratch) + exp_bytes + pop_bytes);
+}
+
+// Copies the header and the first b.count problems into the table of capacity NP.
+template <int NP>
+static void shrink(const MatchBatch& b, MatchBatchT<NP>* o) {
+    o->count = b.count;
+    o->tiles = b.tiles;
+    o->units = b.units;
+    o->grid = b.grid;
+    o->queries = b.queries;
+    for (int i = 0; i < b.count; ++i) o->p[i] = b.p[i];
+}
+
+template <int NP>
+static cudaError_t launch_match_np(const MatchBatch& full, const CUtensorMap& map, const int32_t* pop,
+                                   uint64_t* partials, int32_t* tile_cnt, latch_match* out, uint32_t* flags,
+                                   cudaStream_t stream) {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(match_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+        cudaError_t e =
+            cudaFuncSetAttribute(match_tc_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    if (b.units > 0) {
-        CUtensorMap map;
-        if (!make_map(&map, exp, rows)) return cudaErrorInvalidValue;
-        match_tc_kernel<<<static_cast<unsigned>(b.grid), kThreads, kSmemBytes, stream>>>(map, b, pop, partials, flags);
-        note_launches(1);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+    MatchBatchT<NP>* b = new (std::nothrow) MatchBatchT<NP>;
+    if (!b) return cudaErrorMemoryAllocation;
+    shrink(full, b);
+    cudaError_t e = cudaSuccess;
+    if (b->units > 0)
+        e = launch_chained(match_tc_kernel<NP>, dim3(static_cast<unsigned>(b->grid)), dim3(kThreads), kSmemBytes,
+                           stream, map, *b, pop, partials, tile_cnt, out, flags);
+    if (e == cudaSuccess && !tile_cnt && b->queries > 0) {
+        const int threads = 256;
+        const int64_t grid = (b->queries + threads - 1) / threads;
+        e = launch_chained(match_merge_kernel<NP>, dim3(static_cast<unsigned>(grid)), dim3(threads), 0, stream, *b,
+                           partials, out);
     }
+    delete b;
+    return e;
+}
+
+cudaError_t launch_match_tc_rows(const MatchBatch& b, const uint8_t* exp, int64_t rows, const int32_t* pop,
+                                 uint64_t* partials, int32_t* tile_cnt, latch_match* out, uint32_t* flags,
+                                 cudaStream_t stream) {
     if (b.queries == 0) return cudaSuccess;
-    const int threads = 256;
-    const int64_t grid = (b.queries + threads - 1) / threads;
-    match_merge_kernel<<<static_cast<unsigned>(grid), threads, 0, stream>>>(b, partials, out);
-    note_launches(1);
-    return cudaGetLastError();
+    CUtensorMap map;
+    if (b.units > 0 && !make_map(&map, exp, rows)) return cudaErrorInvalidValue;
+    // the matcher combines each query tile's records itself unless some problem has
+    // queries but no train rows (its tiles have no unit, so no block visits them)
+    bool fused = b.units > 0 && tile_cnt != nullptr;
+    for (int i = 0; i < b.count; ++i)
+        if (b.p[i].nq > 0 && b.p[i].ntl == 0) fused = false;
+    if (!fused) tile_cnt = nullptr;
+    if (b.count <= 1) return launch_match_np<1>(b, map, pop, partials, tile_cnt, out, flags, stream);
+    if (b.count <= 16) return launch_match_np<16>(b, map, pop, partials, tile_cnt, out, flags, stream);
+    return launch_match_np<kMaxProblems>(b, map, pop, partials, tile_cnt, out, flags, stream);
 }
 
 // Scratch: expanded rows (rows x 512 B), popcounts, partial records.  The expanded
 // rows and popcounts must already be filled (launch_expand).
-cudaError_t launch_match_tc_batch(const MatchBatch& b, int64_t rows, void* scratch, latch_match* out,
-                                  uint32_t* flags, cudaStream_t stream) {
+cudaError_t launch_match_tc_batch(const MatchBatch& b, int64_t rows, int64_t counter_tiles, void* scratch,
+                                  latch_match* out, uint32_t* flags, cudaStream_t stream) {
     uint8_t* base = static_cast<uint8_t*>(scratch);
     const size_t exp_bytes = align_up(static_cast<size_t>(rows) * kKBytes, 1024);
     const size_t pop_bytes = align_up(static_cast<size_t>(rows) * 4, 256);
+    const size_t cnt_bytes = match_tc_counter_bytes(counter_tiles);
     return launch_match_tc_rows(b, base, rows, reinterpret_cast<const int32_t*>(base + exp_bytes),
-                                reinterpret_cast<uint64_t*>(base + exp_bytes + pop_bytes), out, flags, stream);
+                                reinterpret_cast<uint64_t*>(base + exp_bytes + pop_bytes + cnt_bytes),
+                                reinterpret_cast<int32_t*>(base + exp_bytes + pop_bytes), out, flags, stream);
 }
 
 static void single_problem(MatchBatch* b, int32_t nq, int32_t nt, int64_t sms, int32_t k = 2, int32_t r = 800) {
@@ -590,7 +669,7 @@ static void single_problem(MatchBatch* b, int32_t nq, int32_t nt, int64_t sms, i
 size_t match_tc_scratch_bytes_sms(int64_t sms, int64_t nq, int64_t nt) {
     MatchBatch* b = new MatchBatch;
     single_problem(b, static_cast<int32_t>(nq), static_cast<int32_t>(nt), sms);
-    const size_t r = match_tc_batch_scratch_bytes(nq + nt, *b);
+    const size_t r = match_tc_batch_scratch_bytes(nq + nt, *b, b->tiles);
     delete b;
     return r;
 }
@@ -608,10 +687,12 @@ cudaError_t launch_match_tc(const latch_context* ctx, const uint8_t* q, int32_t 
     int32_t* pop = reinterpret_cast<int32_t*>(base + exp_bytes);
     cudaError_t e = cudaSuccess;
     if (b->units > 0) {
-        e = launch_expand(q, nq, base, pop, stream);
+        // the arrival counters are cleared ahead of the kernels, off their dependency chain
+        e = cudaMemsetAsync(match_tc_batch_counters(scratch, nq + nt), 0, match_tc_counter_bytes(b->tiles), stream);
+        if (e == cudaSuccess) e = launch_expand(q, nq, base, pop, stream);
         if (e == cudaSuccess) e = launch_expand(t, nt, base + static_cast<size_t>(nq) * kKBytes, pop + nq, stream);
     }
-    if (e == cudaSuccess) e = launch_match_tc_batch(*b, nq + nt, scratch, out, ctx->d_flags, stream);
+    if (e == cudaSuccess) e = launch_match_tc_batch(*b, nq + nt, b->tiles, scratch, out, ctx->d_flags, stream);
     delete b;
     return e;
 }

@@ -179,13 +179,16 @@ latch_status run_batch(latch_session* s, int li, DoneArg* done) {
     }
     plan_match_batch(mb, nb, s->ctx->sm_count);
     uint64_t* partials = reinterpret_cast<uint64_t*>(cv.take(match_tc_partial_bytes(*mb) + 16));
-    if (!ext_scratch || !partials) e = cudaErrorMemoryAllocation;  // admission bug guard
+    int32_t* tile_cnt = reinterpret_cast<int32_t*>(cv.take(match_tc_counter_bytes(mb->tiles)));
+    if (!ext_scratch || !partials || !tile_cnt) e = cudaErrorMemoryAllocation;  // admission bug guard
+    if (e == cudaSuccess && total > 0) e = cudaMemsetAsync(tile_cnt, 0, match_tc_counter_bytes(mb->tiles), st);
+    // the extraction writes the queries' expanded rows into the lane's arena rows
     if (e == cudaSuccess && total > 0)
-        e = launch_extract_batch(s->ctx, imgs.data(), kp0.data(), n.data(), nb, d_kps, d_desc, ext_scratch, st);
+        e = launch_extract_batch(s->ctx, imgs.data(), kp0.data(), n.data(), nb, d_kps, d_desc, ext_scratch, st,
+                                 s->arena + L.qrow0 * 512, s->arena_pop + L.qrow0);
     if (e == cudaSuccess && total > 0)
-        e = launch_expand(d_desc, total, s->arena + L.qrow0 * 512, s->arena_pop + L.qrow0, st);
-    if (e == cudaSuccess && total > 0)
-        e = launch_match_tc_rows(*mb, s->arena, s->arena_rows, s->arena_pop, partials, d_match, s->ctx->d_flags, st);
+        e = launch_match_tc_rows(*mb, s->arena, s->arena_rows, s->arena_pop, partials, tile_cnt, d_match,
+                                 s->ctx->d_flags, st);
     for (int i = 0; i < nb && e == cudaSuccess; ++i) {
         const latch_request& r = L.batch[i]->req;
         if (r.n == 0) continue;
@@ -250,9 +253,11 @@ void scheduler(latch_session* s) {
         const double t = now_s(s);
         while (!s->queue.empty() && static_cast<int>(L.batch.size()) < s->max_batch) {
             Ticket* tk = s->queue.front();
-            // per-batch partial records: at most (query tiles + blocks) x 256 rows x 16 B
-            const size_t part = static_cast<size_t>((kps + tk->req.n) / 256 + L.batch.size() + 1 + 2 * s->ctx->sm_count) *
-                                256 * 16 + 1024;
+            // per-batch partial records, (query tiles + blocks) x 256 rows x 16 B, and one
+            // 4-byte arrival counter per query tile; a request of n keypoints has at most
+            // n / 128 + 1 query tiles, a launch at most one block per SM
+            const size_t tiles = static_cast<size_t>((kps + tk->req.n) / 128 + L.batch.size() + 1);
+            const size_t part = (tiles + static_cast<size_t>(s->ctx->sm_count)) * 256 * 16 + tiles * 4 + 1024;
             if (kps + tk->req.n > s->max_batch_kps || bytes + tk->bytes + part > s->lane_bytes) break;
             s->queue.pop_front();
             bytes += tk->bytes;

@@ -95,3 +95,37 @@ def test_sfm_batch_full_size_sampled(gpu_ctx, triplets):
         q, t = wl["pairs"][p]
         rows = rng.choice(len(wl["kps"][q]), 3, replace=False)
         _same(matches[p][rows], oracle.match(descs[q][rows], descs[t], 2, 0.8))
+
+
+def test_more_pairs_than_one_launch(gpu_ctx, triplets):
+    """700 pairs: two matching launches share the scratch (partial records and the
+    per-query-tile arrival counters, which each complete launch leaves zero).  The
+    second launch holds a pair with an empty train set, so it combines its records
+    in a separate pass; the first combines them in the matching kernel.  Every
+    pair's matches equal a single hamming_match call on the same descriptors, and a
+    second run of the batch gives the same bytes."""
+    rng = np.random.default_rng(35)
+    nimg = 30
+    sizes = [(160, 120)] * nimg
+    imgs = [synth.image(synth.seed(35, i, synth.KIND_IMAGE), 160, 120, n_ellipses=10) for i in range(nimg)]
+    counts = [0] + [int(c) for c in rng.integers(1, 400, nimg - 1)]  # image 0 has no keypoints
+    kps = [synth.keypoints(synth.seed(35, i, synth.KIND_KEYPOINTS), 160, 120, counts[i], 16, True, 3)
+           if counts[i] else np.zeros((0, 4), np.int32) for i in range(nimg)]
+    pairs = [(int(q), int(t)) for q, t in zip(rng.integers(1, nimg, 700), rng.integers(1, nimg, 700))]
+    pairs[600] = (5, 0)  # queries against an empty train set, in the second launch
+    descs, matches = _run_batch(gpu_ctx, imgs, sizes, kps, pairs)
+    _, again = _run_batch(gpu_ctx, imgs, sizes, kps, pairs)
+    dev = [to_dev(d) if len(d) else torch.zeros((1, 64), dtype=torch.uint8, device="cuda") for d in descs]
+    for p, (q, t) in enumerate(pairs):
+        _same(again[p], matches[p])
+        if counts[q] == 0:
+            assert len(matches[p]) == 0
+            continue
+        out = torch.empty((counts[q], 16), dtype=torch.uint8, device="cuda")
+        P.hamming_match(gpu_ctx.handle, dev[q], counts[q], dev[t], counts[t], 2, 0.8, out, P.PATH_TENSOR,
+                        int(torch.cuda.current_stream().cuda_stream))
+        torch.cuda.synchronize()
+        _same(matches[p], P.matches_from_bytes(out.cpu().numpy()))
+    assert np.all(matches[600]["idx1"] == -1) and np.all(matches[600]["dist1"] == 65535)
+    rows = rng.choice(counts[pairs[3][0]], min(5, counts[pairs[3][0]]), replace=False)
+    _same(matches[3][rows], oracle.match(descs[pairs[3][0]][rows], descs[pairs[3][1]], 2, 0.8))

@@ -1,8 +1,9 @@
 // LATCH descriptor extraction (Sec. 3.1 Eq. 1; Sec. 3.2).
 //
-// 1. bucket_kernel (one block per image): counting sort of the keypoints into
-//    32x32-pixel image cells; the launch's record array receives one 16-byte record
-//    per keypoint (position, output row, offset table, image), cell by cell.  The
+// 1. sort_count_kernel + sort_scatter_kernel (1024 keypoints per block): counting
+//    sort of the keypoints into 32x32-pixel image cells; the launch's record array
+//    receives one 16-byte record per keypoint (position, output row, offset table,
+//    image), cell by cell.  The
 //    cell grid reaches 128 px beyond every border; keypoints further out have
 //    windows wholly outside the image (the window reaches at most `reach` <= 78
 //    px), whose samples all read 0, so their descriptor is all zeros and is written
@@ -48,8 +49,8 @@ constexpr int kThreads = 256;           // 8 warps
 constexpr int kRowWords = 12;           // 48 bytes per window row
 constexpr int kCopyWords = kWin * kRowWords + 4;   // one byte-shifted copy (+4: bank offset; 16-byte multiple)
 constexpr int kWinWords = 4 * kCopyWords;          // 4 copies
-constexpr int kBucketThreads = 1024;
-constexpr int kMaxSmemCells = 12288;
+constexpr int kSortThreads = 256;
+constexpr int kSortKps = 1024;          // keypoints per sorting block (4 per thread)
 constexpr int kRing = 64;               // keypoint records in flight per block (1 KB: four blocks still fit an SM)
 
 struct CellGrid {
@@ -80,7 +81,9 @@ struct ExtractParams {
     int32_t kp0[NI];      // first keypoint of image i in the concatenated keypoint array
     int32_t n[NI];        // keypoints of image i
     int32_t cell0[NI];    // first entry of image i in the global cell-count scratch
+    int32_t blk0[NI];     // first sorting block of image i (ceil(n / kSortKps) blocks each)
     int32_t count;        // images in this launch
+    int32_t active;       // images with at least one keypoint
     int32_t nscales;
     TileGeom tg;
 };
@@ -91,107 +94,168 @@ __device__ __forceinline__ int4 kp_record(const latch_keypoint& kp, int row, int
     return make_int4(kp.x, kp.y, row, (kp.scale_idx * kBins + (kp.angle_bin & (kBins - 1))) | (img << 16));
 }
 
-// One block per image: counting sort of its keypoints into cells.  The image's
-// keypoints that have a cell take the positions [base, base + count) of the
-// launch's record array, cell by cell (base from an atomic on counters[0], which
-// ends as the launch's number of records; zeroed by the host).
+// Image of sorting block `blk` (largest i with blk0[i] <= blk).
 template <int NI>
-__global__ void __launch_bounds__(kBucketThreads) bucket_kernel(const __grid_constant__ ExtractParams<NI> prm,
-                                                                const latch_keypoint* __restrict__ kps,
-                                                                int* __restrict__ gcount, int* __restrict__ counters,
-                                                                int4* __restrict__ recs, uint4* __restrict__ out,
-                                                                uint4* __restrict__ exp_out,
-                                                                int32_t* __restrict__ pop_out,
-                                                                uint32_t* __restrict__ flags) {
-    extern __shared__ int s_cnt[];
-    __shared__ int s_part[kBucketThreads / 32];
-    __shared__ int s_base;
+__device__ __forceinline__ int image_of_block(const ExtractParams<NI>& prm, int blk) {
+    int lo = 0, hi = prm.count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prm.blk0[mid] <= blk) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Sorting, pass 1 (kSortKps keypoints of one image per block): the cell of every
+// keypoint; a keypoint with a cell takes its rank in the cell from an atomic on the
+// cell's count (order of arrival), one without gets its zero descriptor here.  The
+// last block of an image to finish turns the image's counts into exclusive starts;
+// the last image to finish turns the images' totals into the bases of their record
+// ranges (records of all images are contiguous) and sets counters[0] = records.
+// Scratch zeroed by the host: counters, img_tot / img_done, the cell counts.
+template <int NI>
+__global__ void __launch_bounds__(kSortThreads) sort_count_kernel(
+    const __grid_constant__ ExtractParams<NI> prm, const latch_keypoint* __restrict__ kps, int* __restrict__ cells,
+    int* __restrict__ rank, int* __restrict__ img_tot, int* __restrict__ img_done, int* __restrict__ img_base,
+    int* __restrict__ counters, uint4* __restrict__ out, uint4* __restrict__ exp_out, int32_t* __restrict__ pop_out,
+    uint32_t* __restrict__ flags) {
+    __shared__ int s_part[kSortThreads / 32];
+    __shared__ int s_flag;
     griddep_wait();
     griddep_launch_dependents();
-    const int img = blockIdx.x;
+    const int img = image_of_block(prm, blockIdx.x);
     const CellGrid g = prm.grid[img];
     const int n = prm.n[img], kp0 = prm.kp0[img];
-    const int ncell = g.gx * g.gy;
-    const bool in_smem = ncell <= kMaxSmemCells;
-    int* cnt = in_smem ? s_cnt : gcount + prm.cell0[img];  // the global counts were zeroed by the host
-    if (in_smem)
-        for (int c = threadIdx.x; c < ncell; c += blockDim.x) cnt[c] = 0;
-    __syncthreads();
+    int* cnt = cells + prm.cell0[img];
+    const int i0 = (blockIdx.x - prm.blk0[img]) * kSortKps + threadIdx.x;
+    // all loads first, then the atomics
+    latch_keypoint kp[kSortKps / kSortThreads];
+#pragma unroll
+    for (int q = 0; q < kSortKps / kSortThreads; ++q)
+        if (i0 + q * kSortThreads < n) kp[q] = kps[kp0 + i0 + q * kSortThreads];
+    int valid = 0;
     bool bad = false;
-    // 8 independent keypoint loads in flight per thread
-    for (int i0 = threadIdx.x; i0 < n; i0 += 8 * blockDim.x) {
-        int cc[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int i = i0 + j * blockDim.x;
-            cc[j] = i < n ? cell_of(kps[kp0 + i], prm.nscales, g) : -3;
-        }
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int i = i0 + j * blockDim.x;
-            if (cc[j] >= 0) {
-                atomicAdd(&cnt[cc[j]], 1);
-            } else if (cc[j] > -3) {
-                const uint4 z = make_uint4(0, 0, 0, 0);
-                uint4* d = out + static_cast<size_t>(kp0 + i) * 4;
-                d[0] = z;
-                d[1] = z;
-                d[2] = z;
-                d[3] = z;
-                if (exp_out) {
-                    uint4* x = exp_out + static_cast<size_t>(kp0 + i) * 32;
-                    for (int q = 0; q < 32; ++q) x[q] = z;
-                    pop_out[kp0 + i] = 0;
-                }
-                bad |= (cc[j] == -2);
+    for (int q = 0; q < kSortKps / kSortThreads; ++q) {
+        const int i = i0 + q * kSortThreads;
+        const int c = i < n ? cell_of(kp[q], prm.nscales, g) : -3;
+        if (c >= 0) {
+            rank[kp0 + i] = atomicAdd(&cnt[c], 1);
+            ++valid;
+        } else if (c > -3) {
+            const uint4 z = make_uint4(0, 0, 0, 0);
+            uint4* d = out + static_cast<size_t>(kp0 + i) * 4;
+            d[0] = z;
+            d[1] = z;
+            d[2] = z;
+            d[3] = z;
+            if (exp_out) {
+                uint4* x = exp_out + static_cast<size_t>(kp0 + i) * 32;
+                for (int u = 0; u < 32; ++u) x[u] = z;
+                pop_out[kp0 + i] = 0;
             }
+            bad |= (c == -2);
         }
     }
-    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, kFlagBadScale);
-    // exclusive scan of the counts: each thread sums a contiguous run of cells
-    const int per = (ncell + blockDim.x - 1) / blockDim.x;
-    const int c0 = threadIdx.x * per, c1 = min(c0 + per, ncell);
-    int sum = 0;
-    for (int c = c0; c < c1; ++c) sum += cnt[c];
+    __threadfence();  // this thread's count increments before the block's arrival below
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int incl = sum;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
+    valid = __reduce_add_sync(0xffffffffu, static_cast<uint32_t>(valid));
+    if (lane == 0) s_part[warp] = valid;
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, kFlagBadScale);
+    if (threadIdx.x == 0) {
+        int v = 0;
+        for (int w = 0; w < kSortThreads / 32; ++w) v += s_part[w];
+        atomicAdd(&img_tot[img], v);
+        __threadfence();  // the block's total before its arrival
+        const int nblk = (n + kSortKps - 1) / kSortKps;
+        s_flag = atomicAdd(&img_done[img], 1) == nblk - 1;
     }
-    if (lane == 31) s_part[warp] = incl;
     __syncthreads();
-    if (warp == 0) {
-        int v = lane < kBucketThreads / 32 ? s_part[lane] : 0;
+    if (!s_flag) return;
+    // ---- last block of the image: exclusive starts of its cells, in place, in
+    // tiles of 8 cells per thread (eight independent loads in flight) ----
+    __threadfence();
+    const int ncell = g.gx * g.gy;
+    int carry = 0;
+    for (int tb = 0; tb < ncell; tb += 8 * kSortThreads) {
+        const int c0 = tb + 8 * threadIdx.x;
+        int v[8];
+        int sum = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            v[q] = c0 + q < ncell ? __ldcg(&cnt[c0 + q]) : 0;
+            sum += v[q];
+        }
+        int incl = sum;
         for (int o = 1; o < 32; o <<= 1) {
-            const int w = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += w;
+            const int x = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += x;
         }
-        if (lane < kBucketThreads / 32) s_part[lane] = v;
-        if (lane == kBucketThreads / 32 - 1) s_base = atomicAdd(&counters[0], v);
-    }
-    __syncthreads();
-    int run = s_base + incl - sum + (warp > 0 ? s_part[warp - 1] : 0);
-    for (int c = c0; c < c1; ++c) {
-        const int k = cnt[c];
-        cnt[c] = run;  // becomes the insertion cursor (a record position)
-        run += k;
-    }
-    __syncthreads();
-    // scatter the records (the keypoints are read again: 8 loads in flight)
-    for (int i0 = threadIdx.x; i0 < n; i0 += 8 * blockDim.x) {
-        latch_keypoint kp[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int i = i0 + j * blockDim.x;
-            if (i < n) kp[j] = kps[kp0 + i];
+        __syncthreads();  // s_part free (its previous readers are done)
+        if (lane == 31) s_part[warp] = incl;
+        __syncthreads();
+        int run = carry + incl - sum, tile_total = 0;
+        for (int w = 0; w < kSortThreads / 32; ++w) {
+            const int x = s_part[w];
+            if (w < warp) run += x;
+            tile_total += x;
         }
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int i = i0 + j * blockDim.x;
-            const int c = i < n ? cell_of(kp[j], prm.nscales, g) : -3;
-            if (c >= 0) recs[atomicAdd(&cnt[c], 1)] = kp_record(kp[j], kp0 + i, img);
-        }
+        for (int q = 0; q < 8; ++q)
+            if (c0 + q < ncell) {
+                cnt[c0 + q] = run;
+                run += v[q];
+            }
+        carry += tile_total;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_flag = atomicAdd(&counters[1], 1) == prm.active - 1;
+    __syncthreads();
+    if (!s_flag || threadIdx.x >= 32) return;
+    // ---- last image: bases of the images' record ranges (at most 64 images) ----
+    __threadfence();
+    const int a = lane < prm.count ? __ldcg(&img_tot[lane]) : 0;
+    const int b = lane + 32 < prm.count ? __ldcg(&img_tot[lane + 32]) : 0;
+    int ia = a;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, ia, o);
+        if (lane >= o) ia += v;
+    }
+    const int tot_a = __shfl_sync(0xffffffffu, ia, 31);
+    int ib = b;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, ib, o);
+        if (lane >= o) ib += v;
+    }
+    if (lane < prm.count) img_base[lane] = ia - a;
+    if (lane + 32 < prm.count) img_base[lane + 32] = tot_a + ib - b;
+    if (lane == 31) counters[0] = tot_a + ib;
+}
+
+// Sorting, pass 2 (same blocks): each keypoint with a cell writes its record at
+// image base + cell start + rank.
+template <int NI>
+__global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(
+    const __grid_constant__ ExtractParams<NI> prm, const latch_keypoint* __restrict__ kps,
+    const int* __restrict__ cells, const int* __restrict__ rank, const int* __restrict__ img_base,
+    int4* __restrict__ recs) {
+    griddep_wait();
+    griddep_launch_dependents();
+    const int img = image_of_block(prm, blockIdx.x);
+    const CellGrid g = prm.grid[img];
+    const int n = prm.n[img], kp0 = prm.kp0[img];
+    const int* start = cells + prm.cell0[img];
+    const int base = img_base[img];
+    const int i0 = (blockIdx.x - prm.blk0[img]) * kSortKps + threadIdx.x;
+    latch_keypoint kp[kSortKps / kSortThreads];
+#pragma unroll
+    for (int q = 0; q < kSortKps / kSortThreads; ++q)
+        if (i0 + q * kSortThreads < n) kp[q] = kps[kp0 + i0 + q * kSortThreads];
+#pragma unroll
+    for (int q = 0; q < kSortKps / kSortThreads; ++q) {
+        const int i = i0 + q * kSortThreads;
+        const int c = i < n ? cell_of(kp[q], prm.nscales, g) : -3;
+        if (c >= 0) recs[base + start[c] + rank[kp0 + i]] = kp_record(kp[q], kp0 + i, img);
     }
 }
 
@@ -529,10 +593,11 @@ static EncodeTiledFn extract_encode_fn() {
     return fn;
 }
 
-// Scratch of one launch over images [i0, i1): sorted keypoint records, counters,
-// cell counts (for grids too large for shared memory).
+// Scratch of one launch over images [i0, i1): sorted keypoint records, ranks, image
+// bases, then the region the host zeroes: counters, image totals, image arrival
+// counters, cell counts.
 struct ChunkLayout {
-    size_t recs, counters, cells, total;
+    size_t recs, rank, img_base, zero, counters, img_tot, img_done, cells, total;
     int64_t ncell, nkp;
 };
 
@@ -546,8 +611,13 @@ static ChunkLayout chunk_layout(const latch_image* imgs, const int64_t* n, int i
         l.nkp += n[i];
     }
     l.recs = 0;  // int4, 16-byte aligned
-    l.counters = l.recs + static_cast<size_t>(l.nkp) * sizeof(int4);
-    l.cells = l.counters + 16;
+    l.rank = l.recs + static_cast<size_t>(l.nkp) * sizeof(int4);
+    l.img_base = (l.rank + static_cast<size_t>(l.nkp) * sizeof(int) + 255) / 256 * 256;
+    l.zero = l.img_base + 64 * sizeof(int);
+    l.counters = l.zero;
+    l.img_tot = l.counters + 16;
+    l.img_done = l.img_tot + 64 * sizeof(int);
+    l.cells = l.img_done + 64 * sizeof(int);
     l.total = (l.cells + static_cast<size_t>(l.ncell) * sizeof(int) + 255) / 256 * 256;
     return l;
 }
@@ -573,12 +643,9 @@ static cudaError_t launch_chunk(const latch_context* ctx, const latch_image* img
     const TileGeom tg = tile_geom(ctx->reach);
     cudaError_t e;
     if (!attr) {
-        e = cudaFuncSetAttribute(bucket_kernel<NI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(sizeof(int) * kMaxSmemCells));
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(extract_cells_kernel<NI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     static_cast<int>(extract_smem_bytes(tile_geom(kMaxReach + 1))));
-        if (e == cudaSuccess)  // four 56 KB blocks per SM
+        e = cudaFuncSetAttribute(extract_cells_kernel<NI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(extract_smem_bytes(tile_geom(kMaxReach + 1))));
+        if (e == cudaSuccess)  // four 57 KB blocks per SM
             e = cudaFuncSetAttribute(extract_cells_kernel<NI>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e != cudaSuccess) return e;
         attr = true;
@@ -587,29 +654,30 @@ static cudaError_t launch_chunk(const latch_context* ctx, const latch_image* img
     if (!enc) return cudaErrorNotSupported;
     const ChunkLayout l = chunk_layout(imgs, n, i0, i1);
     int4* recs = reinterpret_cast<int4*>(scratch + l.recs);
+    int* rank = reinterpret_cast<int*>(scratch + l.rank);
+    int* img_base = reinterpret_cast<int*>(scratch + l.img_base);
     int* counters = reinterpret_cast<int*>(scratch + l.counters);
+    int* img_tot = reinterpret_cast<int*>(scratch + l.img_tot);
+    int* img_done = reinterpret_cast<int*>(scratch + l.img_done);
     int* cells = reinterpret_cast<int*>(scratch + l.cells);
 
     ExtractParams<NI>* prm = new ExtractParams<NI>;
     prm->count = i1 - i0;
     prm->nscales = ctx->nscales;
     prm->tg = tg;
-    bool global_cells = false;
     int64_t cell0 = 0;
-    size_t bucket_smem = 0;
+    int blocks = 0, active = 0;
     for (int i = i0; i < i1; ++i) {
         const int j = i - i0;
         const CellGrid g = cell_grid(&imgs[i]);
-        const int64_t ncell = static_cast<int64_t>(g.gx) * g.gy;
         prm->grid[j] = g;
         prm->kp0[j] = static_cast<int32_t>(kp0[i]);
         prm->n[j] = static_cast<int32_t>(n[i]);
         prm->cell0[j] = static_cast<int32_t>(cell0);
-        cell0 += ncell;
-        if (ncell > kMaxSmemCells)
-            global_cells = true;
-        else if (sizeof(int) * ncell > bucket_smem)
-            bucket_smem = sizeof(int) * ncell;
+        prm->blk0[j] = blocks;
+        cell0 += static_cast<int64_t>(g.gx) * g.gy;
+        blocks += static_cast<int>((n[i] + kSortKps - 1) / kSortKps);
+        active += n[i] > 0;
         cuuint64_t dims[2] = {static_cast<cuuint64_t>(imgs[i].width), static_cast<cuuint64_t>(imgs[i].height)};
         cuuint64_t strides[1] = {static_cast<cuuint64_t>(imgs[i].pitch)};
         cuuint32_t box[2] = {static_cast<cuuint32_t>(tg.tw), static_cast<cuuint32_t>(tg.th)};
@@ -621,13 +689,16 @@ static cudaError_t launch_chunk(const latch_context* ctx, const latch_image* img
             return cudaErrorInvalidValue;
         }
     }
-    e = cudaMemsetAsync(counters, 0, 16, stream);
-    if (e == cudaSuccess && global_cells) e = cudaMemsetAsync(cells, 0, sizeof(int) * l.ncell, stream);
-    if (e == cudaSuccess) {
-        e = launch_chained(bucket_kernel<NI>, dim3(i1 - i0), dim3(kBucketThreads), bucket_smem, stream, *prm,
-                           d_kps, cells, counters, recs, reinterpret_cast<uint4*>(d_out),
+    prm->active = active;
+    e = cudaMemsetAsync(scratch + l.zero, 0, l.total - l.zero, stream);
+    if (e == cudaSuccess)
+        e = launch_chained(sort_count_kernel<NI>, dim3(blocks), dim3(kSortThreads), 0, stream, *prm, d_kps, cells,
+                           rank, img_tot, img_done, img_base, counters, reinterpret_cast<uint4*>(d_out),
                            reinterpret_cast<uint4*>(exp_out), pop_out, ctx->d_flags);
-    }
+    if (e == cudaSuccess)
+        e = launch_chained(sort_scatter_kernel<NI>, dim3(blocks), dim3(kSortThreads), 0, stream, *prm, d_kps,
+                           static_cast<const int*>(cells), static_cast<const int*>(rank),
+                           static_cast<const int*>(img_base), recs);
     if (e == cudaSuccess) {
         // the records are split evenly over the blocks, at least item_kps keypoints each
         const int64_t want = (l.nkp + ctx->item_kps - 1) / ctx->item_kps;

@@ -83,7 +83,6 @@ struct ExtractParams {
     int32_t cell0[NI];    // first entry of image i in the global cell-count scratch
     int32_t blk0[NI];     // first sorting block of image i (ceil(n / kSortKps) blocks each)
     int32_t count;        // images in this launch
-    int32_t active;       // images with at least one keypoint
     int32_t nscales;
     TileGeom tg;
 };
@@ -108,16 +107,13 @@ __device__ __forceinline__ int image_of_block(const ExtractParams<NI>& prm, int 
 // Sorting, pass 1 (kSortKps keypoints of one image per block): the cell of every
 // keypoint; a keypoint with a cell takes its rank in the cell from an atomic on the
 // cell's count (order of arrival), one without gets its zero descriptor here.  The
-// last block of an image to finish turns the image's counts into exclusive starts;
-// the last image to finish turns the images' totals into the bases of their record
-// ranges (records of all images are contiguous) and sets counters[0] = records.
-// Scratch zeroed by the host: counters, img_tot / img_done, the cell counts.
+// last block of an image to finish turns the image's counts into exclusive starts.
+// Scratch zeroed by the host: img_tot / img_done, the cell counts.
 template <int NI>
 __global__ void __launch_bounds__(kSortThreads) sort_count_kernel(
     const __grid_constant__ ExtractParams<NI> prm, const latch_keypoint* __restrict__ kps, int* __restrict__ cells,
-    int* __restrict__ rank, int* __restrict__ img_tot, int* __restrict__ img_done, int* __restrict__ img_base,
-    int* __restrict__ counters, uint4* __restrict__ out, uint4* __restrict__ exp_out, int32_t* __restrict__ pop_out,
-    uint32_t* __restrict__ flags) {
+    int* __restrict__ rank, int* __restrict__ img_tot, int* __restrict__ img_done, uint4* __restrict__ out,
+    uint4* __restrict__ exp_out, int32_t* __restrict__ pop_out, uint32_t* __restrict__ flags) {
     __shared__ int s_part[kSortThreads / 32];
     __shared__ int s_flag;
     griddep_wait();
@@ -156,7 +152,6 @@ __global__ void __launch_bounds__(kSortThreads) sort_count_kernel(
             bad |= (c == -2);
         }
     }
-    __threadfence();  // this thread's count increments before the block's arrival below
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     valid = __reduce_add_sync(0xffffffffu, static_cast<uint32_t>(valid));
     if (lane == 0) s_part[warp] = valid;
@@ -165,7 +160,9 @@ __global__ void __launch_bounds__(kSortThreads) sort_count_kernel(
         int v = 0;
         for (int w = 0; w < kSortThreads / 32; ++w) v += s_part[w];
         atomicAdd(&img_tot[img], v);
-        __threadfence();  // the block's total before its arrival
+        // release: the block's count increments (ordered before this by the barrier
+        // above) and its total, before its arrival
+        __threadfence();
         const int nblk = (n + kSortKps - 1) / kSortKps;
         s_flag = atomicAdd(&img_done[img], 1) == nblk - 1;
     }
@@ -207,50 +204,43 @@ __global__ void __launch_bounds__(kSortThreads) sort_count_kernel(
             }
         carry += tile_total;
     }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_flag = atomicAdd(&counters[1], 1) == prm.active - 1;
-    __syncthreads();
-    if (!s_flag || threadIdx.x >= 32) return;
-    // ---- last image: bases of the images' record ranges (at most 64 images) ----
-    __threadfence();
-    const int a = lane < prm.count ? __ldcg(&img_tot[lane]) : 0;
-    const int b = lane + 32 < prm.count ? __ldcg(&img_tot[lane + 32]) : 0;
-    int ia = a;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, ia, o);
-        if (lane >= o) ia += v;
-    }
-    const int tot_a = __shfl_sync(0xffffffffu, ia, 31);
-    int ib = b;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, ib, o);
-        if (lane >= o) ib += v;
-    }
-    if (lane < prm.count) img_base[lane] = ia - a;
-    if (lane + 32 < prm.count) img_base[lane + 32] = tot_a + ib - b;
-    if (lane == 31) counters[0] = tot_a + ib;
 }
 
 // Sorting, pass 2 (same blocks): each keypoint with a cell writes its record at
-// image base + cell start + rank.
+// image base + cell start + rank; the records of all images are contiguous, image
+// by image (base = the totals of the earlier images).  Block 0 sets counters[0] =
+// the launch's number of records.
 template <int NI>
 __global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(
     const __grid_constant__ ExtractParams<NI> prm, const latch_keypoint* __restrict__ kps,
-    const int* __restrict__ cells, const int* __restrict__ rank, const int* __restrict__ img_base,
-    int4* __restrict__ recs) {
+    const int* __restrict__ cells, const int* __restrict__ rank, const int* __restrict__ img_tot,
+    int* __restrict__ counters, int4* __restrict__ recs) {
+    __shared__ int s_base;
     griddep_wait();
     griddep_launch_dependents();
     const int img = image_of_block(prm, blockIdx.x);
     const CellGrid g = prm.grid[img];
     const int n = prm.n[img], kp0 = prm.kp0[img];
     const int* start = cells + prm.cell0[img];
-    const int base = img_base[img];
     const int i0 = (blockIdx.x - prm.blk0[img]) * kSortKps + threadIdx.x;
     latch_keypoint kp[kSortKps / kSortThreads];
 #pragma unroll
     for (int q = 0; q < kSortKps / kSortThreads; ++q)
         if (i0 + q * kSortThreads < n) kp[q] = kps[kp0 + i0 + q * kSortThreads];
+    if (threadIdx.x < 32) {  // at most 64 images
+        const int lane = threadIdx.x;
+        const int a = lane < prm.count ? img_tot[lane] : 0;
+        const int b = lane + 32 < prm.count ? img_tot[lane + 32] : 0;
+        const int before = (lane < img ? a : 0) + (lane + 32 < img ? b : 0);
+        const int base = __reduce_add_sync(0xffffffffu, static_cast<uint32_t>(before));
+        const int total = __reduce_add_sync(0xffffffffu, static_cast<uint32_t>(a + b));
+        if (lane == 0) {
+            s_base = base;
+            if (blockIdx.x == 0) counters[0] = total;
+        }
+    }
+    __syncthreads();
+    const int base = s_base;
 #pragma unroll
     for (int q = 0; q < kSortKps / kSortThreads; ++q) {
         const int i = i0 + q * kSortThreads;
@@ -593,11 +583,11 @@ static EncodeTiledFn extract_encode_fn() {
     return fn;
 }
 
-// Scratch of one launch over images [i0, i1): sorted keypoint records, ranks, image
-// bases, then the region the host zeroes: counters, image totals, image arrival
-// counters, cell counts.
+// Scratch of one launch over images [i0, i1): sorted keypoint records, ranks, then
+// the region the host zeroes: counters, image totals, image arrival counters, cell
+// counts.
 struct ChunkLayout {
-    size_t recs, rank, img_base, zero, counters, img_tot, img_done, cells, total;
+    size_t recs, rank, zero, counters, img_tot, img_done, cells, total;
     int64_t ncell, nkp;
 };
 
@@ -612,8 +602,7 @@ static ChunkLayout chunk_layout(const latch_image* imgs, const int64_t* n, int i
     }
     l.recs = 0;  // int4, 16-byte aligned
     l.rank = l.recs + static_cast<size_t>(l.nkp) * sizeof(int4);
-    l.img_base = (l.rank + static_cast<size_t>(l.nkp) * sizeof(int) + 255) / 256 * 256;
-    l.zero = l.img_base + 64 * sizeof(int);
+    l.zero = (l.rank + static_cast<size_t>(l.nkp) * sizeof(int) + 255) / 256 * 256;
     l.counters = l.zero;
     l.img_tot = l.counters + 16;
     l.img_done = l.img_tot + 64 * sizeof(int);
@@ -655,7 +644,6 @@ static cudaError_t launch_chunk(const latch_context* ctx, const latch_image* img
     const ChunkLayout l = chunk_layout(imgs, n, i0, i1);
     int4* recs = reinterpret_cast<int4*>(scratch + l.recs);
     int* rank = reinterpret_cast<int*>(scratch + l.rank);
-    int* img_base = reinterpret_cast<int*>(scratch + l.img_base);
     int* counters = reinterpret_cast<int*>(scratch + l.counters);
     int* img_tot = reinterpret_cast<int*>(scratch + l.img_tot);
     int* img_done = reinterpret_cast<int*>(scratch + l.img_done);
@@ -666,7 +654,7 @@ static cudaError_t launch_chunk(const latch_context* ctx, const latch_image* img
     prm->nscales = ctx->nscales;
     prm->tg = tg;
     int64_t cell0 = 0;
-    int blocks = 0, active = 0;
+    int blocks = 0;
     for (int i = i0; i < i1; ++i) {
         const int j = i - i0;
         const CellGrid g = cell_grid(&imgs[i]);
@@ -677,7 +665,6 @@ static cudaError_t launch_chunk(const latch_context* ctx, const latch_image* img
         prm->blk0[j] = blocks;
         cell0 += static_cast<int64_t>(g.gx) * g.gy;
         blocks += static_cast<int>((n[i] + kSortKps - 1) / kSortKps);
-        active += n[i] > 0;
         cuuint64_t dims[2] = {static_cast<cuuint64_t>(imgs[i].width), static_cast<cuuint64_t>(imgs[i].height)};
         cuuint64_t strides[1] = {static_cast<cuuint64_t>(imgs[i].pitch)};
         cuuint32_t box[2] = {static_cast<cuuint32_t>(tg.tw), static_cast<cuuint32_t>(tg.th)};
@@ -689,16 +676,15 @@ static cudaError_t launch_chunk(const latch_context* ctx, const latch_image* img
             return cudaErrorInvalidValue;
         }
     }
-    prm->active = active;
     e = cudaMemsetAsync(scratch + l.zero, 0, l.total - l.zero, stream);
     if (e == cudaSuccess)
         e = launch_chained(sort_count_kernel<NI>, dim3(blocks), dim3(kSortThreads), 0, stream, *prm, d_kps, cells,
-                           rank, img_tot, img_done, img_base, counters, reinterpret_cast<uint4*>(d_out),
+                           rank, img_tot, img_done, reinterpret_cast<uint4*>(d_out),
                            reinterpret_cast<uint4*>(exp_out), pop_out, ctx->d_flags);
     if (e == cudaSuccess)
         e = launch_chained(sort_scatter_kernel<NI>, dim3(blocks), dim3(kSortThreads), 0, stream, *prm, d_kps,
                            static_cast<const int*>(cells), static_cast<const int*>(rank),
-                           static_cast<const int*>(img_base), recs);
+                           static_cast<const int*>(img_tot), counters, recs);
     if (e == cudaSuccess) {
         // the records are split evenly over the blocks, at least item_kps keypoints each
         const int64_t want = (l.nkp + ctx->item_kps - 1) / ctx->item_kps;

@@ -69,6 +69,9 @@ size_t match_tc_batch_scratch_bytes(int64_t rows, const MatchBatch& b, int64_t c
 int32_t* match_tc_batch_counters(void* scratch, int64_t rows);
 size_t match_tc_partial_bytes(const MatchBatch& b);
 size_t match_tc_counter_bytes(int64_t tiles);
+// Upper bound of match_tc_partial_bytes + match_tc_counter_bytes (each rounded up
+// to 256 bytes) for any launch over `problems` problems, `queries` query rows.
+size_t match_tc_partial_bound(int64_t queries, int64_t problems, int64_t sms);
 // The batched layout: the expanded rows and popcounts of every problem's query and
 // train sets must be filled already, and the arrival counters zero (a complete
 // launch leaves them zero, so consecutive launches need one clearing).

@@ -17,7 +17,9 @@
 //   warp 1     MMA issuer: per unit 16 tcgen05.mma (M=128, N=256, K=32) into one of
 //              two double-buffered 256-column TMEM accumulators;
 //   warp 2     TMEM allocator (all 512 columns);
-//   warps 4-11 epilogue (one query row and 128 columns per thread): double-buffered tcgen05.ld of
+//   warp 3     column keys: per unit, (popc(train row) + 512) << 8 | column into a
+//              4-deep ring in shared memory, ahead of the epilogue;
+//   warps 4-19 epilogue (one query row and 64 columns per thread): double-buffered tcgen05.ld of
 //              the fp32 dot products, key =
 //              ((popc(t) - 2*dot + 512) << 8 | column) formed exactly in fp32 by
 //              one FMA, four interleaved min / second-min chains with FMNMX; the tile's two best are
@@ -47,31 +49,36 @@ using namespace sm103;
 constexpr int kRowsA = 128;             // rows per MMA (M) = query rows per tile
 constexpr int kRowsQ = kRowsA;          // queries per tile
 constexpr int kColsB = 256;             // train rows per unit (N)
-constexpr int kRowsP = 2 * kRowsQ;      // partial records per tile: (row, column half)
+constexpr int kRowsP = kRowsQ;          // partial records per tile slot: one per query row
 constexpr int kKBytes = 512;            // expanded descriptor: 512 x 8-bit
 constexpr int kChunk = 128;             // K bytes per swizzle atom / TMA box
 constexpr int kChunks = kKBytes / kChunk;
 constexpr int kStages = 4;
 constexpr int kTileBytes = kRowsA * kChunk;   // 16 KB: one TMA box of 128 rows x 128 B
 constexpr int kStageBytes = kColsB * kChunk;  // 32 KB: a train chunk of 256 rows x 128 B
-constexpr int kThreads = 384;   // 12 warps: producer, MMA, TMEM, idle, 8 epilogue
-constexpr int kEpiThreads = 256;
+constexpr int kEpiWarps = 16;                       // epilogue: 4 lane quarters x 4 column groups
+constexpr int kEpiThreads = kEpiWarps * 32;
+constexpr int kThreads = 128 + kEpiThreads;         // producer, MMA, TMEM, idle, then the epilogue
+constexpr int kColGroups = kEpiWarps / 4;
+constexpr int kColsPerThread = kColsB / kColGroups;  // accumulator columns one epilogue thread scans
+constexpr int kLdCols = 16;                          // columns per tcgen05.ld (double-buffered)
+constexpr int kKeyStages = 4;                        // column-key vectors prepared ahead of the epilogue
 constexpr int kTmemCols = 512;  // two 256-column accumulators
 constexpr uint32_t kIdesc = idesc_e4m3_f32(kRowsA, kColsB);
 
-// Barrier of the 256 epilogue threads (named barrier 1).
-__device__ __forceinline__ void group_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+// Barrier of the epilogue threads (named barrier 1).
+__device__ __forceinline__ void group_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
 
-// AND of `v` over the 256 epilogue threads (named barrier 1).
+// AND of `v` over the epilogue threads (named barrier 1).
 __device__ __forceinline__ bool group_all(bool v) {
     uint32_t r;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\t"
         "setp.ne.u32 q, %1, 0;\n\t"
-        "bar.red.and.pred p, 1, 256, q;\n\t"
+        "bar.red.and.pred p, 1, %2, q;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(r)
-        : "r"(static_cast<uint32_t>(v))
+        : "r"(static_cast<uint32_t>(v)), "n"(kEpiThreads)
         : "memory");
     return r != 0;
 }
@@ -80,9 +87,10 @@ struct Smem {
     // offsets in the 1024-aligned dynamic buffer
     static constexpr int a = 0;                                        // [kChunks] tiles of 16 KB
     static constexpr int b = a + kChunks * kTileBytes;                 // [kStages] chunks of 32 KB
-    static constexpr int cvec = b + kStages * kStageBytes;             // float [2][kColsB]
-    static constexpr int bars = cvec + 2 * kColsB * 4;                 // uint64 barriers
-    static constexpr int nbars = 2 * kStages + 2 + 4 + 1;
+    static constexpr int cvec = b + kStages * kStageBytes;             // float [kKeyStages][kColsB]
+    static constexpr int part = cvec + kKeyStages * kColsB * 4;        // uint64 [kEpiThreads][2]
+    static constexpr int bars = part + kEpiThreads * 16;               // uint64 barriers
+    static constexpr int nbars = 2 * kStages + 2 + 4 + 1 + 2 * kKeyStages;
     static constexpr int misc = bars + nbars * 8;                      // tmem base, abort flag, last-arrival flag
     static constexpr int total = misc + 16;
 };
@@ -138,9 +146,6 @@ __device__ __forceinline__ void combine_row(const B& b, const MatchProblem& P, i
         const uint64_t* rec = partials + ((g + c) * kRowsP + r) * 2;
         top2_insert_u64(__ldcg(rec), k1, k2);
         top2_insert_u64(__ldcg(rec + 1), k1, k2);
-        const uint64_t* rec2 = rec + 2 * kRowsQ;  // the row's other column half
-        top2_insert_u64(__ldcg(rec2), k1, k2);
-        top2_insert_u64(__ldcg(rec2 + 1), k1, k2);
     }
 }
 
@@ -177,6 +182,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
     uint8_t* sA = smem + Smem::a;
     uint8_t* sB = smem + Smem::b;
     float* sC = reinterpret_cast<float*>(smem + Smem::cvec);
+    uint64_t* sPart = reinterpret_cast<uint64_t*>(smem + Smem::part);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Smem::bars);
     uint64_t* full = bars;
     uint64_t* empty = bars + kStages;
@@ -185,6 +191,8 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
     uint64_t* acc_full = a_full + 2;
     uint64_t* acc_empty = a_full + 4;
     uint64_t* mma_done = a_full + 6;
+    uint64_t* key_full = a_full + 7;               // [kKeyStages]
+    uint64_t* key_empty = key_full + kKeyStages;   // [kKeyStages]
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + Smem::misc);
     volatile int* abort = reinterpret_cast<volatile int*>(smem + Smem::misc + 4);
     volatile int* last_arrival = reinterpret_cast<volatile int*>(smem + Smem::misc + 8);
@@ -207,6 +215,10 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
             mbar_init(&acc_empty[i], kEpiThreads / 32);
         }
         mbar_init(mma_done, 1);
+        for (int i = 0; i < kKeyStages; ++i) {
+            mbar_init(&key_full[i], 32);
+            mbar_init(&key_empty[i], kEpiWarps);
+        }
         *abort = 0;
         fence_mbar_init();
     }
@@ -329,13 +341,33 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
             while (!mbar_try_wait(mma_done, 0) && globaltimer() - t0 < 200000000ull) {
             }
         }
+    } else if (warp == 3) {
+        // ---------------- column keys: for each unit, key(column j) = (popc(train
+        // row) + 512) << 8 | j, or +inf past the train set, into a ring of
+        // kKeyStages vectors, so that the epilogue never waits on these loads ----------------
+        UnitIter it;
+        it.init(batch, u0, u1);
+        for (int64_t u = u0, i = 0; u < u1; ++u, ++i, it.next(batch)) {
+            const int slot = static_cast<int>(i % kKeyStages);
+            const uint32_t par = static_cast<uint32_t>(i / kKeyStages) & 1u;
+            if (!mbar_wait(&key_empty[slot], par ^ 1, abort)) break;
+            const MatchProblem& P = batch.p[it.p];
+            float* kv = sC + slot * kColsB;
+#pragma unroll
+            for (int j = lane; j < kColsB; j += 32) {
+                const int64_t col = static_cast<int64_t>(it.n) * kColsB + j;
+                kv[j] = col < P.nt ? static_cast<float>((pop[P.t_row0 + col] + 512) * 256 + j)
+                                   : __int_as_float(0x7f800000);
+            }
+            mbar_arrive(&key_full[slot]);  // each lane releases its own stores
+        }
     } else if (warp >= 4) {
-        // ---------------- epilogue: 8 warps, thread = one query row ----------------
-        const int et = threadIdx.x - 128;  // 0..255: column of sC this thread fills
+        // ---------------- epilogue: kEpiWarps warps; thread = one query row x one
+        // group of kColsPerThread accumulator columns ----------------
+        const int et = threadIdx.x - 128;  // 0 .. kEpiThreads-1 (et < kColsB: the column of sC it fills)
         const int quarter = warp & 3;      // TMEM lane quarter this warp may access
-        const int half = (warp - 4) >> 2;  // accumulator columns [128*half, 128*half + 128)
+        const int cg = (warp - 4) >> 2;    // column group [cg * kColsPerThread, +kColsPerThread)
         const int row_in_tile = quarter * 32 + lane;
-        const int prow = half * kRowsQ + row_in_tile;  // partial record of (row, half)
         UnitIter it;
         it.init(batch, u0, u1);
         uint32_t acc_par[2] = {0, 0};
@@ -354,57 +386,59 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                 k1 = k2 = kNoKey;
                 prev_g = g;
             }
-            {
-                const int64_t col = n * kColsB + et;
-                sC[buf * kColsB + et] = col < P.nt ? static_cast<float>((pop[P.t_row0 + col] + 512) * 256 + et)
-                                                   : __int_as_float(0x7f800000);
-            }
-            // one vote of the 256 epilogue threads: also publishes sC; exits are group-uniform
-            if (!group_all(mbar_wait(&acc_full[buf], acc_par[buf], abort))) break;
+            const int slot = i % kKeyStages;
+            const uint32_t kpar = static_cast<uint32_t>(i / kKeyStages) & 1u;
+            // one vote of the epilogue threads, so that exits are group-uniform
+            if (!group_all(mbar_wait(&acc_full[buf], acc_par[buf], abort) &&
+                           mbar_wait(&key_full[slot], kpar, abort)))
+                break;
             acc_par[buf] ^= 1;
             tc_fence_after();
-            const float* cv = sC + buf * kColsB;  // (advanced to this warp's half below)
+            const float* cv = sC + slot * kColsB + cg * kColsPerThread;
             const uint32_t base = tmem + (static_cast<uint32_t>(quarter * 32) << 16) +
-                                  static_cast<uint32_t>(buf * kColsB + half * 128);
-            cv += half * 128;
-            // four independent min / second-min chains over the 128 columns
+                                  static_cast<uint32_t>(buf * kColsB + cg * kColsPerThread);
+            // four independent min / second-min chains over this thread's columns
             float m1[4], m2[4];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) m1[c] = m2[c] = __int_as_float(0x7f800000);
-            uint32_t va[32], vb[32];
-            tmem_ld_32x32b_x32(base, va);
+            for (int q = 0; q < 4; ++q) m1[q] = m2[q] = __int_as_float(0x7f800000);
+            uint32_t va[kLdCols], vb[kLdCols];
+            tmem_ld_32x32b_x16(base, va);
             tmem_ld_wait();
+            constexpr int kLds = kColsPerThread / kLdCols;
 #pragma unroll
-            for (int ch = 0; ch < 4; ++ch) {
+            for (int ch = 0; ch < kLds; ++ch) {
                 uint32_t* cur_v = (ch & 1) ? vb : va;
-                if (ch + 1 < 4) tmem_ld_32x32b_x32(base + (ch + 1) * 32, (ch & 1) ? va : vb);
+                if (ch + 1 < kLds) tmem_ld_32x32b_x16(base + (ch + 1) * kLdCols, (ch & 1) ? va : vb);
 #pragma unroll
-                for (int j = 0; j < 32; j += 4) {
-                    const float4 cc = *reinterpret_cast<const float4*>(cv + ch * 32 + j);
+                for (int j = 0; j < kLdCols; j += 4) {
+                    const float4 cc = *reinterpret_cast<const float4*>(cv + ch * kLdCols + j);
                     const float e[4] = {fmaf(__uint_as_float(cur_v[j + 0]), -512.0f, cc.x),
                                         fmaf(__uint_as_float(cur_v[j + 1]), -512.0f, cc.y),
                                         fmaf(__uint_as_float(cur_v[j + 2]), -512.0f, cc.z),
                                         fmaf(__uint_as_float(cur_v[j + 3]), -512.0f, cc.w)};
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const float h = fmaxf(m1[c], e[c]);
-                        m1[c] = fminf(m1[c], e[c]);
-                        m2[c] = fminf(m2[c], h);
+                    for (int q = 0; q < 4; ++q) {
+                        const float h = fmaxf(m1[q], e[q]);
+                        m1[q] = fminf(m1[q], e[q]);
+                        m2[q] = fminf(m2[q], h);
                     }
                 }
-                if (ch + 1 < 4) tmem_ld_wait();
+                if (ch + 1 < kLds) tmem_ld_wait();
             }
             // combine the chains (keys are unique): (a1,a2) + (b1,b2) -> (min, second min)
 #pragma unroll
-            for (int c = 1; c < 4; ++c) {
-                const float lo = fminf(m1[0], m1[c]), hi = fmaxf(m1[0], m1[c]);
-                m2[0] = fminf(hi, fminf(m2[0], m2[c]));
+            for (int q = 1; q < 4; ++q) {
+                const float lo = fminf(m1[0], m1[q]), hi = fmaxf(m1[0], m1[q]);
+                m2[0] = fminf(hi, fminf(m2[0], m2[q]));
                 m1[0] = lo;
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&acc_empty[buf]);
-            // the tile's two best (exact integers below 2^19) -> (distance << 32 | index) keys
+            if (lane == 0) {
+                mbar_arrive(&acc_empty[buf]);
+                mbar_arrive(&key_empty[slot]);
+            }
+            // the unit's two best (exact integers below 2^19) -> (distance << 32 | index) keys
 #pragma unroll
             for (int b = 0; b < 2; ++b) {
                 const float mk = b == 0 ? m1[0] : m2[0];
@@ -416,9 +450,21 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                 }
             }
             if (it.last_of_tile(batch)) {
-                uint64_t* rec = partials + ((g + c) * kRowsP + prow) * 2;
-                rec[0] = k1;
-                rec[1] = k2;
+                // the column groups of each row meet in shared memory; group 0 writes the
+                // row's partial record (slot g + c)
+                sPart[2 * et] = k1;
+                sPart[2 * et + 1] = k2;
+                group_sync();
+                if (cg == 0) {
+#pragma unroll
+                    for (int q = 1; q < kColGroups; ++q) {
+                        top2_insert_u64(sPart[2 * (q * kRowsQ + row_in_tile)], k1, k2);
+                        top2_insert_u64(sPart[2 * (q * kRowsQ + row_in_tile) + 1], k1, k2);
+                    }
+                    uint64_t* rec = partials + ((g + c) * kRowsP + row_in_tile) * 2;
+                    rec[0] = k1;
+                    rec[1] = k2;
+                }
                 if (tile_cnt) {
                     // publish the records; the last owner of the tile to arrive combines them
                     __threadfence();
@@ -432,7 +478,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                         *last_arrival = last;
                     }
                     group_sync();
-                    if (*last_arrival && half == 0) {
+                    if (*last_arrival && cg == 0) {
                         __threadfence();
                         const int64_t row = m * kRowsQ + row_in_tile;
                         uint64_t f1 = kNoKey, f2 = kNoKey;
@@ -572,6 +618,13 @@ static size_t partial_record_bytes(const MatchBatch& b) {
 size_t match_tc_partial_bytes(const MatchBatch& b) { return partial_record_bytes(b); }
 
 size_t match_tc_counter_bytes(int64_t tiles) { return align_up(static_cast<size_t>(tiles) * 4, 256); }
+
+// A launch over `problems` problems with `queries` query rows in total has at most
+// queries / 128 + problems query tiles and at most `sms` blocks.
+size_t match_tc_partial_bound(int64_t queries, int64_t problems, int64_t sms) {
+    const int64_t tiles = queries / kRowsQ + problems;
+    return static_cast<size_t>(tiles + sms) * kRowsP * 16 + match_tc_counter_bytes(tiles) + 512;
+}
 
 size_t match_tc_batch_scratch_bytes(int64_t rows, const MatchBatch& b, int64_t counter_tiles) {
     const size_t exp_bytes = align_up(static_cast<size_t>(rows) * kKBytes, 1024);

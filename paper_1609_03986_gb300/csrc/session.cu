@@ -253,11 +253,9 @@ void scheduler(latch_session* s) {
         const double t = now_s(s);
         while (!s->queue.empty() && static_cast<int>(L.batch.size()) < s->max_batch) {
             Ticket* tk = s->queue.front();
-            // per-batch partial records, (query tiles + blocks) x 256 rows x 16 B, and one
-            // 4-byte arrival counter per query tile; a request of n keypoints has at most
-            // n / 128 + 1 query tiles, a launch at most one block per SM
-            const size_t tiles = static_cast<size_t>((kps + tk->req.n) / 128 + L.batch.size() + 1);
-            const size_t part = (tiles + static_cast<size_t>(s->ctx->sm_count)) * 256 * 16 + tiles * 4 + 1024;
+            // per-batch partial records and arrival counters
+            const size_t part = match_tc_partial_bound(kps + tk->req.n, static_cast<int64_t>(L.batch.size()) + 1,
+                                                       s->ctx->sm_count) + 512;
             if (kps + tk->req.n > s->max_batch_kps || bytes + tk->bytes + part > s->lane_bytes) break;
             s->queue.pop_front();
             bytes += tk->bytes;
@@ -397,7 +395,7 @@ latch_status latch_submit(latch_session* s, const latch_request* r, uint64_t* ti
             ++s->stats.rejected;
             return sfail(s, LATCH_EINVAL, "unknown gallery");
         }
-        const size_t part = static_cast<size_t>(r->n / 256 + 2 + 2 * s->ctx->sm_count) * 256 * 16 + 1024;
+        const size_t part = match_tc_partial_bound(r->n, 1, s->ctx->sm_count) + 512;
         if (r->n > s->max_batch_kps || tk->bytes + part > s->lane_bytes) {
             delete tk;
             ++s->stats.rejected;

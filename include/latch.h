@@ -192,6 +192,33 @@ latch_status latch_reserve_batch(latch_context *ctx, const latch_batch_desc *bat
  * identical to calling latch_extract and hamming_match one by one. */
 latch_status latch_batch_run(latch_context *ctx, const latch_batch_desc *batch, latch_stream_t stream);
 
+/* The batch of latch_batch_run with every buffer in host memory (pinned memory,
+ * cudaHostAlloc / cudaHostRegister, makes the copies asynchronous; pageable memory
+ * works but serialises them).  Layouts as in latch_batch_desc. */
+typedef struct {
+    int32_t n_images;
+    const latch_image *h_images;     /* host array [n_images] of HOST images (any pitch >= width) */
+    const int32_t *h_n_kps;          /* host array [n_images]: keypoints per image */
+    const latch_keypoint *h_kps;     /* host: all keypoints, image by image */
+    uint8_t *h_desc;                 /* host out, 64 bytes per keypoint; NULL: not copied back */
+    int32_t n_pairs;
+    const int32_t *h_pairs;          /* host array [2 * n_pairs]: (query image, train image) */
+    int32_t k;                       /* 1 or 2 */
+    float ratio;                     /* in [0, 1] */
+    latch_match *h_matches;          /* host out */
+} latch_host_batch_desc;
+
+/* latch_batch_run from and to host memory (the end-to-end form of Sec. 4's
+ * pipeline: upload, extract, match, download).  Enqueued without synchronising:
+ * the inputs are copied into one of two device staging sets owned by the context
+ * (alternating per call, grown on demand) on the context's upload stream, then the
+ * batch and the copies of the outputs back to host memory run on `stream`, so once
+ * `stream` is synchronised the host outputs are valid.  The host inputs must stay unchanged, and the outputs
+ * unread, until then.  Consecutive calls overlap: the upload of call i+1 runs while
+ * call i computes.  A call that must grow a staging set first waits for that set's
+ * previous use.  Errors as latch_batch_run. */
+latch_status latch_batch_run_host(latch_context *ctx, const latch_host_batch_desc *batch, latch_stream_t stream);
+
 /* ---- Serving session: extract-and-match requests against resident galleries ----
  *
  * A session owns a context, an HBM budget and a host scheduler thread.  Galleries

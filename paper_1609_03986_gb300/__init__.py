@@ -52,6 +52,13 @@ class latch_batch_desc(ctypes.Structure):
                 ("d_matches", ctypes.c_void_p)]
 
 
+class latch_host_batch_desc(ctypes.Structure):
+    _fields_ = [("n_images", ctypes.c_int32), ("h_images", ctypes.c_void_p), ("h_n_kps", ctypes.c_void_p),
+                ("h_kps", ctypes.c_void_p), ("h_desc", ctypes.c_void_p), ("n_pairs", ctypes.c_int32),
+                ("h_pairs", ctypes.c_void_p), ("k", ctypes.c_int32), ("ratio", ctypes.c_float),
+                ("h_matches", ctypes.c_void_p)]
+
+
 class latch_tuning(ctypes.Structure):
     _fields_ = [("item_kps", ctypes.c_int32), ("tensor_min_pairs", ctypes.c_int64)]
 
@@ -103,6 +110,7 @@ EXPORTS = [
     ("latch_set_tuning", ctypes.c_int, [_P, ctypes.POINTER(latch_tuning)]),
     ("latch_reserve_batch", ctypes.c_int, [_P, ctypes.POINTER(latch_batch_desc)]),
     ("latch_batch_run", ctypes.c_int, [_P, ctypes.POINTER(latch_batch_desc), _P]),
+    ("latch_batch_run_host", ctypes.c_int, [_P, ctypes.POINTER(latch_host_batch_desc), _P]),
     ("latch_session_create", ctypes.c_int, [ctypes.c_int, ctypes.c_size_t, _I64, _I32, _I64, _P,
                                             ctypes.POINTER(_P)]),
     ("latch_session_destroy", ctypes.c_int, [_P]),
@@ -240,6 +248,31 @@ def latch_reserve_batch(ctx, batch: BatchDesc) -> None:
 
 def latch_batch_run(ctx, batch: BatchDesc, stream: int = 0) -> None:
     _check(ctx, library().latch_batch_run(ctx, ctypes.byref(batch.desc), stream))
+
+
+class HostBatchDesc:
+    """Host-side arrays of a latch_host_batch_desc, kept alive with the struct.
+
+    images: list of (host pointer, width, height, pitch); n_kps: list of ints;
+    pairs: list of (query image, train image); h_kps / h_desc / h_matches: host
+    buffers (pinned for asynchronous copies), h_desc may be None."""
+
+    def __init__(self, images, n_kps, h_kps, h_desc, pairs, k, ratio, h_matches):
+        self._imgs = (latch_image * max(1, len(images)))(*[latch_image(_ptr(p), w, h, pt) for p, w, h, pt in images])
+        self._n = np.ascontiguousarray(n_kps, dtype=np.int32)
+        self._pairs = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+        self.desc = latch_host_batch_desc(len(images), ctypes.addressof(self._imgs), self._n.ctypes.data,
+                                          _ptr(h_kps), _ptr(h_desc), self._pairs.shape[0], self._pairs.ctypes.data,
+                                          k, ratio, _ptr(h_matches))
+
+    def match_offsets(self):
+        """First match record of every pair."""
+        q = self._n[self._pairs[:, 0]].astype(np.int64)
+        return np.concatenate([[0], np.cumsum(q)])
+
+
+def latch_batch_run_host(ctx, batch: HostBatchDesc, stream: int = 0) -> None:
+    _check(ctx, library().latch_batch_run_host(ctx, ctypes.byref(batch.desc), stream))
 
 
 def _scheck(sess, status: int):

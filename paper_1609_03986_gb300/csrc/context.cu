@@ -94,6 +94,13 @@ static latch_status upload_scales(latch_context* ctx, const double* scales, int 
         if (dev) cudaFree(dev);
         return cuda_check(ctx, e, "upload offset tables");
     }
+    for (latch::HostStaging& h : ctx->staging) {
+        for (latch::Scratch* sc : {&h.img, &h.kps, &h.desc, &h.matches})
+            if (sc->ptr) cudaFree(sc->ptr);
+        for (cudaEvent_t e : {h.in_ready, h.out_done})
+            if (e) cudaEventDestroy(e);
+    }
+    if (ctx->up_stream) cudaStreamDestroy(ctx->up_stream);
     if (ctx->d_tile_offsets) cudaFree(ctx->d_tile_offsets);
     ctx->d_tile_offsets = dev;
     ctx->nscales = n;
@@ -232,6 +239,13 @@ latch_status latch_context_destroy(latch_context* ctx) {
     latch_trace_enable(ctx, 0);
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
+    for (latch::HostStaging& h : ctx->staging) {
+        for (latch::Scratch* sc : {&h.img, &h.kps, &h.desc, &h.matches})
+            if (sc->ptr) cudaFree(sc->ptr);
+        for (cudaEvent_t e : {h.in_ready, h.out_done})
+            if (e) cudaEventDestroy(e);
+    }
+    if (ctx->up_stream) cudaStreamDestroy(ctx->up_stream);
     if (ctx->d_tile_offsets) cudaFree(ctx->d_tile_offsets);
     if (ctx->d_trip) cudaFree(ctx->d_trip);
     if (ctx->d_trip_offsets) cudaFree(ctx->d_trip_offsets);

@@ -39,6 +39,14 @@ struct Scratch {
     size_t bytes = 0;
 };
 
+// One device staging set of latch_batch_run_host: images, keypoints, descriptors,
+// matches (grow-only), and the events that order its use.
+struct HostStaging {
+    Scratch img, kps, desc, matches;
+    cudaEvent_t in_ready = nullptr;  // uploads done (upload stream)
+    cudaEvent_t out_done = nullptr;  // batch and downloads done (caller's stream): the set is free again
+};
+
 }  // namespace latch
 
 struct latch_context {
@@ -61,6 +69,10 @@ struct latch_context {
     int32_t trace_cap = 0, trace_n = 0;
     int64_t tensor_min_pairs = int64_t(1) << 22;  // matching: AUTO uses the tensor path from here
     latch::Scratch scratch[4];           // grow-only scratch regions
+    // latch_batch_run_host: two staging sets used alternately, upload stream
+    latch::HostStaging staging[2];
+    cudaStream_t up_stream = nullptr;
+    uint64_t host_calls = 0;
     char err[256] = {};
 };
 

@@ -129,3 +129,52 @@ def test_more_pairs_than_one_launch(gpu_ctx, triplets):
     assert np.all(matches[600]["idx1"] == -1) and np.all(matches[600]["dist1"] == 65535)
     rows = rng.choice(counts[pairs[3][0]], min(5, counts[pairs[3][0]]), replace=False)
     _same(matches[3][rows], oracle.match(descs[pairs[3][0]][rows], descs[pairs[3][1]], 2, 0.8))
+
+
+def _pinned(a: np.ndarray) -> torch.Tensor:
+    t = torch.empty(a.nbytes, dtype=torch.uint8, pin_memory=True)
+    t.numpy()[:] = np.ascontiguousarray(a).view(np.uint8).reshape(-1)
+    return t
+
+
+def test_host_batch_pipelined_equals_device_batch(gpu_ctx, triplets):
+    """latch_batch_run_host: three calls with different inputs enqueued back to back
+    (the two staging sets alternate, uploads overlap the previous call's kernels,
+    the first call grows the sets), synchronised once; each call's host outputs
+    equal latch_batch_run on device copies of the same inputs."""
+    sizes = [(320, 240), (641, 480), (200, 150), (1000, 700)]
+    pairs = [(0, 1), (1, 0), (2, 3), (3, 2), (1, 3)]
+    calls = []
+    for c in range(3):
+        imgs, kps = [], []
+        for i, (w, h) in enumerate(sizes):
+            imgs.append(synth.image(synth.seed(36, 10 * c + i, synth.KIND_IMAGE), w, h, n_ellipses=20))
+            kps.append(synth.keypoints(synth.seed(36, 10 * c + i, synth.KIND_KEYPOINTS), w, h,
+                                       [400, 1500, 0, 2200][i] + 37 * c, 0, True, 3))
+        calls.append((imgs, kps))
+    stream = torch.cuda.current_stream()
+    outs = []
+    for imgs, kps in calls:
+        n = [len(k) for k in kps]
+        h_imgs = [_pinned(im) for im in imgs]
+        h_kps = _pinned(np.concatenate([P.pack_keypoints(k) for k in kps]))
+        h_desc = torch.zeros(sum(n) * 64, dtype=torch.uint8, pin_memory=True)
+        nout = sum(n[q] for q, _ in pairs)
+        h_m = torch.zeros(nout * 16, dtype=torch.uint8, pin_memory=True)
+        # host rows keep synth.image's padded pitch (the array's row stride)
+        hb = P.HostBatchDesc([(t, w, h, im.shape[1]) for t, im, (w, h) in zip(h_imgs, imgs, sizes)], n, h_kps,
+                             h_desc, pairs, 2, 0.8, h_m)
+        P.latch_batch_run_host(gpu_ctx.handle, hb, int(stream.cuda_stream))
+        outs.append((h_imgs, h_kps, h_desc, h_m, hb, n))  # inputs stay alive until the sync
+    torch.cuda.synchronize()
+    gpu_ctx.check()
+    for (imgs, kps), (_, _, h_desc, h_m, hb, n) in zip(calls, outs):
+        descs, matches = _run_batch(gpu_ctx, imgs, sizes, kps, pairs)
+        off = np.concatenate([[0], np.cumsum(n)]).astype(np.int64)
+        got_d = h_desc.numpy().reshape(-1, 64)
+        for i in range(len(imgs)):
+            assert np.array_equal(got_d[off[i]:off[i + 1]], descs[i]), i
+        mo = hb.match_offsets()
+        recs = P.matches_from_bytes(h_m.numpy().reshape(-1, 16))
+        for p in range(len(pairs)):
+            _same(recs[mo[p]:mo[p + 1]], matches[p])

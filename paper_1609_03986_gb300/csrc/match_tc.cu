@@ -96,57 +96,103 @@ struct Smem {
 };
 constexpr int kSmemBytes = Smem::total + 1024;
 
-// Walks the units of a block's range in increasing order without dividing:
-// (problem p, query tile m, train tile n) of the current unit, and g = the global
-// index of its query tile.  last_of_tile(): the next unit is in another query tile
-// (or beyond the range).
+// Walks the units of block c: for every problem in turn, the block's share of that
+// problem's U units, [start(c'), start(c' + 1)) with start(x) = floor(x U / G) and
+// c' = (c - unit0) mod G (the rotation continues each problem where the previous
+// one ended, so problems smaller than G still spread over all blocks), without
+// dividing inside a share.  All blocks thus work on the same problem at a time and
+// share its train set in L2.  last_of_tile(): the next unit of the walk is in
+// another query tile.  A block's record of tile g in problem p sits in slot
+// g + c' + p (G - 1): within a problem a later share never touches an earlier
+// tile, and the problems' slot ranges follow one another.
 struct UnitIter {
-    int p;
-    int32_t m, n;
-    int64_t u, u_end;
+    int p;          // current problem (count once the walk is over)
+    int32_t m, n;   // query tile, train tile of the current unit
+    int32_t cs;     // c': the block's share index in problem p
+    int64_t left;   // units left in the share, the current one included
     template <class B>
-    __device__ __forceinline__ void init(const B& b, int64_t u0, int64_t u1) {
-        p = 0;
-        while (p + 1 < b.count && b.p[p + 1].unit0 <= u0) ++p;
-        const int64_t r = u0 - b.p[p].unit0;
-        m = static_cast<int32_t>(r / b.p[p].ntl);
-        n = static_cast<int32_t>(r - static_cast<int64_t>(m) * b.p[p].ntl);
-        u = u0;
-        u_end = u1;
+    __device__ __forceinline__ void seek(const B& b, int64_t c) {
+        for (++p; p < b.count; ++p) {
+            const MatchProblem& P = b.p[p];
+            const int64_t U = static_cast<int64_t>(P.mt) * P.ntl;
+            if (U == 0) continue;
+            const int64_t rot = P.unit0 % b.grid;
+            const int64_t cp = c >= rot ? c - rot : c - rot + b.grid;
+            const int64_t s0 = split_start(cp, U, b.grid), s1 = split_start(cp + 1, U, b.grid);
+            if (s1 > s0) {
+                m = static_cast<int32_t>(s0 / P.ntl);
+                n = static_cast<int32_t>(s0 - static_cast<int64_t>(m) * P.ntl);
+                cs = static_cast<int32_t>(cp);
+                left = s1 - s0;
+                return;
+            }
+        }
     }
+    template <class B>
+    __device__ __forceinline__ void init(const B& b, int64_t c) {
+        p = -1;
+        seek(b, c);
+    }
+    template <class B>
+    __device__ __forceinline__ bool done(const B& b) const { return p >= b.count; }
     template <class B>
     __device__ __forceinline__ int64_t g(const B& b) const { return b.p[p].g0 + m; }
     template <class B>
-    __device__ __forceinline__ bool last_of_tile(const B& b) const {
-        return u + 1 >= u_end || n + 1 == b.p[p].ntl;
+    __device__ __forceinline__ int64_t slot(const B& b) const {
+        return b.p[p].g0 + m + cs + static_cast<int64_t>(p) * (b.grid - 1);
     }
     template <class B>
-    __device__ __forceinline__ void next(const B& b) {
-        ++u;
+    __device__ __forceinline__ bool last_of_tile(const B& b) const { return left == 1 || n + 1 == b.p[p].ntl; }
+    template <class B>
+    __device__ __forceinline__ void next(const B& b, int64_t c) {
+        if (--left == 0) {
+            seek(b, c);
+            return;
+        }
         if (++n == b.p[p].ntl) {
             n = 0;
-            if (++m == b.p[p].mt) {
-                m = 0;
-                ++p;
-                while (p + 1 < b.count && b.p[p].mt * static_cast<int64_t>(b.p[p].ntl) == 0) ++p;  // skip empty
-            }
+            ++m;
         }
     }
 };
 
-// Combines the partial records of row r of query tile (problem P, tile m, global
-// index g) over the blocks that own the tile's units.
+// Calls f(c') for the share index of every block that holds a record of query tile
+// m of problem P, and returns how many there are.  With U >= G every share is
+// non-empty and the owners are the contiguous range from the share of the tile's
+// first unit to that of its last; with U < G every non-empty share holds one unit,
+// so the owners are those of the tile's ntl units.
+template <class B, class F>
+__device__ __forceinline__ int64_t for_each_owner(const B& b, const MatchProblem& P, int64_t m, F&& f) {
+    const int64_t U = static_cast<int64_t>(P.mt) * P.ntl;
+    const int64_t u0 = m * P.ntl;
+    if (U >= b.grid) {
+        const int64_t clo = split_owner(u0, U, b.grid), chi = split_owner(u0 + P.ntl - 1, U, b.grid);
+        for (int64_t cs = clo; cs <= chi; ++cs) f(cs);
+        return chi - clo + 1;
+    }
+    for (int64_t u = u0; u < u0 + P.ntl; ++u) f(split_owner(u, U, b.grid));
+    return P.ntl;
+}
+
+// Number of blocks that hold a record of query tile m of problem P.
 template <class B>
-__device__ __forceinline__ void combine_row(const B& b, const MatchProblem& P, int64_t m, int64_t g, int r,
+__device__ __forceinline__ int64_t tile_owner_count(const B& b, const MatchProblem& P, int64_t m) {
+    const int64_t U = static_cast<int64_t>(P.mt) * P.ntl;
+    if (U < b.grid) return P.ntl;
+    const int64_t u0 = m * P.ntl;
+    return split_owner(u0 + P.ntl - 1, U, b.grid) - split_owner(u0, U, b.grid) + 1;
+}
+
+// Combines the partial records of row r of query tile m (global index g) of problem
+// p over the blocks that own the tile's units.
+template <class B>
+__device__ __forceinline__ void combine_row(const B& b, int p, int64_t m, int64_t g, int r,
                                             const uint64_t* partials, uint64_t& k1, uint64_t& k2) {
-    const int64_t ua = P.unit0 + m * P.ntl, ub = ua + P.ntl - 1;
-    const int64_t clo = split_owner(ua, b.units, b.grid);
-    const int64_t chi = split_owner(ub, b.units, b.grid);
-    for (int64_t c = clo; c <= chi; ++c) {
-        const uint64_t* rec = partials + ((g + c) * kRowsP + r) * 2;
+    for_each_owner(b, b.p[p], m, [&](int64_t cs) {
+        const uint64_t* rec = partials + ((g + cs + static_cast<int64_t>(p) * (b.grid - 1)) * kRowsP + r) * 2;
         top2_insert_u64(__ldcg(rec), k1, k2);
         top2_insert_u64(__ldcg(rec + 1), k1, k2);
-    }
+    });
 }
 
 // The output record of a query from its two best keys (Sec. 4 ratio test).
@@ -200,8 +246,6 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int64_t c = blockIdx.x;
-    const int64_t u0 = split_start(c, batch.units, batch.grid);
-    const int64_t u1 = split_start(c + 1, batch.units, batch.grid);
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < kStages; ++i) {
@@ -238,14 +282,14 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
         // ---------------- TMA producer ----------------
         if (lane == 0) {
             UnitIter it;
-            it.init(batch, u0, u1);
+            it.init(batch, c);
             int stage = 0;
             uint32_t ring = 0, a_par = 0;
             uint32_t fill_par[kStages];
             bool filled[kStages];
             for (int s = 0; s < kStages; ++s) filled[s] = false, fill_par[s] = 0;
             int64_t prev_g = -1;
-            for (int64_t u = u0; u < u1; ++u, it.next(batch)) {
+            for (; !it.done(batch); it.next(batch, c)) {
                 const MatchProblem& P = batch.p[it.p];
                 const int64_t m = it.m, n = it.n;
                 const int64_t g = it.g(batch);
@@ -294,13 +338,13 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             UnitIter it;
-            it.init(batch, u0, u1);
+            it.init(batch, c);
             int stage = 0;
             uint32_t ring = 0, a_par = 0;
             uint32_t acc_par[2] = {0, 0};
             int64_t prev_g = -1;
             int i = 0;
-            for (int64_t u = u0; u < u1 && !*abort; ++u, ++i, it.next(batch)) {
+            for (; !it.done(batch) && !*abort; ++i, it.next(batch, c)) {
                 const int64_t g = it.g(batch);
                 const int buf = i & 1;
                 if (g != prev_g) {
@@ -346,8 +390,8 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
         // row) + 512) << 8 | j, or +inf past the train set, into a ring of
         // kKeyStages vectors, so that the epilogue never waits on these loads ----------------
         UnitIter it;
-        it.init(batch, u0, u1);
-        for (int64_t u = u0, i = 0; u < u1; ++u, ++i, it.next(batch)) {
+        it.init(batch, c);
+        for (int64_t i = 0; !it.done(batch); ++i, it.next(batch, c)) {
             const int slot = static_cast<int>(i % kKeyStages);
             const uint32_t par = static_cast<uint32_t>(i / kKeyStages) & 1u;
             if (!mbar_wait(&key_empty[slot], par ^ 1, abort)) break;
@@ -369,13 +413,13 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
         const int cg = (warp - 4) >> 2;    // column group [cg * kColsPerThread, +kColsPerThread)
         const int row_in_tile = quarter * 32 + lane;
         UnitIter it;
-        it.init(batch, u0, u1);
+        it.init(batch, c);
         uint32_t acc_par[2] = {0, 0};
         uint64_t k1 = kNoKey, k2 = kNoKey;
         int32_t pq = 0;
         int64_t prev_g = -1;
         int i = 0;
-        for (int64_t u = u0; u < u1; ++u, ++i, it.next(batch)) {
+        for (; !it.done(batch); ++i, it.next(batch, c)) {
             const MatchProblem& P = batch.p[it.p];
             const int64_t m = it.m, n = it.n;
             const int64_t g = it.g(batch);
@@ -461,7 +505,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                         top2_insert_u64(sPart[2 * (q * kRowsQ + row_in_tile)], k1, k2);
                         top2_insert_u64(sPart[2 * (q * kRowsQ + row_in_tile) + 1], k1, k2);
                     }
-                    uint64_t* rec = partials + ((g + c) * kRowsP + row_in_tile) * 2;
+                    uint64_t* rec = partials + (it.slot(batch) * kRowsP + row_in_tile) * 2;
                     rec[0] = k1;
                     rec[1] = k2;
                 }
@@ -470,10 +514,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                     __threadfence();
                     group_sync();
                     if (et == 0) {
-                        const int64_t ua = P.unit0 + m * P.ntl;
-                        const int64_t owners = split_owner(ua + P.ntl - 1, batch.units, batch.grid) -
-                                               split_owner(ua, batch.units, batch.grid) + 1;
-                        const bool last = atomicAdd(&tile_cnt[g], 1) == owners - 1;
+                        const bool last = atomicAdd(&tile_cnt[g], 1) == tile_owner_count(batch, P, m) - 1;
                         if (last) tile_cnt[g] = 0;  // no other block touches it again: leave it zero
                         *last_arrival = last;
                     }
@@ -482,7 +523,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                         __threadfence();
                         const int64_t row = m * kRowsQ + row_in_tile;
                         uint64_t f1 = kNoKey, f2 = kNoKey;
-                        combine_row(batch, P, m, g, row_in_tile, partials, f1, f2);
+                        combine_row(batch, it.p, m, g, row_in_tile, partials, f1, f2);
                         if (row < P.nq) out[P.out0 + row] = final_match(f1, f2, P.k, P.r_milli);
                     }
                 }
@@ -515,7 +556,7 @@ __global__ void match_merge_kernel(const __grid_constant__ MatchBatchT<NP> batch
     uint64_t k1 = kNoKey, k2 = kNoKey;
     if (P.ntl > 0) {
         const int64_t m = ql / kRowsQ;
-        combine_row(batch, P, m, P.g0 + m, static_cast<int>(ql % kRowsQ), partials, k1, k2);
+        combine_row(batch, lo, m, P.g0 + m, static_cast<int>(ql % kRowsQ), partials, k1, k2);
     }
     out[q] = final_match(k1, k2, P.k, P.r_milli);
 }
@@ -608,11 +649,9 @@ void plan_match_batch(MatchBatch* b, int count, int64_t max_grid) {
     b->grid = units < max_grid ? units : max_grid;
 }
 
-// Block c's record of query tile g sits in slot g + c: blocks own increasing unit
-// ranges, so a later block never touches an earlier tile and the slots of
-// different (block, tile) pairs differ; tiles + grid - 1 slots suffice.
+// Slots g + c' + p (G - 1) (UnitIter): tiles + count (G - 1) of them.
 static size_t partial_record_bytes(const MatchBatch& b) {
-    return static_cast<size_t>(b.tiles + b.grid) * kRowsP * 16;
+    return static_cast<size_t>(b.tiles + static_cast<int64_t>(b.count) * b.grid + 1) * kRowsP * 16;
 }
 
 size_t match_tc_partial_bytes(const MatchBatch& b) { return partial_record_bytes(b); }
@@ -623,7 +662,7 @@ size_t match_tc_counter_bytes(int64_t tiles) { return align_up(static_cast<size_
 // queries / 128 + problems query tiles and at most `sms` blocks.
 size_t match_tc_partial_bound(int64_t queries, int64_t problems, int64_t sms) {
     const int64_t tiles = queries / kRowsQ + problems;
-    return static_cast<size_t>(tiles + sms) * kRowsP * 16 + match_tc_counter_bytes(tiles) + 512;
+    return static_cast<size_t>(tiles + problems * sms + 1) * kRowsP * 16 + match_tc_counter_bytes(tiles) + 512;
 }
 
 size_t match_tc_batch_scratch_bytes(int64_t rows, const MatchBatch& b, int64_t counter_tiles) {

@@ -105,34 +105,49 @@ constexpr int kSmemBytes = Smem::total + 1024;
 // another query tile.  A block's record of tile g in problem p sits in slot
 // g + c' + p (G - 1): within a problem a later share never touches an earlier
 // tile, and the problems' slot ranges follow one another.
+// A block's share of one problem: the first unit (m, n), the share index and the
+// number of units; p == count when there is none left.
+struct Share {
+    int32_t p, m, n, cs;
+    int64_t left;
+};
+
+// The first problem from p on in which block c has a non-empty share.  Out of line:
+// it divides, and runs only where a share starts.
+template <class B>
+__device__ __noinline__ Share next_share(const B& b, int p, int64_t c) {
+    for (; p < b.count; ++p) {
+        const MatchProblem& P = b.p[p];
+        const int64_t U = static_cast<int64_t>(P.mt) * P.ntl;
+        if (U == 0) continue;
+        const int64_t rot = P.unit0 % b.grid;
+        const int64_t cp = c >= rot ? c - rot : c - rot + b.grid;
+        const int64_t s0 = split_start(cp, U, b.grid), s1 = split_start(cp + 1, U, b.grid);
+        if (s1 > s0) {
+            const int32_t m = static_cast<int32_t>(s0 / P.ntl);
+            return Share{p, m, static_cast<int32_t>(s0 - static_cast<int64_t>(m) * P.ntl), static_cast<int32_t>(cp),
+                         s1 - s0};
+        }
+    }
+    return Share{b.count, 0, 0, 0, 0};
+}
+
 struct UnitIter {
     int p;          // current problem (count once the walk is over)
     int32_t m, n;   // query tile, train tile of the current unit
     int32_t cs;     // c': the block's share index in problem p
     int64_t left;   // units left in the share, the current one included
     template <class B>
-    __device__ __forceinline__ void seek(const B& b, int64_t c) {
-        for (++p; p < b.count; ++p) {
-            const MatchProblem& P = b.p[p];
-            const int64_t U = static_cast<int64_t>(P.mt) * P.ntl;
-            if (U == 0) continue;
-            const int64_t rot = P.unit0 % b.grid;
-            const int64_t cp = c >= rot ? c - rot : c - rot + b.grid;
-            const int64_t s0 = split_start(cp, U, b.grid), s1 = split_start(cp + 1, U, b.grid);
-            if (s1 > s0) {
-                m = static_cast<int32_t>(s0 / P.ntl);
-                n = static_cast<int32_t>(s0 - static_cast<int64_t>(m) * P.ntl);
-                cs = static_cast<int32_t>(cp);
-                left = s1 - s0;
-                return;
-            }
-        }
+    __device__ __forceinline__ void take(const B& b, int from, int64_t c) {
+        const Share s = next_share(b, from, c);
+        p = s.p;
+        m = s.m;
+        n = s.n;
+        cs = s.cs;
+        left = s.left;
     }
     template <class B>
-    __device__ __forceinline__ void init(const B& b, int64_t c) {
-        p = -1;
-        seek(b, c);
-    }
+    __device__ __forceinline__ void init(const B& b, int64_t c) { take(b, 0, c); }
     template <class B>
     __device__ __forceinline__ bool done(const B& b) const { return p >= b.count; }
     template <class B>
@@ -146,7 +161,7 @@ struct UnitIter {
     template <class B>
     __device__ __forceinline__ void next(const B& b, int64_t c) {
         if (--left == 0) {
-            seek(b, c);
+            take(b, p + 1, c);
             return;
         }
         if (++n == b.p[p].ntl) {

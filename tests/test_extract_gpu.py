@@ -75,6 +75,23 @@ def test_tiny_and_odd_images(gpu_ctx, triplets):
         assert np.array_equal(got, oracle.extract(img, w, h, kps, triplets, synth.SCALES))
 
 
+def test_longest_image_sides(gpu_ctx, triplets):
+    """Images at the 32,768-pixel limit in either direction, keypoints at, near and
+    beyond the far corners (some far enough that their windows miss the image, some
+    at coordinates near the int32 range), every scale."""
+    rng = np.random.default_rng(13)
+    for w, h in ((32768, 40), (40, 32768)):
+        img = synth.image(synth.seed(13, w, synth.KIND_IMAGE), w, h, n_ellipses=20)
+        pts = []
+        for x0, y0 in ((0, 0), (w - 1, 0), (0, h - 1), (w - 1, h - 1), (w // 2, h // 2)):
+            for dx, dy in ((0, 0), (-60, 30), (90, -90), (-130, 0), (0, 140), (200, 200)):
+                pts.append([x0 + dx, y0 + dy, int(rng.integers(0, 32)), int(rng.integers(0, 3))])
+        pts += [[2**30, 5, 3, 1], [-2**30, -2**30, 7, 2], [w + 77, h + 77, 9, 2]]
+        kps = np.array(pts, np.int32)
+        got = _extract(gpu_ctx, img, w, h, kps)
+        assert np.array_equal(got, oracle.extract(img, w, h, kps, triplets, synth.SCALES)), (w, h)
+
+
 def test_empty_and_invalid_arguments(gpu_ctx, triplets):
     img = torch.zeros((64, 64), dtype=torch.uint8, device="cuda")
     kps = torch.zeros((0, 12), dtype=torch.uint8, device="cuda")

@@ -178,3 +178,23 @@ def test_host_batch_pipelined_equals_device_batch(gpu_ctx, triplets):
         recs = P.matches_from_bytes(h_m.numpy().reshape(-1, 16))
         for p in range(len(pairs)):
             _same(recs[mo[p]:mo[p + 1]], matches[p])
+
+
+def test_bench_step_full_size(gpu_ctx, triplets):
+    """The bench's step exactly: latch_batch_run on the 2 x 1920x1080, 10,000-keypoint
+    oriented and scaled pair, 10k x 10k top-2 (ratio 0.8).  Every descriptor equals the
+    plain latch_extract; 400 sampled keypoints per image and 64 sampled query rows
+    (against the full train set) equal the oracle."""
+    wl = synth.pair("oriented_scaled_1920x1080_10k")
+    w, h = wl["width"], wl["height"]
+    descs, matches = _run_batch(gpu_ctx, wl["images"], [(w, h)] * 2, wl["kps"], [(0, 1)])
+    rng = np.random.default_rng(37)
+    for i in range(2):
+        plain = gpu_ctx.extract(to_dev(wl["images"][i]), w, h, to_dev(P.pack_keypoints(wl["kps"][i])))
+        torch.cuda.synchronize()
+        assert np.array_equal(descs[i], plain.cpu().numpy()), i
+        rows = rng.choice(len(wl["kps"][i]), 400, replace=False)
+        want = oracle.extract(wl["images"][i], w, h, wl["kps"][i][rows], triplets, synth.SCALES)
+        assert np.array_equal(descs[i][rows], want), i
+    rows = rng.choice(len(wl["kps"][0]), 64, replace=False)
+    _same(matches[0][rows], oracle.match(descs[0][rows], descs[1], 2, 0.8))

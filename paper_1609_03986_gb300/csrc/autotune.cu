@@ -1,5 +1,6 @@
-// Autotuner: picks, by measurement on this device, (1) the number of keypoints per
-// extraction work item and (2) the pair count from which LATCH_PATH_AUTO matches on
+// Autotuner: picks, by measurement on this device, (1) the fewest keypoints an
+// extraction block takes (which sets the grid on small inputs) and (2) the pair count
+// from which LATCH_PATH_AUTO matches on
 // the tensor cores instead of the CUDA cores.  It runs on synthetic device data
 // shaped like the caller's workload (image size, keypoints, query and train counts),
 // times every candidate with CUDA events (median of 3 after a warm-up), and stores
@@ -106,7 +107,7 @@ latch_status latch_autotune(latch_context* ctx, const latch_tune_shape* shape, l
     cudaStream_t s = nullptr;
     LATCH_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     latch_status st = LATCH_OK;
-    // ---- extraction: keypoints per work item ----
+    // ---- extraction: fewest keypoints per block ----
     if (sh.n_keypoints > 0) {
         const int64_t pitch = (static_cast<int64_t>(sh.width) + 15) / 16 * 16;
         uint8_t *img = nullptr, *out_desc = nullptr;

@@ -134,6 +134,35 @@ def test_triplet_table_switch(gpu_ctx, triplets):
     assert np.array_equal(got, oracle.extract(img, w, h, kps, triplets, synth.SCALES))
 
 
+def test_degenerate_triplet_tables(gpu_ctx, triplets):
+    """Tables with identical companions (bit always 0), the anchor on companion 1
+    (D1 = 0: bit 0) or on companion 2 (bit 1 unless D1 = 0), and patches at the
+    extreme centres 3 and 44; and the regular table with the companions swapped
+    (every bit flips except ties).  GPU = oracle, and the invariants hold."""
+    w, h = 400, 300
+    img = synth.image(synth.seed(14, 0, synth.KIND_IMAGE), w, h, n_ellipses=30)
+    kps = synth.keypoints(synth.seed(14, 0, synth.KIND_KEYPOINTS), w, h, 300, 0, True, 3)
+    rng = np.random.default_rng(14)
+    t = rng.integers(3, 45, (512, 6)).astype(np.uint8)
+    t[0:128, 4:6] = t[0:128, 2:4]      # C2 = C1
+    t[128:256, 2:4] = t[128:256, 0:2]  # C1 = A
+    t[256:384, 4:6] = t[256:384, 0:2]  # C2 = A
+    t[384:512] = rng.choice([3, 44], (128, 6)).astype(np.uint8)
+    got = _extract(gpu_ctx, img, w, h, kps, t)
+    assert np.array_equal(got, oracle.extract(img, w, h, kps, t, synth.SCALES))
+    bits = np.unpackbits(got, axis=1, bitorder="little")
+    assert not bits[:, 0:256].any()
+    swapped = triplets.copy()
+    swapped[:, [2, 3, 4, 5]] = triplets[:, [4, 5, 2, 3]]
+    # (a table passed to a call stays loaded: the regular one goes last)
+    b = np.unpackbits(_extract(gpu_ctx, img, w, h, kps, swapped), axis=1, bitorder="little")
+    a = np.unpackbits(_extract(gpu_ctx, img, w, h, kps, triplets), axis=1, bitorder="little")
+    want = oracle.extract(img, w, h, kps, swapped, synth.SCALES)
+    assert np.array_equal(b, np.unpackbits(want, axis=1, bitorder="little"))
+    assert not (a & b).any()  # never both set: D1 > D2 and D2 > D1 exclude each other
+    assert (a | b).mean() > 0.9  # and one of them is set unless the distances tie
+
+
 def test_device_wait_timeout_is_reported(gpu_ctx, triplets):
     """A device-side wait that can never complete gives up after its limit and the
     host sees LATCH_ETIMEOUT; the context keeps working afterwards."""

@@ -124,7 +124,10 @@ latch_status latch_context_destroy(latch_context *ctx);
 latch_status latch_set_scales(latch_context *ctx, const double *h_scales, int32_t n);
 
 /* Load the 512-triplet table (Sec. 3.1: the triplets are fixed for every
- * keypoint).  Coordinates are checked to lie in [3, 44].  Synchronous. */
+ * keypoint).  Coordinates are checked to lie in [3, 44].  Synchronous.  Each
+ * extraction launch carries the table in its parameters, so a call captured in a
+ * CUDA graph keeps the table (and the scale table) of its capture: capture again
+ * after latch_set_triplets or latch_set_scales. */
 latch_status latch_set_triplets(latch_context *ctx, const latch_triplet *h_triplets);
 
 /* Pre-size the context's scratch memory so that later calls up to these sizes

@@ -125,22 +125,14 @@ static latch_status validate_triplets(latch_context* ctx, const latch_triplet* t
     return LATCH_OK;
 }
 
-static latch_status load_triplets(latch_context* ctx, const latch_triplet* t, cudaStream_t stream, bool sync) {
+// The table reaches the kernels as a launch parameter (copied at each launch), so
+// loading one needs no device copy and orders itself with the calls that follow.
+static latch_status load_triplets(latch_context* ctx, const latch_triplet* t) {
     if (ctx->has_trip && memcmp(ctx->h_trip, t, sizeof(ctx->h_trip)) == 0) return LATCH_OK;
     latch_status st = validate_triplets(ctx, t);
     if (st != LATCH_OK) return st;
     memcpy(ctx->h_trip, t, sizeof(ctx->h_trip));
     build_triplet_offsets(ctx->h_trip, ctx->h_trip_offsets);
-    // The copies are ordered on `stream` before any kernel that reads the tables.
-    cudaError_t e = cudaMemcpyAsync(ctx->d_trip, ctx->h_trip, sizeof(ctx->h_trip), cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(ctx->d_trip_offsets, ctx->h_trip_offsets, sizeof(ctx->h_trip_offsets),
-                            cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess && sync) e = cudaStreamSynchronize(stream);
-    if (e != cudaSuccess) {
-        ctx->has_trip = false;
-        return cuda_check(ctx, e, "upload triplets");
-    }
     ctx->has_trip = true;
     return LATCH_OK;
 }
@@ -178,9 +170,6 @@ latch_status latch_context_create(int device, latch_context** out) {
     ctx->sm_count = prop.multiProcessorCount;
     const double defaults[3] = {1.0, 1.5, 2.25};
     latch_status st = upload_scales(ctx, defaults, 3);
-    if (st == LATCH_OK) st = cuda_check(ctx, cudaMalloc(&ctx->d_trip, sizeof(ctx->h_trip)), "cudaMalloc(triplets)");
-    if (st == LATCH_OK)
-        st = cuda_check(ctx, cudaMalloc(&ctx->d_trip_offsets, sizeof(ctx->h_trip_offsets)), "cudaMalloc(triplets)");
     if (st == LATCH_OK) st = cuda_check(ctx, cudaMalloc(&ctx->d_flags, 64), "cudaMalloc(flags)");
     if (st == LATCH_OK) st = cuda_check(ctx, cudaMemset(ctx->d_flags, 0, 64), "cudaMemset(flags)");
     if (st != LATCH_OK) {
@@ -247,8 +236,6 @@ latch_status latch_context_destroy(latch_context* ctx) {
     }
     if (ctx->up_stream) cudaStreamDestroy(ctx->up_stream);
     if (ctx->d_tile_offsets) cudaFree(ctx->d_tile_offsets);
-    if (ctx->d_trip) cudaFree(ctx->d_trip);
-    if (ctx->d_trip_offsets) cudaFree(ctx->d_trip_offsets);
     if (ctx->d_flags) cudaFree(ctx->d_flags);
     for (auto& s : ctx->scratch)
         if (s.ptr) cudaFree(s.ptr);
@@ -270,7 +257,7 @@ latch_status latch_set_scales(latch_context* ctx, const double* scales, int32_t 
 latch_status latch_set_triplets(latch_context* ctx, const latch_triplet* h_triplets) {
     if (!ctx || !h_triplets) return fail(ctx, LATCH_EINVAL, "NULL argument");
     LATCH_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-    return load_triplets(ctx, h_triplets, nullptr, true);
+    return load_triplets(ctx, h_triplets);
 }
 
 latch_status latch_reserve(latch_context* ctx, int64_t max_keypoints, int64_t max_query, int64_t max_train) {
@@ -330,7 +317,7 @@ latch_status latch_extract(latch_context* ctx, const latch_image* img, const lat
     LATCH_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (h_triplets) {
-        latch_status st = load_triplets(ctx, h_triplets, s, false);
+        latch_status st = load_triplets(ctx, h_triplets);
         if (st != LATCH_OK) return st;
     }
     if (!ctx->has_trip) return fail(ctx, LATCH_EINVAL, "no triplet table: pass one or call latch_set_triplets");

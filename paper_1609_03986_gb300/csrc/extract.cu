@@ -9,30 +9,38 @@
 //    px), whose samples all read 0, so their descriptor is all zeros and is written
 //    here directly.  Keypoints with a scale index outside the scale table also get
 //    zeros and raise the context's device flag.
-// 2. extract_cells_kernel (8 warps per block, four blocks per SM): block b takes
-//    the b-th of G equal shares of the records.  The image tile under a cell plus a
-//    `reach` halo is staged into shared memory by one TMA 2-D load (samples outside
-//    the image arrive as 0, the border reading) whenever the next keypoint lies in
-//    another cell.  For each keypoint in turn, the block
-//      - samples the 48x48 window through the per-(scale, bin) offset table
-//        (nearest pixel; offsets pre-multiplied into tile offsets) and stores it
-//        as 4 byte-shifted copies, so that the 8 bytes holding any 7-pixel patch
-//        row are two aligned 32-bit words;
-//      - evaluates Eq. 1 for 32 triplets per warp at a time, one triplet per lane:
-//        D1 - D2 = (sum C1^2 - sum C2^2) - 2 (sum A.C1 - sum A.C2) over the 7 rows,
-//        with __dp4a on 4 pixels at a time, all exact in 32-bit integers;
-//      - packs the 32 bits of each warp-group with __ballot_sync (bit t = bit
-//        t % 32 of word t / 32, i.e. bit t % 8 of byte t / 8) and writes the
-//        64-byte descriptor as four 128-bit stores (the last warp, which builds no
-//        window, does this); when the caller also wants the tensor matcher's
-//        input, it writes the expanded row (byte t = E4M3 1.0 or 0 for bit t) and
-//        the descriptor's popcount as well, so no separate pass over the
-//        descriptors is needed.
-//    Windows are double-buffered so one __syncthreads per keypoint suffices.
+// 2. extract_lanes_kernel (one block of 28 warps per SM): the records are taken 32
+//    at a time ("batches", in sort order), one keypoint per lane.  A batch's work
+//    is 64 chunks of 8 triplets; the chunks of all batches are split into G equal
+//    contiguous ranges, range b for block b, so a batch may be shared by two
+//    blocks (each builds its windows and evaluates its own chunks).  The block
+//    is a two-stage pipeline over double-buffered windows:
+//      - 12 builder warps build the 32 windows of batch i: for each run of
+//        keypoints in one image cell, the tile under the cell plus a `reach`
+//        halo is staged into shared memory by one TMA 2-D load (samples outside
+//        the image arrive as 0, the border reading; two tile slots, the next
+//        run's tile requested while the current one is read), and every window
+//        pixel is read from it through the per-(scale, bin) offset table
+//        (nearest pixel; offsets pre-multiplied into tile offsets; the table
+//        words are loaded three keypoints ahead).  Window j sits at word 577 j:
+//        with an odd stride, the 32 lanes reading the same word of their
+//        windows hit 32 different banks;
+//      - 16 evaluator warps evaluate Eq. 1 on batch i - 1, warp w on chunks 4w ..
+//        4w+3, all 32 lanes on the same triplet at a time (the triplet table is
+//        staged in shared memory: one broadcast load per triplet): a 7-pixel
+//        patch row is two or three words, aligned by a funnel shift; D1 - D2 =
+//        (sum C1^2 - sum C2^2) - 2 (sum A.C1 - sum A.C2) over the 7 rows with
+//        __dp4a, all exact in 32-bit integers.  Each warp writes its bytes of
+//        every lane's descriptor (bit t = bit t % 8 of byte t / 8) and, when
+//        the caller also wants the tensor matcher's input, the 32-byte sector
+//        of the expanded row (byte t = E4M3 1.0 or 0 for bit t) and adds its
+//        bits to the popcount (which the sort zeroes).
+//    The stages hand the window buffers over through mbarriers (full: 384
+//    builder arrivals, empty: 16 evaluator arrivals); every wait is bounded.
 #include <cuda.h>
 
-#include <cmath>
 #include <cstdint>
+#include <cstring>
 
 #include "internal.h"
 #include "sm103.h"
@@ -45,13 +53,18 @@ using namespace sm103;
 
 constexpr int kCell = 32;
 constexpr int kMargin = 128;            // cell grid reaches this far beyond each border
-constexpr int kThreads = 256;           // 8 warps
+constexpr int kBuildWarps = 12;         // window builders (4, 8, 16 measured slower)
+constexpr int kComputeWarps = 16;       // Eq. 1 evaluators (4 chunks each per batch)
+constexpr int kBuildThreads = 32 * kBuildWarps;
+constexpr int kComputeThreads = 32 * kComputeWarps;
+constexpr int kThreads = kBuildThreads + kComputeThreads;  // 896
 constexpr int kRowWords = 12;           // 48 bytes per window row
-constexpr int kCopyWords = kWin * kRowWords + 4;   // one byte-shifted copy (+4: bank offset; 16-byte multiple)
-constexpr int kWinWords = 4 * kCopyWords;          // 4 copies
+constexpr int kWinWords = kWinPix / 4;  // 576 words per window
+constexpr int kLaneWords = kWinWords + 1;          // window stride: odd, so a warp's same-offset loads hit 32 banks
+constexpr int kBatch = 32;              // keypoints per batch, one per lane
+constexpr int kChunks = kBits / 8;      // chunks of 8 triplets per batch
 constexpr int kSortThreads = 256;
 constexpr int kSortKps = 1024;          // keypoints per sorting block (4 per thread)
-constexpr int kRing = 64;               // keypoint records in flight per block (1 KB: four blocks still fit an SM)
 
 struct CellGrid {
     int gx, gy;  // cells in x / y (including the margins)
@@ -136,6 +149,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_count_kernel(
         const int c = i < n ? cell_of(kp[q], prm.nscales, g) : -3;
         if (c >= 0) {
             rank[kp0 + i] = atomicAdd(&cnt[c], 1);
+            if (pop_out) pop_out[kp0 + i] = 0;  // the extraction adds the chunks' counts
             ++valid;
         } else if (c > -3) {
             const uint4 z = make_uint4(0, 0, 0, 0);
@@ -249,229 +263,311 @@ __global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(
     }
 }
 
-// Offset-table entries 16*bseg .. 16*bseg+19 of window row `by` of table `tab`
-// (scale * 32 + bin): two 16-byte and one 8-byte load.
-__device__ __forceinline__ void load_table_segment(const int16_t* __restrict__ toff, int tab, int by, int bseg,
-                                                   int32_t (&tw)[10]) {
-    const int16_t* t = toff + static_cast<size_t>(tab) * kWinPix + by * kWin + 16 * bseg;
-    const int4 ta = reinterpret_cast<const int4*>(t)[0];
-    const int4 tb = reinterpret_cast<const int4*>(t)[1];
-    const int2 tc = reinterpret_cast<const int2*>(t)[4];
-    tw[0] = ta.x; tw[1] = ta.y; tw[2] = ta.z; tw[3] = ta.w;
-    tw[4] = tb.x; tw[5] = tb.y; tw[6] = tb.z; tw[7] = tb.w;
-    tw[8] = tc.x; tw[9] = tc.y;
-}
-
 // Tile key of a record: launch-local image, cell row and column (the record's
 // keypoint has a cell, so x + kMargin and y + kMargin are >= 0).
 __device__ __forceinline__ int tile_key(const int4& r) {
     return ((r.w >> 16) << 22) | (((r.y + kMargin) / kCell) << 11) | ((r.x + kMargin) / kCell);
 }
 
-// Block b extracts the records [b V / G, (b+1) V / G) of the launch's V records
-// (cell-sorted), one keypoint per step.  Records reach shared memory through a
-// ring filled 32 keypoints ahead by asynchronous copies; the tile under the next
-// keypoint's cell is requested, when the cell changes, right after the barrier of
-// the last keypoint that reads the current tile, so it lands during that
-// keypoint's triplets.
+// Window words of every triplet's three patches (top-left word of the 7x7 patch
+// in a 48x48 window of 12-word rows) and their byte shifts: x = A | C1 << 16,
+// y = C2 | shift A << 16 | shift C1 << 18 | shift C2 << 20.
+struct LaneTriplets {
+    uint2 e[kBits];
+};
+
+// One patch row: the 7 bytes at byte `sh` of word p[0] onwards, as two words whose
+// last byte is junk (the third word is read only when the bytes reach into it).
+__device__ __forceinline__ void patch_row(const uint32_t* p, uint32_t sh, uint32_t& lo, uint32_t& hi) {
+    const uint32_t w0 = p[0], w1 = p[1];
+    const uint32_t w2 = sh >= 2 ? p[2] : 0u;
+    lo = __funnelshift_r(w0, w1, 8 * sh);
+    hi = __funnelshift_r(w1, w2, 8 * sh);
+}
+
+// Bit i of the result: Eq. 1 for triplet 8 c + i of the window at `wl` (`trip`:
+// the LaneTriplets entries, in shared memory: one broadcast load per triplet).
+__device__ __forceinline__ uint32_t eval_chunk(const uint2* trip, const uint32_t* wl, int c) {
+    uint32_t byte = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const uint2 e = trip[8 * c + i];
+        const uint32_t* pa = wl + (e.x & 0xffffu);
+        const uint32_t* p1 = wl + (e.x >> 16);
+        const uint32_t* p2 = wl + (e.y & 0xffffu);
+        const uint32_t sa = (e.y >> 16) & 3u, s1 = (e.y >> 18) & 3u, s2 = (e.y >> 20) & 3u;
+        uint32_t sa1 = 0, sa2 = 0, s11 = 0, s22 = 0;
+#pragma unroll
+        for (int rr = 0; rr < 2 * kPatchR + 1; ++rr) {
+            uint32_t a0, a1, c0, c1, d0, d1;
+            patch_row(pa + rr * kRowWords, sa, a0, a1);
+            patch_row(p1 + rr * kRowWords, s1, c0, c1);
+            patch_row(p2 + rr * kRowWords, s2, d0, d1);
+            c1 &= 0x00ffffffu;  // pixel 8 of the run is not in the patch (A's is multiplied by 0)
+            d1 &= 0x00ffffffu;
+            sa1 = __dp4a(a0, c0, sa1);
+            sa1 = __dp4a(a1, c1, sa1);
+            sa2 = __dp4a(a0, d0, sa2);
+            sa2 = __dp4a(a1, d1, sa2);
+            s11 = __dp4a(c0, c0, s11);
+            s11 = __dp4a(c1, c1, s11);
+            s22 = __dp4a(d0, d0, s22);
+            s22 = __dp4a(d1, d1, s22);
+        }
+        // D1 - D2 = sum C1^2 - sum C2^2 - 2 (sum A.C1 - sum A.C2)
+        const int diff =
+            (static_cast<int>(s11) - static_cast<int>(s22)) - 2 * (static_cast<int>(sa1) - static_cast<int>(sa2));
+        byte |= (diff > 0 ? 1u : 0u) << i;
+    }
+    return byte;
+}
+
+// Expanded row segment for 16 descriptor bits: byte q is 0x38 (E4M3 1.0) when bit q
+// is set.  x * 0x00204081 moves bit q of a 4-bit x to bit 8q (no two partial
+// products overlap).
+__device__ __forceinline__ uint32_t expand4(uint32_t x) { return ((x * 0x00204081u) & 0x01010101u) * 0x38u; }
+__device__ __forceinline__ uint4 expand16(uint32_t h) {
+    return make_uint4(expand4(h & 15u), expand4((h >> 4) & 15u), expand4((h >> 8) & 15u), expand4((h >> 12) & 15u));
+}
+
+struct LanesSmem {  // static part
+    uint2 trip[kBits];                // LaneTriplets
+    int4 rec[2][kBatch];              // builders: the batch's records
+    int32_t row[2][kBatch];           // output row of each lane's keypoint
+    uint64_t tile_bar[2], full[2], empty[2];
+    uint32_t runs[2];
+    int abort;
+};
+
+// Block b takes chunks [b U / G, (b+1) U / G) of the U = 64 * ceil(V / 32) chunks
+// of the launch's V records (cell-sorted), batch by batch.  Warps 0-11 build the
+// windows of batch i into buffer i % 2 while warps 12-27 evaluate batch i - 1.
 template <int NI>
-__global__ void __launch_bounds__(kThreads, 4) extract_cells_kernel(
-    const __grid_constant__ ExtractParams<NI> prm, const int4* __restrict__ recs, const int* __restrict__ counters,
-    const int16_t* __restrict__ toff, const uint2* __restrict__ trip_off, uint4* __restrict__ out,
-    uint4* __restrict__ exp_out, int32_t* __restrict__ pop_out, uint32_t* __restrict__ flags) {
+__global__ void __launch_bounds__(kThreads, 1) extract_lanes_kernel(
+    const __grid_constant__ ExtractParams<NI> prm, const __grid_constant__ LaneTriplets tt,
+    const int4* __restrict__ recs, const int* __restrict__ counters, const int16_t* __restrict__ toff,
+    uint8_t* __restrict__ out, uint8_t* __restrict__ exp_out, int32_t* __restrict__ pop_out,
+    uint32_t* __restrict__ flags) {
     extern __shared__ uint8_t smem_raw[];
-    __shared__ int4 s_rec[kRing];
+    __shared__ LanesSmem S;
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    uint32_t* s_win = reinterpret_cast<uint32_t*>(smem);                  // [2][kWinWords]
-    uint8_t* s_bits = reinterpret_cast<uint8_t*>(s_win + 2 * kWinWords);  // [2][512] one byte per bit
-    uint64_t* s_bar = reinterpret_cast<uint64_t*>(s_bits + 2 * kBits);
-    volatile int* s_abort = reinterpret_cast<volatile int*>(s_bar + 1);
-    uint8_t* s_tile = reinterpret_cast<uint8_t*>(s_bar + 2);
-    s_tile = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(s_tile) + 127) & ~uintptr_t(127));
     const TileGeom tg = prm.tg;
+    const int tile_bytes = (tg.tw * tg.th + 127) / 128 * 128;
+    uint32_t* s_win0 = reinterpret_cast<uint32_t*>(smem);  // [2][32][kLaneWords]
+    uint8_t* s_tile0 = smem + 2 * static_cast<size_t>(kBatch) * kLaneWords * 4;  // [2][tile_bytes]
     griddep_wait();
     griddep_launch_dependents();
     const int nrec = counters[0];
-    const int j0 = static_cast<int>(static_cast<int64_t>(blockIdx.x) * nrec / gridDim.x);
-    const int m = static_cast<int>(static_cast<int64_t>(blockIdx.x + 1) * nrec / gridDim.x) - j0;
-    if (m <= 0) return;
-    const int4* brec = recs + j0;
-
+    if (nrec <= 0) return;
+    const int64_t units = static_cast<int64_t>((nrec + kBatch - 1) / kBatch) * kChunks;
+    const int64_t u0 = static_cast<int64_t>(blockIdx.x) * units / gridDim.x;
+    const int64_t u1 = static_cast<int64_t>(blockIdx.x + 1) * units / gridDim.x;
+    if (u0 >= u1) return;
+    const int bfirst = static_cast<int>(u0 / kChunks), blast = static_cast<int>((u1 - 1) / kChunks);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr int kLastWarp = kThreads / 32 - 1;
+    volatile int* abort = &S.abort;
     if (threadIdx.x == 0) {
-        mbar_init(s_bar, 1);
-        *s_abort = 0;
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&S.tile_bar[s], 1);
+            mbar_init(&S.full[s], kBuildThreads);
+            mbar_init(&S.empty[s], kComputeWarps);
+        }
+        S.abort = 0;
         fence_mbar_init();
     }
-    for (int t = threadIdx.x; t < m && t < kRing - 32; t += kThreads) s_rec[t] = brec[t];
-    // this thread's window-build job (threads 0..143): row by, 16-pixel segment bseg
-    const int by = threadIdx.x / 3, bseg = threadIdx.x % 3;
-    // this lane's two triplets (slots 64*warp + lane and +32 of the bank-conflict
-    // minimising order): patch word offsets and the triplet's bit position
-    const uint2 to0 = trip_off[64 * warp + lane];
-    const uint2 to1 = trip_off[64 * warp + 32 + lane];
-    __syncthreads();
+    if (threadIdx.x < kBatch && kBatch * bfirst + lane < nrec) S.rec[0][lane] = recs[kBatch * bfirst + lane];
+    for (int t = threadIdx.x; t < kBits; t += kThreads) S.trip[t] = tt.e[t];
+    __syncthreads();  // the last block-wide barrier: the two roles meet only at mbarriers from here on
 
-    int cur_key = -1, ox = 0, oy = 0;
-    uint32_t tile_par = 0;
-    auto issue_tile = [&](const int4& r) {  // thread 0
-        const int key = tile_key(r);
-        const int img = key >> 22;
-        const int tx = (key & 2047) * kCell - kMargin + tg.mx, ty = ((key >> 11) & 2047) * kCell - kMargin + tg.my;
-        mbar_arrive_expect_tx(s_bar, static_cast<uint32_t>(tg.tw * tg.th));
-        tma_load_2d(s_tile, &prm.map[img], tx, ty, s_bar);
-    };
-    if (threadIdx.x == 0) issue_tile(s_rec[0]);
-
-    // offset-table entries 0..19 of this thread's row segment for the first keypoint
-    // (32-byte aligned: 96*by + 32*bseg bytes); later ones are prefetched one keypoint
-    // ahead, during the previous keypoint's triplets, into the other register set
-    // (the two sets swap roles every keypoint)
-    int32_t ta[10], tb[10];
-    if (threadIdx.x < 144) load_table_segment(toff, s_rec[0].w & 0xffff, by, bseg, ta);
-
-    // One step: build the window of keypoint k from `tw` (prefetching k+1's entries
-    // into `tn`), then, after the barrier, pack keypoint k-1 and evaluate keypoint k's
-    // triplets.  Returns true after the last step.
-    auto step = [&](int k, int32_t (&tw)[10], int32_t (&tn)[10]) -> bool {
-        const int buf = k & 1;
+    if (warp < kBuildWarps) {
+        // ================= builders (named barrier 1) =================
+        const int tb = threadIdx.x;
+        auto issue_tile = [&](int slot, int key) {  // thread 0; the slot is free
+            const int img = key >> 22;
+            const int tx = (key & 2047) * kCell - kMargin + tg.mx;
+            const int ty = ((key >> 11) & 2047) * kCell - kMargin + tg.my;
+            mbar_arrive_expect_tx(&S.tile_bar[slot], static_cast<uint32_t>(tg.tw * tg.th));
+            tma_load_2d(s_tile0 + slot * tile_bytes, &prm.map[img], tx, ty, &S.tile_bar[slot]);
+        };
+        int g = 0, issued = 1;  // runs started / tiles requested (run r uses slot r % 2)
+        if (tb == 0) issue_tile(0, tile_key(S.rec[0][0]));
         bool ok = true;
-        if (k < m) {
-            const int4 r = s_rec[k % kRing];
-            const int key = tile_key(r);
-            if (key != cur_key) {  // block-uniform: a new tile was requested for this keypoint
-                if (threadIdx.x < 144) ok = mbar_wait(s_bar, tile_par, s_abort);
-                tile_par ^= 1;
-                cur_key = key;
-                ox = (key & 2047) * kCell - kMargin + tg.mx;
-                oy = ((key >> 11) & 2047) * kCell - kMargin + tg.my;
+        for (int bt = bfirst; bt <= blast && ok; ++bt) {
+            const int i = bt - bfirst, buf = i & 1;
+            const int4* rec = S.rec[buf];
+            const int nk = nrec - kBatch * bt < kBatch ? nrec - kBatch * bt : kBatch;
+            uint32_t* win = s_win0 + buf * (kBatch * kLaneWords);
+            // the next batch's first record (for its first tile) and all its records
+            int4 next_first = make_int4(0, 0, 0, 0);
+            if (bt < blast) {
+                if (tb == 0) next_first = recs[kBatch * (bt + 1)];
+                if (warp == kBuildWarps - 1 && kBatch * (bt + 1) + lane < nrec)
+                    cp_async_16(&S.rec[buf ^ 1][lane], recs + kBatch * (bt + 1) + lane);
             }
-            if (threadIdx.x < 144 && ok) {
-                // ---- sample the window of keypoint k into 4 byte-shifted copies; this
-                // thread: row by, pixels 16*bseg .. 16*bseg+18 ----
-                const int base = (r.y - oy) * tg.tw + (r.x - ox);
-                uint32_t p[5] = {0, 0, 0, 0, 0};
+            if (warp == 0) {  // runs of keypoints in one cell
+                const int key = lane < nk ? tile_key(rec[lane]) : -1;
+                const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+                const uint32_t starts = __ballot_sync(0xffffffffu, lane < nk && (lane == 0 || key != prev));
+                if (lane == 0) S.runs[buf] = starts;
+            }
+            // window buffer `buf` is free once the evaluators are done with batch i - 2
+            if (i >= 2) ok = mbar_wait(&S.empty[buf], ((i >> 1) - 1) & 1, abort);
+            if (ok && tb < nk) S.row[buf][tb] = rec[tb].z;
+            ok = bar_and<1, kBuildThreads>(ok);
+            if (!ok) break;
+            const uint32_t starts = S.runs[buf];
+            // The offset-table words of keypoint j (entries 4 wd .. 4 wd + 3: the pixels of
+            // window word wd, for this thread's words wd = tb + kBuildThreads q) are loaded
+            // three keypoints ahead into a ring of four register sets whose roles rotate
+            // with j (no set is copied while its loads are in flight).
+            constexpr int kQ = (kWinWords + kBuildThreads - 1) / kBuildThreads;
+            auto load_tab = [&](int j, uint2 (&e)[kQ]) {
+                if (j < nk) {
+                    const uint2* tab = reinterpret_cast<const uint2*>(toff + static_cast<size_t>(rec[j].w & 0xffff) * kWinPix);
 #pragma unroll
-                for (int u = 0; u < 19; ++u) {
-                    if (16 * bseg + u < kWin) {
-                        const int16_t o = static_cast<int16_t>((tw[u >> 1] >> (16 * (u & 1))) & 0xffff);
-                        p[u >> 2] |= static_cast<uint32_t>(s_tile[base + o]) << (8 * (u & 3));
+                    for (int q = 0; q < kQ; ++q)
+                        if (tb + q * kBuildThreads < kWinWords) e[q] = __ldg(tab + tb + q * kBuildThreads);
+                }
+            };
+            uint2 A[kQ], B[kQ], C[kQ], D[kQ];
+            load_tab(0, A);
+            load_tab(1, B);
+            load_tab(2, C);
+            int j1 = 0, ox = 0, oy = 0;
+            const uint8_t* tile = s_tile0;
+            bool tok = true;  // this thread's wait for the current run's tile succeeded
+            // keypoint j from `use` (its entries), loading j + 3's into `nxt`; false once
+            // a barrier reported a failure
+            auto step = [&](int j, const uint2 (&use)[kQ], uint2 (&nxt)[kQ]) -> bool {
+                if (j >= nk) return true;
+                if ((starts >> j) & 1u) {  // a run starts: its tile was requested one run ahead
+                    const uint32_t rest = starts & ~((2u << j) - 1u);
+                    j1 = rest ? __ffs(rest) - 1 : nk;
+                    const int slot = g & 1;
+                    const int key = tile_key(rec[j]);
+                    // request the following run's tile into the other slot (its last
+                    // reader, run g - 1, finished at the barrier that ended it)
+                    if (tb == 0) {
+                        const int nkey = rest ? tile_key(rec[j1]) : bt < blast ? tile_key(next_first) : -1;
+                        if (nkey >= 0) {
+                            issue_tile(slot ^ 1, nkey);
+                            ++issued;
+                        }
+                    }
+                    tok = mbar_wait(&S.tile_bar[slot], (g >> 1) & 1, abort);
+                    tile = s_tile0 + slot * tile_bytes;
+                    ox = (key & 2047) * kCell - kMargin + tg.mx;
+                    oy = ((key >> 11) & 2047) * kCell - kMargin + tg.my;
+                }
+                load_tab(j + 3, nxt);
+                if (tok) {
+                    const int4 r = rec[j];
+                    const uint8_t* t = tile + (r.y - oy) * tg.tw + (r.x - ox);
+                    uint32_t* w = win + j * kLaneWords;
+#pragma unroll
+                    for (int q = 0; q < kQ; ++q) {
+                        if (tb + q * kBuildThreads < kWinWords) {
+                            const uint32_t b0 = t[static_cast<int16_t>(use[q].x & 0xffffu)];
+                            const uint32_t b1 = t[static_cast<int16_t>(use[q].x >> 16)];
+                            const uint32_t b2 = t[static_cast<int16_t>(use[q].y & 0xffffu)];
+                            const uint32_t b3 = t[static_cast<int16_t>(use[q].y >> 16)];
+                            w[tb + q * kBuildThreads] = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
+                        }
                     }
                 }
-                uint4* w = reinterpret_cast<uint4*>(s_win + buf * kWinWords + by * kRowWords + 4 * bseg);
-                w[0] = make_uint4(p[0], p[1], p[2], p[3]);
-                w[kCopyWords / 4] = make_uint4(__funnelshift_r(p[0], p[1], 8), __funnelshift_r(p[1], p[2], 8),
-                                               __funnelshift_r(p[2], p[3], 8), __funnelshift_r(p[3], p[4], 8));
-                w[2 * kCopyWords / 4] =
-                    make_uint4(__funnelshift_r(p[0], p[1], 16), __funnelshift_r(p[1], p[2], 16),
-                               __funnelshift_r(p[2], p[3], 16), __funnelshift_r(p[3], p[4], 16));
-                w[3 * kCopyWords / 4] =
-                    make_uint4(__funnelshift_r(p[0], p[1], 24), __funnelshift_r(p[1], p[2], 24),
-                               __funnelshift_r(p[2], p[3], 24), __funnelshift_r(p[3], p[4], 24));
-                if (k + 1 < m) load_table_segment(toff, s_rec[(k + 1) % kRing].w & 0xffff, by, bseg, tn);
-            }
+                if (j + 1 == j1) {  // the run ends: its tile slot is free after the barrier
+                    if (j1 == nk && warp == kBuildWarps - 1) cp_async_wait_all();
+                    if (!bar_and<1, kBuildThreads>(tok)) return false;
+                    ++g;
+                }
+                return true;
+            };
+            for (int j = 0; j < nk && ok; j += 4)
+                ok = step(j, A, D) && step(j + 1, B, A) && step(j + 2, C, B) && step(j + 3, D, C);
+            // batch i's windows are complete (the barrier above ordered all builders' stores)
+            if (ok) mbar_arrive(&S.full[buf]);
         }
-        if (!__syncthreads_and(ok)) {
-            if (threadIdx.x == 0) {
+        if (!ok) {  // let the copies in flight land before the block's memory is released
+            if (tb == 0) {
                 atomicOr(flags, kFlagTimeout);
-                const uint64_t t0 = globaltimer();  // let the copy land before the block exits
-                while (!mbar_try_wait(s_bar, tile_par ^ 1) && globaltimer() - t0 < 200000000ull) {
+                const uint64_t t0 = globaltimer();
+                for (int r = g; r < issued; ++r)
+                    while (!mbar_try_wait(&S.tile_bar[r & 1], (r >> 1) & 1) && globaltimer() - t0 < 200000000ull) {
+                    }
+            }
+            if (warp == kBuildWarps - 1) cp_async_wait_all();
+        }
+        return;
+    }
+
+    // ================= evaluators =================
+    const int cw = warp - kBuildWarps;
+    for (int bt = bfirst; bt <= blast; ++bt) {
+        const int i = bt - bfirst, buf = i & 1;
+        const int nk = nrec - kBatch * bt < kBatch ? nrec - kBatch * bt : kBatch;
+        const int64_t bu = static_cast<int64_t>(bt) * kChunks;  // the batch's first chunk
+        const int ca = static_cast<int>((u0 > bu ? u0 : bu) - bu);
+        const int cb = static_cast<int>((u1 < bu + kChunks ? u1 : bu + kChunks) - bu);
+        if (!mbar_wait(&S.full[buf], (i >> 1) & 1, abort)) {
+            if (lane == 0) atomicOr(flags, kFlagTimeout);
+            return;
+        }
+        // ---- Eq. 1: this warp's chunks [wa, wb), lane = keypoint ----
+        const int n = cb - ca;
+        const int wa = ca + cw * n / kComputeWarps, wb = ca + (cw + 1) * n / kComputeWarps;
+        const uint32_t* wl = s_win0 + buf * (kBatch * kLaneWords) + lane * kLaneWords;
+        uint32_t v = 0;  // byte c - wa: chunk c
+#pragma unroll 1
+        for (int c = wa; c < wb; ++c) v |= eval_chunk(S.trip, wl, c) << (8 * (c - wa));
+        // output rows: this lane's keypoint, and the keypoints whose expanded sector
+        // this lane writes (lane / 2 and 16 + lane / 2)
+        const int32_t row = S.row[buf][lane];
+        const int32_t row_a = S.row[buf][lane >> 1], row_b = S.row[buf][16 + (lane >> 1)];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&S.empty[buf]);  // the windows and rows are free again
+        if (wb == wa) continue;
+        // ---- descriptor bytes [wa, wb), expanded bytes [8 wa, 8 wb), popcount ----
+        if (wb - wa == 4 && (wa & 3) == 0) {
+            if (lane < nk) reinterpret_cast<uint32_t*>(out + static_cast<size_t>(row) * kDescBytes)[wa >> 2] = v;
+            if (exp_out) {
+                // the 32 expanded bytes of a keypoint are one sector: lanes 2m, 2m + 1
+                // write keypoint m's (and 16 + m's) halves
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const int m = 16 * k + (lane >> 1);
+                    const uint32_t vm = __shfl_sync(0xffffffffu, v, m);
+                    if (m < nk)
+                        reinterpret_cast<uint4*>(exp_out + static_cast<size_t>(k ? row_b : row_a) * kBits +
+                                                 8 * wa)[lane & 1] = expand16((vm >> (16 * (lane & 1))) & 0xffffu);
                 }
             }
-            if (warp == kLastWarp) cp_async_wait_all();
-            return true;
-        }
-        // the tile is free once keypoint k's window is built: request the next cell's
-        if (threadIdx.x == 0 && k + 1 < m && tile_key(s_rec[(k + 1) % kRing]) != cur_key)
-            issue_tile(s_rec[(k + 1) % kRing]);
-        if (warp == kLastWarp) {
-            if (k > 0) {
-                // ---- pack and store the descriptor of keypoint k-1 (all its bits were
-                // written before the barrier above; this warp builds no window): word w
-                // collects bits 32w..32w+31 ----
-                const uint8_t* b = s_bits + ((k - 1) & 1) * kBits;
-                uint32_t mine = 0;  // lane w < 16 keeps word w
-#pragma unroll
-                for (int w = 0; w < kDescWords; ++w) {
-                    const uint32_t word = __ballot_sync(0xffffffffu, b[32 * w + lane] != 0);
-                    if (lane == w) mine = word;
-                }
-                const int src = (4 * lane) & 31;
-                const uint32_t x = __shfl_sync(0xffffffffu, mine, src);
-                const uint32_t y = __shfl_sync(0xffffffffu, mine, src + 1);
-                const uint32_t z = __shfl_sync(0xffffffffu, mine, src + 2);
-                const uint32_t v = __shfl_sync(0xffffffffu, mine, src + 3);
-                const size_t row = static_cast<size_t>(s_rec[(k - 1) % kRing].z);
-                if (lane < 4) out[row * 4 + lane] = make_uint4(x, y, z, v);
+        } else if (lane < nk) {
+            uint8_t* d = out + static_cast<size_t>(row) * kDescBytes;
+            for (int c = wa; c < wb; ++c) {
+                const uint32_t byte = (v >> (8 * (c - wa))) & 0xffu;
+                d[c] = static_cast<uint8_t>(byte);
                 if (exp_out) {
-                    // bytes 16*lane .. 16*lane+15 are 0 or 1: times 0x38 gives E4M3 0 / 1.0
-                    const uint4 e = reinterpret_cast<const uint4*>(b)[lane];
-                    exp_out[row * 32 + lane] = make_uint4(e.x * 0x38u, e.y * 0x38u, e.z * 0x38u, e.w * 0x38u);
-                    const int pc = __reduce_add_sync(0xffffffffu, static_cast<uint32_t>(__popc(mine)));
-                    if (lane == 0) pop_out[row] = pc;
+                    const uint4 ex = expand16(byte);
+                    reinterpret_cast<uint2*>(exp_out + static_cast<size_t>(row) * kBits)[c] = make_uint2(ex.x, ex.y);
                 }
             }
-            // ---- record ring: at steps k = 32i the records k+32 .. k+63 are requested
-            // (their slots held k-32 .. k-1, all consumed, the last by the pack above);
-            // at step k+16 this warp waits for them, so the barrier of step k+17
-            // publishes them before step k+31 first reads one
-            if ((k & 31) == 0) {
-                const int t = k + kRing - 32 + lane;
-                if (t < m) cp_async_16(&s_rec[t % kRing], brec + t);
-            } else if ((k & 31) == 16) {
-                cp_async_wait_all();
-            }
         }
-        if (k == m) {
-            if (warp == kLastWarp) cp_async_wait_all();
-            return true;
-        }
-        // ---- Eq. 1 for this lane's two triplets ----
-        const uint32_t* wb = s_win + buf * kWinWords;
-        uint8_t* bits = s_bits + buf * kBits;
-#pragma unroll
-        for (int gi = 0; gi < 2; ++gi) {
-            const uint2 to = gi == 0 ? to0 : to1;
-            const uint32_t* pa = wb + (to.x & 0xffffu);
-            const uint32_t* p1 = wb + (to.x >> 16);
-            const uint32_t* p2 = wb + (to.y & 0xffffu);
-            uint32_t sa1 = 0, sa2 = 0, s11 = 0, s22 = 0;
-#pragma unroll
-            for (int i = 0; i < 2 * kPatchR + 1; ++i) {
-                const uint32_t a0 = pa[i * kRowWords], a1 = pa[i * kRowWords + 1];
-                const uint32_t c0 = p1[i * kRowWords], c1 = p1[i * kRowWords + 1] & 0x00ffffffu;
-                const uint32_t e0 = p2[i * kRowWords], e1 = p2[i * kRowWords + 1] & 0x00ffffffu;
-                sa1 = __dp4a(a0, c0, sa1);
-                sa1 = __dp4a(a1, c1, sa1);
-                sa2 = __dp4a(a0, e0, sa2);
-                sa2 = __dp4a(a1, e1, sa2);
-                s11 = __dp4a(c0, c0, s11);
-                s11 = __dp4a(c1, c1, s11);
-                s22 = __dp4a(e0, e0, s22);
-                s22 = __dp4a(e1, e1, s22);
-            }
-            // D1 - D2 = sum C1^2 - sum C2^2 - 2 (sum A.C1 - sum A.C2)
-            const int diff = (static_cast<int>(s11) - static_cast<int>(s22)) -
-                             2 * (static_cast<int>(sa1) - static_cast<int>(sa2));
-            bits[to.y >> 16] = diff > 0 ? 1 : 0;
-        }
-        return false;
-    };
-    for (int k = 0;; k += 2) {
-        if (step(k, ta, tb)) break;
-        if (step(k + 1, tb, ta)) break;
+        if (exp_out && lane < nk) atomicAdd(pop_out + row, __popc(v));
     }
 }
 
 }  // namespace
 
-// Host-side precomputation for the cell kernel ------------------------------------
+// Host-side precomputation for the extraction kernel ------------------------------
 
 static TileGeom tile_geom(int reach) {
     TileGeom t;
     const int rx = (reach + 15) / 16 * 16;  // x margin rounded to the 16-byte TMA granule
     t.tw = kCell + 2 * rx;
+    // an odd number of 16-byte granules per row: rows then start in 8 different bank
+    // groups (an even number gives 2 or 4), so the gathers along a rotated window
+    // row collide less
+    if ((t.tw / 16) % 2 == 0) t.tw += 16;
     t.th = kCell + 2 * reach;
     t.mx = -rx;
     t.my = -reach;
@@ -480,76 +576,19 @@ static TileGeom tile_geom(int reach) {
 
 int extract_tile_pitch(int reach) { return tile_geom(reach).tw; }
 
-// Word offset of the top-left 8-byte run of the patch centred at (cx, cy) in the
-// 4-copy window layout.
-static uint32_t patch_word(int cx, int cy) {
-    const int x0 = cx - kPatchR, y0 = cy - kPatchR;
-    return static_cast<uint32_t>((x0 & 3) * kCopyWords + y0 * kRowWords + (x0 >> 2));
-}
-
-// Order in which the lanes evaluate the triplets.  32 lanes of a warp read the
-// same row of their patches with one shared-memory instruction; lanes whose words
-// fall in the same bank serialise.  A short deterministic annealing over swaps
-// between the 16 groups of 32 minimises the sum over groups and patch roles of the
-// squared bank occupancies.  Bits go back to their triplet positions through
-// shared memory, so the descriptor does not depend on the order.
-static void plan_triplet_order(const latch_triplet* trip, int* order) {
-    int bank[kBits][3];
+// Per triplet: the window word holding the first pixel of each patch's top row and
+// the pixel's byte in it (LaneTriplets layout).
+void build_triplet_offsets(const latch_triplet* trip, uint32_t* out /* 2 per triplet */) {
     for (int t = 0; t < kBits; ++t) {
         const uint8_t* c = &trip[t].ax;
-        for (int p = 0; p < 3; ++p) bank[t][p] = static_cast<int>(patch_word(c[2 * p], c[2 * p + 1]) & 31);
-    }
-    constexpr int kGroups = kBits / 32;
-    int cnt[kGroups][3][32] = {};
-    for (int i = 0; i < kBits; ++i) {
-        order[i] = i;
-        for (int p = 0; p < 3; ++p) ++cnt[i / 32][p][bank[i][p]];
-    }
-    uint64_t st = 0x9E3779B97F4A7C15ull;
-    auto next = [&st]() {
-        st ^= st << 13;
-        st ^= st >> 7;
-        st ^= st << 17;
-        return st;
-    };
-    const int iters = 400000;
-    for (int it = 0; it < iters; ++it) {
-        const int s1 = static_cast<int>(next() % kBits), s2 = static_cast<int>(next() % kBits);
-        const int g1 = s1 / 32, g2 = s2 / 32;
-        if (g1 == g2) continue;
-        const int t1 = order[s1], t2 = order[s2];
-        // change of sum(count^2) when t1 moves g1 -> g2 and t2 moves g2 -> g1
-        int delta = 0;
+        uint32_t word[3], shift[3];
         for (int p = 0; p < 3; ++p) {
-            const int b1 = bank[t1][p], b2 = bank[t2][p];
-            if (b1 == b2) continue;
-            delta += 2 * (cnt[g1][p][b2] - cnt[g1][p][b1] + 1);  // g1 loses b1, gains b2
-            delta += 2 * (cnt[g2][p][b1] - cnt[g2][p][b2] + 1);  // g2 loses b2, gains b1
+            const int x0 = c[2 * p] - kPatchR, y0 = c[2 * p + 1] - kPatchR;
+            word[p] = static_cast<uint32_t>(y0 * kRowWords + (x0 >> 2));
+            shift[p] = static_cast<uint32_t>(x0 & 3);
         }
-        const double temp = 3.0 * (1.0 - static_cast<double>(it) / iters) + 1e-3;
-        const double u = static_cast<double>(next() >> 11) * 0x1.0p-53;
-        if (delta <= 0 || u < std::exp(-delta / temp)) {
-            for (int p = 0; p < 3; ++p) {
-                --cnt[g1][p][bank[t1][p]];
-                ++cnt[g1][p][bank[t2][p]];
-                --cnt[g2][p][bank[t2][p]];
-                ++cnt[g2][p][bank[t1][p]];
-            }
-            order[s1] = t2;
-            order[s2] = t1;
-        }
-    }
-}
-
-// Per lane slot: the three patches' word offsets and the triplet's bit position.
-void build_triplet_offsets(const latch_triplet* trip, uint32_t* out /* 2 per triplet */) {
-    int order[kBits];
-    plan_triplet_order(trip, order);
-    for (int slot = 0; slot < kBits; ++slot) {
-        const int t = order[slot];
-        const uint8_t* c = &trip[t].ax;
-        out[2 * slot] = patch_word(c[0], c[1]) | (patch_word(c[2], c[3]) << 16);
-        out[2 * slot + 1] = patch_word(c[4], c[5]) | (static_cast<uint32_t>(t) << 16);
+        out[2 * t] = word[0] | (word[1] << 16);
+        out[2 * t + 1] = word[2] | (shift[0] << 16) | (shift[1] << 18) | (shift[2] << 20);
     }
 }
 
@@ -562,8 +601,10 @@ static CellGrid cell_grid(const latch_image* img) {
     return g;
 }
 
+// Two buffers of 32 windows, then two tiles (128 bytes of alignment slack).  At the
+// largest reach 221 KB (+5 KB static): one block per SM.
 static size_t extract_smem_bytes(const TileGeom& tg) {
-    return 128 + static_cast<size_t>(2 * kWinWords) * 4 + 2 * kBits + 16 + 128 + static_cast<size_t>(tg.tw) * tg.th;
+    return 128 + 2 * static_cast<size_t>(kBatch) * kLaneWords * 4 + 2 * ((static_cast<size_t>(tg.tw) * tg.th + 127) / 128 * 128);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -632,10 +673,10 @@ static cudaError_t launch_chunk(const latch_context* ctx, const latch_image* img
     const TileGeom tg = tile_geom(ctx->reach);
     cudaError_t e;
     if (!attr) {
-        e = cudaFuncSetAttribute(extract_cells_kernel<NI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(extract_lanes_kernel<NI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(extract_smem_bytes(tile_geom(kMaxReach + 1))));
-        if (e == cudaSuccess)  // four 57 KB blocks per SM
-            e = cudaFuncSetAttribute(extract_cells_kernel<NI>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(extract_lanes_kernel<NI>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -685,15 +726,18 @@ static cudaError_t launch_chunk(const latch_context* ctx, const latch_image* img
         e = launch_chained(sort_scatter_kernel<NI>, dim3(blocks), dim3(kSortThreads), 0, stream, *prm, d_kps,
                            static_cast<const int*>(cells), static_cast<const int*>(rank),
                            static_cast<const int*>(img_tot), counters, recs);
-    if (e == cudaSuccess) {
-        // the records are split evenly over the blocks, at least item_kps keypoints each
+    LaneTriplets* tt = e == cudaSuccess ? new LaneTriplets : nullptr;
+    if (tt) {
+        static_assert(sizeof(LaneTriplets) == sizeof(ctx->h_trip_offsets), "triplet table layout");
+        memcpy(tt, ctx->h_trip_offsets, sizeof(LaneTriplets));
+        // the chunks are split evenly over the blocks, at least item_kps keypoints' worth each
         const int64_t want = (l.nkp + ctx->item_kps - 1) / ctx->item_kps;
-        const int64_t grid = want < 4 * ctx->sm_count ? want : 4 * ctx->sm_count;
-        e = launch_chained(extract_cells_kernel<NI>, dim3(static_cast<unsigned>(grid)), dim3(kThreads),
-                           extract_smem_bytes(tg), stream, *prm, static_cast<const int4*>(recs),
-                           static_cast<const int*>(counters), ctx->d_tile_offsets,
-                           reinterpret_cast<const uint2*>(ctx->d_trip_offsets), reinterpret_cast<uint4*>(d_out),
-                           reinterpret_cast<uint4*>(exp_out), pop_out, ctx->d_flags);
+        const int64_t grid = want < ctx->sm_count ? want : ctx->sm_count;
+        e = launch_chained(extract_lanes_kernel<NI>, dim3(static_cast<unsigned>(grid)), dim3(kThreads),
+                           extract_smem_bytes(tg), stream, *prm, *tt, static_cast<const int4*>(recs),
+                           static_cast<const int*>(counters), ctx->d_tile_offsets, d_out, exp_out, pop_out,
+                           ctx->d_flags);
+        delete tt;
     }
     delete prm;
     return e;

@@ -31,7 +31,8 @@ void build_offset_tables(const double* scales, int nscales, int8_t* out /* nscal
 int max_reach(const double* scales, int nscales);
 // Staged-tile row pitch of the extraction kernel for a given reach.
 int extract_tile_pitch(int reach);
-// Window word offsets of every triplet's three patches (extract.cu layout).
+// Window words and byte shifts of every triplet's three patches (the extraction
+// kernel's triplet parameter).
 void build_triplet_offsets(const latch_triplet* trip, uint32_t* out /* 2 per triplet */);
 
 struct Scratch {
@@ -56,10 +57,8 @@ struct latch_context {
     double scales[LATCH_MAX_SCALES] = {};
     int reach = 0;                       // max |offset| over the scale table
     int16_t* d_tile_offsets = nullptr;   // nscales * 32 * 2304 (+16 pad) tile offsets dy * pitch + dx
-    uint32_t* d_trip_offsets = nullptr;  // 512 x 2 words: window word offsets of each triplet's patches
     latch_triplet h_trip[LATCH_TRIPLETS] = {};
     bool has_trip = false;
-    uint8_t* d_trip = nullptr;           // 512 * 6 bytes
     uint32_t h_trip_offsets[2 * LATCH_TRIPLETS] = {};
     uint32_t* d_flags = nullptr;         // device error word
     int32_t item_kps = 16;               // extraction: fewest keypoints per block (latch_autotune)

@@ -90,6 +90,22 @@ __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
+// AND of `v` over the `kCount` threads meeting at named barrier `kId` (a barrier
+// with memory ordering among them, like __syncthreads_and for a part of a block).
+template <int kId, int kCount>
+__device__ __forceinline__ bool bar_and(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.and.pred p, %2, %3, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"(static_cast<uint32_t>(v)), "n"(kId), "n"(kCount)
+        : "memory");
+    return r != 0;
+}
+
 // 16-byte asynchronous global -> shared copy (L2 only); completion by cp_async_wait_all
 // in the issuing thread.
 __device__ __forceinline__ void cp_async_16(void* dst_smem, const void* src) {

@@ -67,8 +67,9 @@ def report(extract_ms: float, n_desc: int, match_ms: float, pairs: int, path: st
     ext = {"bound": "alu", "achieved": EXTRACT_OPS_PER_DESC * n_desc / (extract_ms / 1e3) / 1e12,
            "peak": SMS * INT_LANES_PER_SM * clk / 1e12, "unit": "Tops/s (int32)",
            "kernel": "extract", "units_per_launch": n_desc, "traffic": traffic("extract", "extract.cu"),
-           "note": "bound in practice by the shared-memory data pipe (about 85% busy under ncu): two-way bank "
-                   "conflicts on the random patch loads, not int32 issue"}
+           "note": "bound in practice by the shared-memory data pipe and instruction issue together (each about "
+                   "69% busy under ncu: conflict-free patch loads, 1,334 wavefronts per descriptor), not int32 "
+                   "throughput"}
     if path == "tensor":
         mat = {"bound": "tensor", "achieved": TENSOR_FLOP_PER_PAIR * pairs / (match_ms / 1e3) / 1e12,
                "peak": 2.0 * float(peaks["bf16_tflops"]), "unit": "TFLOP/s (fp8 e4m3)", "kernel": "match_tensor",

@@ -196,3 +196,38 @@ def test_autotune_changes_speed_not_results(gpu_ctx, triplets):
     finally:
         P.latch_set_tuning(gpu_ctx.handle, saved["item_kps"], saved["tensor_min_pairs"])
     gpu_ctx.check()
+
+
+def test_batch_and_run_boundaries(gpu_ctx, triplets):
+    """Layouts aimed at the extraction's batches of 32 keypoints (one per lane) and its
+    per-cell tile runs: 150 keypoints in one 32x32 cell (runs spanning several
+    batches), one keypoint in each of 300 cells (a tile per keypoint), and counts
+    around multiples of 32; each at several work-item sizes, so that batches are split
+    between blocks at many chunk offsets."""
+    w, h = 1024, 768
+    img = synth.image(synth.seed(11, 40, synth.KIND_IMAGE), w, h, n_ellipses=40)
+    rng = np.random.default_rng(17)
+
+    def attrs(n):
+        return rng.integers(0, 32, n), rng.integers(0, 3, n)
+
+    cases = []
+    b, s = attrs(150)
+    cases.append(np.stack([320 + rng.integers(0, 32, 150), 256 + rng.integers(0, 32, 150), b, s], 1))
+    gx, gy = np.meshgrid(np.arange(20), np.arange(15))
+    b, s = attrs(300)
+    cases.append(np.stack([gx.ravel() * 32 + rng.integers(0, 32, 300), gy.ravel() * 32 + rng.integers(0, 32, 300), b, s], 1))
+    for n in (1, 31, 32, 33, 64, 65, 97):
+        b, s = attrs(n)
+        cases.append(np.stack([rng.integers(-20, w + 20, n), rng.integers(-20, h + 20, n), b, s], 1))
+    cases = [c.astype(np.int32) for c in cases]
+    wants = [oracle.extract(img, w, h, k, triplets, synth.SCALES) for k in cases]
+    saved = P.latch_get_tuning(gpu_ctx.handle)
+    try:
+        for item in (1, 7, 32):
+            P.latch_set_tuning(gpu_ctx.handle, item, saved["tensor_min_pairs"])
+            for k, want in zip(cases, wants):
+                assert np.array_equal(_extract(gpu_ctx, img, w, h, k), want), (item, len(k))
+    finally:
+        P.latch_set_tuning(gpu_ctx.handle, saved["item_kps"], saved["tensor_min_pairs"])
+    gpu_ctx.check()

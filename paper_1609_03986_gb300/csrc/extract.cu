@@ -21,10 +21,11 @@
 //        the image arrive as 0, the border reading; two tile slots, the next
 //        run's tile requested while the current one is read), and every window
 //        pixel is read from it through the per-(scale, bin) offset table
-//        (nearest pixel; offsets pre-multiplied into tile offsets; the table
-//        words are loaded three keypoints ahead).  Window j sits at word 577 j:
-//        with an odd stride, the 32 lanes reading the same word of their
-//        windows hit 32 different banks;
+//        (nearest pixel; offsets pre-multiplied into tile offsets), in units of
+//        half a window spread over the builder warps, each warp loading the
+//        table words of its next unit while it gathers the current one.  Window
+//        j sits at word 577 j: with an odd stride, the 32 lanes reading the same
+//        word of their windows hit 32 different banks;
 //      - 16 evaluator warps evaluate Eq. 1 on batch i - 1, warp w on chunks 4w ..
 //        4w+3, all 32 lanes on the same triplet at a time (the triplet table is
 //        staged in shared memory: one broadcast load per triplet): a 7-pixel
@@ -415,75 +416,83 @@ __global__ void __launch_bounds__(kThreads, 1) extract_lanes_kernel(
             if (ok && tb < nk) S.row[buf][tb] = rec[tb].z;
             ok = bar_and<1, kBuildThreads>(ok);
             if (!ok) break;
-            const uint32_t starts = S.runs[buf];
-            // The offset-table words of keypoint j (entries 4 wd .. 4 wd + 3: the pixels of
-            // window word wd, for this thread's words wd = tb + kBuildThreads q) are loaded
-            // three keypoints ahead into a ring of four register sets whose roles rotate
-            // with j (no set is copied while its loads are in flight).
-            constexpr int kQ = (kWinWords + kBuildThreads - 1) / kBuildThreads;
-            auto load_tab = [&](int j, uint2 (&e)[kQ]) {
-                if (j < nk) {
-                    const uint2* tab = reinterpret_cast<const uint2*>(toff + static_cast<size_t>(rec[j].w & 0xffff) * kWinPix);
-#pragma unroll
-                    for (int q = 0; q < kQ; ++q)
-                        if (tb + q * kBuildThreads < kWinWords) e[q] = __ldg(tab + tb + q * kBuildThreads);
+            // Each run of keypoints in one cell is built as units of half a window
+            // (288 words, 9 per lane) spread over the builder warps: unit u of a run is
+            // keypoint j0 + u / 2, half u % 2, and warp w takes units w, w + 12, ..., so
+            // the keypoints of a run are gathered in parallel.  A warp loads the
+            // offset-table words of its next unit (in this run or a later one of the
+            // batch) into B while it gathers the current unit from A.
+            constexpr int kHalves = 2;
+            constexpr int kUnitWords = kWinWords / kHalves;     // 288
+            constexpr int kLaneUnitWords = kUnitWords / 32;     // 9
+            // this warp's unit after unit u of run [j0, j1) (later runs: `rest`), as
+            // keypoint << 1 | half, or -1
+            auto next_unit = [&](int j0, int j1, int u, uint32_t rest) -> int {
+                if (u + kBuildWarps < (j1 - j0) * kHalves) {
+                    const int v = u + kBuildWarps;
+                    return ((j0 + v / kHalves) << 1) | (v % kHalves);
                 }
+                while (rest) {
+                    const int a0 = __ffs(rest) - 1;
+                    rest &= rest - 1;
+                    const int a1 = rest ? __ffs(rest) - 1 : nk;
+                    if (warp < (a1 - a0) * kHalves) return ((a0 + warp / kHalves) << 1) | (warp % kHalves);
+                }
+                return -1;
             };
-            uint2 A[kQ], B[kQ], C[kQ], D[kQ];
-            load_tab(0, A);
-            load_tab(1, B);
-            load_tab(2, C);
-            int j1 = 0, ox = 0, oy = 0;
-            const uint8_t* tile = s_tile0;
-            bool tok = true;  // this thread's wait for the current run's tile succeeded
-            // keypoint j from `use` (its entries), loading j + 3's into `nxt`; false once
-            // a barrier reported a failure
-            auto step = [&](int j, const uint2 (&use)[kQ], uint2 (&nxt)[kQ]) -> bool {
-                if (j >= nk) return true;
-                if ((starts >> j) & 1u) {  // a run starts: its tile was requested one run ahead
-                    const uint32_t rest = starts & ~((2u << j) - 1u);
-                    j1 = rest ? __ffs(rest) - 1 : nk;
-                    const int slot = g & 1;
-                    const int key = tile_key(rec[j]);
-                    // request the following run's tile into the other slot (its last
-                    // reader, run g - 1, finished at the barrier that ended it)
-                    if (tb == 0) {
-                        const int nkey = rest ? tile_key(rec[j1]) : bt < blast ? tile_key(next_first) : -1;
-                        if (nkey >= 0) {
-                            issue_tile(slot ^ 1, nkey);
-                            ++issued;
-                        }
+            auto load_unit = [&](int code, uint2 (&e)[kLaneUnitWords]) {
+                if (code < 0) return;
+                const uint2* tab = reinterpret_cast<const uint2*>(toff + static_cast<size_t>(rec[code >> 1].w & 0xffff) * kWinPix) +
+                                   (code & 1) * kUnitWords + lane;
+#pragma unroll
+                for (int q = 0; q < kLaneUnitWords; ++q) e[q] = __ldg(tab + 32 * q);
+            };
+            uint32_t rem = S.runs[buf];
+            uint2 A[kLaneUnitWords], B[kLaneUnitWords];
+            load_unit(next_unit(0, 0, -kBuildWarps, rem), A);
+            while (rem) {
+                const int j0 = __ffs(rem) - 1;
+                rem &= rem - 1;
+                const int j1 = rem ? __ffs(rem) - 1 : nk;
+                const int slot = g & 1;
+                const int key = tile_key(rec[j0]);
+                // request the following run's tile into the other slot (its last
+                // reader, run g - 1, finished at the barrier that ended it)
+                if (tb == 0) {
+                    const int nkey = rem ? tile_key(rec[__ffs(rem) - 1]) : bt < blast ? tile_key(next_first) : -1;
+                    if (nkey >= 0) {
+                        issue_tile(slot ^ 1, nkey);
+                        ++issued;
                     }
-                    tok = mbar_wait(&S.tile_bar[slot], (g >> 1) & 1, abort);
-                    tile = s_tile0 + slot * tile_bytes;
-                    ox = (key & 2047) * kCell - kMargin + tg.mx;
-                    oy = ((key >> 11) & 2047) * kCell - kMargin + tg.my;
                 }
-                load_tab(j + 3, nxt);
+                const bool tok = mbar_wait(&S.tile_bar[slot], (g >> 1) & 1, abort);
                 if (tok) {
-                    const int4 r = rec[j];
-                    const uint8_t* t = tile + (r.y - oy) * tg.tw + (r.x - ox);
-                    uint32_t* w = win + j * kLaneWords;
+                    const uint8_t* tile = s_tile0 + slot * tile_bytes;
+                    const int ox = (key & 2047) * kCell - kMargin + tg.mx;
+                    const int oy = ((key >> 11) & 2047) * kCell - kMargin + tg.my;
+                    for (int u = warp; u < (j1 - j0) * kHalves; u += kBuildWarps) {
+                        load_unit(next_unit(j0, j1, u, rem), B);  // lands during this unit's gathers
+                        const int j = j0 + u / kHalves, half = u % kHalves;
+                        const int4 r = rec[j];
+                        const uint8_t* t = tile + (r.y - oy) * tg.tw + (r.x - ox);
+                        uint32_t* w = win + j * kLaneWords + half * kUnitWords + lane;
 #pragma unroll
-                    for (int q = 0; q < kQ; ++q) {
-                        if (tb + q * kBuildThreads < kWinWords) {
-                            const uint32_t b0 = t[static_cast<int16_t>(use[q].x & 0xffffu)];
-                            const uint32_t b1 = t[static_cast<int16_t>(use[q].x >> 16)];
-                            const uint32_t b2 = t[static_cast<int16_t>(use[q].y & 0xffffu)];
-                            const uint32_t b3 = t[static_cast<int16_t>(use[q].y >> 16)];
-                            w[tb + q * kBuildThreads] = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
+                        for (int q = 0; q < kLaneUnitWords; ++q) {
+                            const uint32_t b0 = t[static_cast<int16_t>(A[q].x & 0xffffu)];
+                            const uint32_t b1 = t[static_cast<int16_t>(A[q].x >> 16)];
+                            const uint32_t b2 = t[static_cast<int16_t>(A[q].y & 0xffffu)];
+                            const uint32_t b3 = t[static_cast<int16_t>(A[q].y >> 16)];
+                            w[32 * q] = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
                         }
+#pragma unroll
+                        for (int q = 0; q < kLaneUnitWords; ++q) A[q] = B[q];
                     }
                 }
-                if (j + 1 == j1) {  // the run ends: its tile slot is free after the barrier
-                    if (j1 == nk && warp == kBuildWarps - 1) cp_async_wait_all();
-                    if (!bar_and<1, kBuildThreads>(tok)) return false;
-                    ++g;
-                }
-                return true;
-            };
-            for (int j = 0; j < nk && ok; j += 4)
-                ok = step(j, A, D) && step(j + 1, B, A) && step(j + 2, C, B) && step(j + 3, D, C);
+                if (j1 == nk && warp == kBuildWarps - 1) cp_async_wait_all();
+                ok = bar_and<1, kBuildThreads>(tok);  // the run's tile slot is free after it
+                if (!ok) break;
+                ++g;
+            }
             // batch i's windows are complete (the barrier above ordered all builders' stores)
             if (ok) mbar_arrive(&S.full[buf]);
         }

@@ -68,7 +68,7 @@ def report(extract_ms: float, n_desc: int, match_ms: float, pairs: int, path: st
            "peak": SMS * INT_LANES_PER_SM * clk / 1e12, "unit": "Tops/s (int32)",
            "kernel": "extract", "units_per_launch": n_desc, "traffic": traffic("extract", "extract.cu"),
            "note": "bound in practice by the shared-memory data pipe and instruction issue together (each about "
-                   "69% busy under ncu: conflict-free patch loads, 1,334 wavefronts per descriptor), not int32 "
+                   "68-70% busy under ncu: conflict-free patch loads, 1,322 wavefronts per descriptor), not int32 "
                    "throughput"}
     if path == "tensor":
         mat = {"bound": "tensor", "achieved": TENSOR_FLOP_PER_PAIR * pairs / (match_ms / 1e3) / 1e12,

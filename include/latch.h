@@ -257,12 +257,20 @@ typedef struct {
 
 typedef struct {
     int64_t submitted, completed, rejected, failed, batches, max_queue, queued, lane_bytes;
+    int64_t hbm_free;    /* free device bytes measured (cudaMemGetInfo) when the session was created */
+    int64_t hbm_budget;  /* device bytes the session holds: min(hbm_budget, hbm_free - 512 MiB) */
 } latch_session_stats;
 
 /* hbm_budget: device bytes the session may hold (arena of max_gallery_rows +
  * 2 x max_batch_kps expanded rows, the rest split between the two lanes; each lane
- * needs at least 64 MB).  max_batch: requests per micro-batch (1..64);
- * max_batch_kps: keypoints per micro-batch; h_triplets: the 512-triplet table. */
+ * needs at least 64 MB).  The budget is clamped to the free device memory measured
+ * at creation less 512 MiB, and the session reserves all of it then, so admission
+ * (latch_submit, and the scheduler filling a lane) is against memory that is really
+ * free.  max_batch: requests per micro-batch (1..64); max_batch_kps: keypoints per
+ * micro-batch; h_triplets: the 512-triplet table.
+ * A batch's kernels report device-side failures through a per-lane error word that
+ * completes its tickets: latch_wait then returns LATCH_ETIMEOUT (a bounded device
+ * wait gave up; results incomplete) or LATCH_EDEVICE. */
 latch_status latch_session_create(int device, size_t hbm_budget, int64_t max_gallery_rows, int32_t max_batch,
                                   int64_t max_batch_kps, const latch_triplet *h_triplets, latch_session **out);
 /* Stops the scheduler, waits for work in flight, frees everything. */
@@ -270,7 +278,9 @@ latch_status latch_session_destroy(latch_session *s);
 /* Copy n packed descriptors (host) into a new resident gallery (synchronous). */
 latch_status latch_gallery_add(latch_session *s, const uint8_t *h_desc, int32_t n, int32_t *gallery_id);
 /* Queue a request; LATCH_ENOMEM if it can never fit a lane, LATCH_EINVAL on bad
- * arguments or an unknown gallery.  Returns at once. */
+ * arguments, an unknown gallery or a keypoint whose scale_idx is outside the scale
+ * table (checked on the host, so that the micro-batch the request would share stays
+ * valid).  Returns at once. */
 latch_status latch_submit(latch_session *s, const latch_request *req, uint64_t *ticket);
 /* Wait for a ticket (timeout_ms < 0: forever); LATCH_ETIMEOUT if still running.
  * On completion the request's host outputs are filled. */
@@ -318,10 +328,20 @@ int32_t hamming_match_path(const latch_context *ctx, int64_t nq, int64_t nt);
  *   device); make that first call before any stream capture.
  *   All calls share the one array: calls whose work overlaps on the GPU (different
  *   streams, or several host threads) race and must be serialised by the caller.
- *   Errors are described by latch_last_error(NULL).
+ *   Errors are described by latch_last_error(NULL); failures that only the device
+ *   sees are reported by hamming_match_noalloc_status().
  */
 latch_status hamming_match_noalloc(const uint8_t *d_query, int32_t nq, const uint8_t *d_train, int32_t nt, int32_t k,
                                    float ratio, latch_match *d_out, latch_stream_t stream);
+
+/* Device-side status of hamming_match_noalloc on the current device (the paper has
+ * no counterpart).  The kernels of every hamming_match_noalloc call OR their error
+ * flags into one status word at the head of the fixed array, which stays set until
+ * this call reads it.  Waits for all work on the current device, reads the word and
+ * clears it: LATCH_OK when no call since the last read reported a problem,
+ * LATCH_ETIMEOUT when a bounded device-side wait gave up (those calls' records are
+ * incomplete).  Allocates nothing. */
+latch_status hamming_match_noalloc_status(void);
 
 /* Wait for all work on the context's device, then report (and clear) a
  * device-side input error (LATCH_EDEVICE) or an asynchronous CUDA error. */

@@ -82,7 +82,7 @@ class latch_result(ctypes.Structure):
 
 class latch_session_stats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in ("submitted", "completed", "rejected", "failed", "batches", "max_queue",
-                                             "queued", "lane_bytes")]
+                                             "queued", "lane_bytes", "hbm_free", "hbm_budget")]
 
 
 _lib = None
@@ -121,6 +121,7 @@ EXPORTS = [
     ("latch_session_get_stats", ctypes.c_int, [_P, ctypes.POINTER(latch_session_stats)]),
     ("latch_session_last_error", ctypes.c_char_p, [_P]),
     ("hamming_match_noalloc", ctypes.c_int, [_P, _I32, _P, _I32, _I32, _F, _P, _P]),
+    ("hamming_match_noalloc_status", ctypes.c_int, []),
 ]
 
 
@@ -216,6 +217,12 @@ def hamming_match_noalloc(query, nq: int, train, nt: int, k: int, ratio: float, 
     callers that may not call cudaMalloc); scratch is the library's fixed 16 MiB
     array, so nq + nt is limited to roughly 30,000 descriptors."""
     _check(None, library().hamming_match_noalloc(_ptr(query), nq, _ptr(train), nt, k, ratio, _ptr(out), stream))
+
+
+def hamming_match_noalloc_status() -> None:
+    """Raise LatchError if a device-side wait of an earlier hamming_match_noalloc call
+    on the current device gave up (reads and clears the status word; synchronises)."""
+    _check(None, library().hamming_match_noalloc_status())
 
 
 def latch_check(ctx) -> None:

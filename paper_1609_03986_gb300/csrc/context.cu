@@ -32,6 +32,17 @@ static std::atomic<uint64_t> g_launches{0};
 
 void note_launches(int count) { g_launches.fetch_add(static_cast<uint64_t>(count), std::memory_order_relaxed); }
 
+cudaError_t once_per_device(unsigned long long* done, cudaError_t (*set)()) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+    if (bit && (__atomic_load_n(done, __ATOMIC_ACQUIRE) & bit)) return cudaSuccess;
+    e = set();  // idempotent: two threads racing here both set the same attributes
+    if (e == cudaSuccess && bit) __atomic_fetch_or(done, bit, __ATOMIC_RELEASE);
+    return e;
+}
+
 latch_status fail(latch_context* ctx, latch_status st, const char* fmt, ...) {
     char* dst = ctx ? ctx->err : g_create_err;
     va_list ap;

@@ -675,20 +675,23 @@ size_t extract_batch_scratch_bytes(const latch_image* imgs, const int64_t* n, in
 size_t extract_scratch_bytes(const latch_image* img, int64_t n) { return extract_batch_scratch_bytes(img, &n, 1); }
 
 template <int NI>
+static cudaError_t set_extract_attributes() {
+    cudaError_t e = cudaFuncSetAttribute(extract_lanes_kernel<NI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(extract_smem_bytes(tile_geom(kMaxReach + 1))));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(extract_lanes_kernel<NI>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    return e;
+}
+
+template <int NI>
 static cudaError_t launch_chunk(const latch_context* ctx, const latch_image* imgs, const int64_t* kp0,
                                 const int64_t* n, int i0, int i1, const latch_keypoint* d_kps, uint8_t* d_out,
-                                uint8_t* exp_out, int32_t* pop_out, uint8_t* scratch, cudaStream_t stream) {
-    static bool attr = false;
+                                uint8_t* exp_out, int32_t* pop_out, uint8_t* scratch, cudaStream_t stream,
+                                uint32_t* flags) {
+    static unsigned long long attr_done = 0;
     const TileGeom tg = tile_geom(ctx->reach);
-    cudaError_t e;
-    if (!attr) {
-        e = cudaFuncSetAttribute(extract_lanes_kernel<NI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(extract_smem_bytes(tile_geom(kMaxReach + 1))));
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(extract_lanes_kernel<NI>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    cudaError_t e = once_per_device(&attr_done, set_extract_attributes<NI>);
+    if (e != cudaSuccess) return e;
     EncodeTiledFn enc = extract_encode_fn();
     if (!enc) return cudaErrorNotSupported;
     const ChunkLayout l = chunk_layout(imgs, n, i0, i1);
@@ -730,7 +733,7 @@ static cudaError_t launch_chunk(const latch_context* ctx, const latch_image* img
     if (e == cudaSuccess)
         e = launch_chained(sort_count_kernel<NI>, dim3(blocks), dim3(kSortThreads), 0, stream, *prm, d_kps, cells,
                            rank, img_tot, img_done, reinterpret_cast<uint4*>(d_out),
-                           reinterpret_cast<uint4*>(exp_out), pop_out, ctx->d_flags);
+                           reinterpret_cast<uint4*>(exp_out), pop_out, flags);
     if (e == cudaSuccess)
         e = launch_chained(sort_scatter_kernel<NI>, dim3(blocks), dim3(kSortThreads), 0, stream, *prm, d_kps,
                            static_cast<const int*>(cells), static_cast<const int*>(rank),
@@ -744,8 +747,7 @@ static cudaError_t launch_chunk(const latch_context* ctx, const latch_image* img
         const int64_t grid = want < ctx->sm_count ? want : ctx->sm_count;
         e = launch_chained(extract_lanes_kernel<NI>, dim3(static_cast<unsigned>(grid)), dim3(kThreads),
                            extract_smem_bytes(tg), stream, *prm, *tt, static_cast<const int4*>(recs),
-                           static_cast<const int*>(counters), ctx->d_tile_offsets, d_out, exp_out, pop_out,
-                           ctx->d_flags);
+                           static_cast<const int*>(counters), ctx->d_tile_offsets, d_out, exp_out, pop_out, flags);
         delete tt;
     }
     delete prm;
@@ -754,8 +756,10 @@ static cudaError_t launch_chunk(const latch_context* ctx, const latch_image* img
 
 cudaError_t launch_extract_batch(const latch_context* ctx, const latch_image* imgs, const int64_t* kp0,
                                  const int64_t* n, int count, const latch_keypoint* d_kps, uint8_t* d_out,
-                                 void* scratch, cudaStream_t stream, uint8_t* exp_out, int32_t* pop_out) {
+                                 void* scratch, cudaStream_t stream, uint8_t* exp_out, int32_t* pop_out,
+                                 uint32_t* flags) {
     uint8_t* base = static_cast<uint8_t*>(scratch);
+    if (!flags) flags = ctx->d_flags;
     for (int i0 = 0; i0 < count; i0 += kBatchImages) {
         const int i1 = i0 + kBatchImages < count ? i0 + kBatchImages : count;
         int64_t nk = 0;
@@ -765,11 +769,11 @@ cudaError_t launch_extract_batch(const latch_context* ctx, const latch_image* im
             // instance that fits keeps the launch's parameter block small
             const int ni = i1 - i0;
             const cudaError_t e =
-                ni == 1    ? launch_chunk<1>(ctx, imgs, kp0, n, i0, i1, d_kps, d_out, exp_out, pop_out, base, stream)
-                : ni <= 4  ? launch_chunk<4>(ctx, imgs, kp0, n, i0, i1, d_kps, d_out, exp_out, pop_out, base, stream)
-                : ni <= 16 ? launch_chunk<16>(ctx, imgs, kp0, n, i0, i1, d_kps, d_out, exp_out, pop_out, base, stream)
+                ni == 1    ? launch_chunk<1>(ctx, imgs, kp0, n, i0, i1, d_kps, d_out, exp_out, pop_out, base, stream, flags)
+                : ni <= 4  ? launch_chunk<4>(ctx, imgs, kp0, n, i0, i1, d_kps, d_out, exp_out, pop_out, base, stream, flags)
+                : ni <= 16 ? launch_chunk<16>(ctx, imgs, kp0, n, i0, i1, d_kps, d_out, exp_out, pop_out, base, stream, flags)
                            : launch_chunk<kBatchImages>(ctx, imgs, kp0, n, i0, i1, d_kps, d_out, exp_out, pop_out,
-                                                        base, stream);
+                                                        base, stream, flags);
             if (e != cudaSuccess) return e;
         }
         base += chunk_layout(imgs, n, i0, i1).total;

@@ -87,6 +87,11 @@ latch_status scratch_reserve(latch_context* ctx, int slot, size_t bytes, void** 
 // Counts kernel launches made by the library (latch_kernel_launches()).
 void note_launches(int count);
 
+// Runs `set` (a cudaFuncSetAttribute sequence for one kernel) once per device: the
+// attributes belong to the current device's context.  `done` is the kernel's mask of
+// devices already set up (devices 0..63; larger indices run `set` on every call).
+cudaError_t once_per_device(unsigned long long* done, cudaError_t (*set)());
+
 // Launches `kernel` so that it may start while the previous kernel on the stream
 // is still running (programmatic dependent launch).  Every kernel launched this way
 // executes griddepcontrol.wait before it reads or writes global memory that earlier
@@ -116,9 +121,11 @@ size_t extract_scratch_bytes(const latch_image* img, int64_t n);
 // Images [0, count) with keypoints d_kps[kp0[i] .. kp0[i] + n[i]) -> d_out rows at the same positions.
 // When exp_out is not NULL, row r of the tensor matcher's input (512 bytes, E4M3 0 / 1.0 per bit)
 // and pop_out[r] (the descriptor's popcount) are written as well.
+// `flags`: the device error word the kernels raise flags in (NULL: the context's).
 cudaError_t launch_extract_batch(const latch_context* ctx, const latch_image* imgs, const int64_t* kp0,
                                  const int64_t* n, int count, const latch_keypoint* d_kps, uint8_t* d_out,
-                                 void* scratch, cudaStream_t stream, uint8_t* exp_out, int32_t* pop_out);
+                                 void* scratch, cudaStream_t stream, uint8_t* exp_out, int32_t* pop_out,
+                                 uint32_t* flags = nullptr);
 size_t extract_batch_scratch_bytes(const latch_image* imgs, const int64_t* n, int count);
 
 cudaError_t launch_match_popc(const latch_context* ctx, const uint8_t* q, int32_t nq, const uint8_t* t, int32_t nt,

@@ -705,15 +705,18 @@ static void shrink(const MatchBatch& b, MatchBatchT<NP>* o) {
 }
 
 template <int NP>
+static cudaError_t set_match_attributes() {
+    return cudaFuncSetAttribute(match_tc_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+}
+
+template <int NP>
 static cudaError_t launch_match_np(const MatchBatch& full, const CUtensorMap& map, const int32_t* pop,
                                    uint64_t* partials, int32_t* tile_cnt, latch_match* out, uint32_t* flags,
                                    cudaStream_t stream) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e =
-            cudaFuncSetAttribute(match_tc_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    static unsigned long long attr_done = 0;
+    {
+        const cudaError_t e = once_per_device(&attr_done, set_match_attributes<NP>);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     MatchBatchT<NP>* b = new (std::nothrow) MatchBatchT<NP>;
     if (!b) return cudaErrorMemoryAllocation;
@@ -822,7 +825,7 @@ cudaError_t launch_match_tc(const latch_context* ctx, const uint8_t* q, int32_t 
 namespace latch {
 
 constexpr size_t kStaticScratchBytes = size_t(16) << 20;  // 16 MiB
-constexpr size_t kStaticFlagBytes = 256;                  // status word, cleared every call
+constexpr size_t kStaticFlagBytes = 256;  // status word: zero at load, raised by the kernels, cleared when read
 
 }  // namespace latch
 
@@ -884,10 +887,8 @@ extern "C" latch_status hamming_match_noalloc(const uint8_t* d_query, int32_t nq
     latch_status st = static_scratch(dev, &base);
     if (st != LATCH_OK) return st;
     uint8_t* bytes = static_cast<uint8_t*>(base);
-    uint32_t* flags = reinterpret_cast<uint32_t*>(bytes);
+    uint32_t* flags = reinterpret_cast<uint32_t*>(bytes);  // sticky until hamming_match_noalloc_status reads it
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
-    e = cudaMemsetAsync(flags, 0, sizeof(uint32_t), cs);
-    if (e != cudaSuccess) return fail(nullptr, LATCH_ECUDA, "clear status word: %s", cudaGetErrorString(e));
     // launch_match_tc reads only the SM count and the status-word pointer of its context
     latch_context shim;
     shim.device = dev;
@@ -896,5 +897,25 @@ extern "C" latch_status hamming_match_noalloc(const uint8_t* d_query, int32_t nq
     const int32_t r_milli = static_cast<int32_t>(std::round(static_cast<double>(ratio) * 1000.0));
     e = launch_match_tc(&shim, d_query, nq, d_train, nt, k, r_milli, d_out, bytes + kStaticFlagBytes, cs);
     if (e != cudaSuccess) return fail(nullptr, LATCH_ECUDA, "tensor match launch: %s", cudaGetErrorString(e));
+    return LATCH_OK;
+}
+
+extern "C" latch_status hamming_match_noalloc_status(void) {
+    using namespace latch;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(nullptr, LATCH_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    void* base = nullptr;
+    latch_status st = static_scratch(dev, &base);
+    if (st != LATCH_OK) return st;
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return fail(nullptr, LATCH_ECUDA, "earlier work failed: %s", cudaGetErrorString(e));
+    uint32_t word = 0;
+    e = cudaMemcpy(&word, base, sizeof(word), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && word) e = cudaMemset(base, 0, sizeof(word));
+    if (e != cudaSuccess) return fail(nullptr, LATCH_ECUDA, "status word: %s", cudaGetErrorString(e));
+    if (word & kFlagTimeout)
+        return fail(nullptr, LATCH_ETIMEOUT, "a device-side wait of hamming_match_noalloc gave up (word 0x%x)", word);
+    if (word) return fail(nullptr, LATCH_EDEVICE, "hamming_match_noalloc status word 0x%x", word);
     return LATCH_OK;
 }

@@ -36,6 +36,7 @@ namespace {
 
 constexpr int kLanes = 2;
 constexpr int64_t kRowBytes = 512 + 4;  // expanded row + popcount
+constexpr size_t kFreeMargin = size_t(512) << 20;  // device memory left free at session creation
 
 struct Ticket {
     latch_request req;
@@ -61,6 +62,8 @@ struct Lane {
     cudaStream_t stream = nullptr;
     DoneArg done{nullptr, 0};  // argument of the lane's completion callback
     uint8_t* region = nullptr;  // lane_bytes of device memory
+    uint32_t* d_flags = nullptr;  // the lane's device error word, cleared at the start of each batch
+    uint32_t* h_flags = nullptr;  // pinned host copy, written at the end of each batch
     int64_t qrow0 = 0;          // first arena row of this lane's query rows
     bool busy = false;
     std::vector<Ticket*> batch;
@@ -79,6 +82,7 @@ struct latch_session {
     int32_t max_batch = 0;
     int64_t max_batch_kps = 0;
     size_t lane_bytes = 0;
+    size_t budget = 0;  // device bytes the session holds: min(caller's budget, free memory - margin)
     // arena: [gallery rows | lane 0 query rows | lane 1 query rows] x 512 B, then popcounts
     uint8_t* arena = nullptr;
     int32_t* arena_pop = nullptr;
@@ -181,14 +185,15 @@ latch_status run_batch(latch_session* s, int li, DoneArg* done) {
     uint64_t* partials = reinterpret_cast<uint64_t*>(cv.take(match_tc_partial_bytes(*mb) + 16));
     int32_t* tile_cnt = reinterpret_cast<int32_t*>(cv.take(match_tc_counter_bytes(mb->tiles)));
     if (!ext_scratch || !partials || !tile_cnt) e = cudaErrorMemoryAllocation;  // admission bug guard
+    if (e == cudaSuccess) e = cudaMemsetAsync(L.d_flags, 0, sizeof(uint32_t), st);
     if (e == cudaSuccess && total > 0) e = cudaMemsetAsync(tile_cnt, 0, match_tc_counter_bytes(mb->tiles), st);
     // the extraction writes the queries' expanded rows into the lane's arena rows
     if (e == cudaSuccess && total > 0)
         e = launch_extract_batch(s->ctx, imgs.data(), kp0.data(), n.data(), nb, d_kps, d_desc, ext_scratch, st,
-                                 s->arena + L.qrow0 * 512, s->arena_pop + L.qrow0);
+                                 s->arena + L.qrow0 * 512, s->arena_pop + L.qrow0, L.d_flags);
     if (e == cudaSuccess && total > 0)
-        e = launch_match_tc_rows(*mb, s->arena, s->arena_rows, s->arena_pop, partials, tile_cnt, d_match,
-                                 s->ctx->d_flags, st);
+        e = launch_match_tc_rows(*mb, s->arena, s->arena_rows, s->arena_pop, partials, tile_cnt, d_match, L.d_flags,
+                                 st);
     for (int i = 0; i < nb && e == cudaSuccess; ++i) {
         const latch_request& r = L.batch[i]->req;
         if (r.n == 0) continue;
@@ -197,6 +202,8 @@ latch_status run_batch(latch_session* s, int li, DoneArg* done) {
             e = cudaMemcpyAsync(r.h_desc, d_desc + kp0[i] * 64, static_cast<size_t>(r.n) * 64, cudaMemcpyDeviceToHost,
                                 st);
     }
+    // the batch's device error word reaches the completion callback through pinned memory
+    if (e == cudaSuccess) e = cudaMemcpyAsync(L.h_flags, L.d_flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaLaunchHostFunc(st, on_batch_done, done);
     if (e == cudaErrorMemoryAllocation) return LATCH_ENOMEM;
     return e == cudaSuccess ? LATCH_OK : LATCH_ECUDA;
@@ -219,12 +226,21 @@ void finish_lane(latch_session* s, int li, latch_status status) {
     L.busy = false;
 }
 
+// Status of a finished batch from its device error word: a device-side wait that
+// gave up (the batch's results are incomplete) or bad input seen by a kernel.
+latch_status batch_status(uint32_t flags) {
+    if (flags & kFlagTimeout) return LATCH_ETIMEOUT;
+    return flags ? LATCH_EDEVICE : LATCH_OK;
+}
+
 void CUDART_CB on_batch_done(void* arg) {
     DoneArg* d = static_cast<DoneArg*>(arg);
     latch_session* s = d->s;
     {
         std::lock_guard<std::mutex> lock(s->mu);
-        finish_lane(s, d->lane, LATCH_OK);
+        const uint32_t flags = *s->lanes[d->lane].h_flags;  // copied before this callback on the lane's stream
+        if (flags) snprintf(s->err, sizeof(s->err), "lane %d: device error word 0x%x", d->lane, flags);
+        finish_lane(s, d->lane, batch_status(flags));
     }
     s->cv_done.notify_all();
     s->cv_sched.notify_all();
@@ -302,10 +318,21 @@ latch_status latch_session_create(int device, size_t hbm_budget, int64_t max_gal
     s->gallery_cap = max_gallery_rows;
     s->arena_rows = max_gallery_rows + kLanes * max_batch_kps;
     const size_t arena_bytes = static_cast<size_t>(s->arena_rows) * kRowBytes + 4096;
-    if (st == LATCH_OK && (hbm_budget <= arena_bytes || (hbm_budget - arena_bytes) / kLanes < (size_t(64) << 20)))
-        st = LATCH_ENOMEM;  // budget too small for the arena plus two lanes of 64 MB
+    // admission by free device memory: the session never holds more than the device
+    // has free when it is created, less a margin for the context's own tables and
+    // scratch; every request is then admitted against this reservation
+    size_t free_b = 0, total_b = 0;
+    if (st == LATCH_OK && cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) st = LATCH_ECUDA;
     if (st == LATCH_OK) {
-        s->lane_bytes = (hbm_budget - arena_bytes) / kLanes / 256 * 256;
+        const size_t usable = free_b > kFreeMargin ? free_b - kFreeMargin : 0;
+        s->budget = hbm_budget < usable ? hbm_budget : usable;
+        s->stats.hbm_free = static_cast<int64_t>(free_b);
+        s->stats.hbm_budget = static_cast<int64_t>(s->budget);
+    }
+    if (st == LATCH_OK && (s->budget <= arena_bytes || (s->budget - arena_bytes) / kLanes < (size_t(64) << 20)))
+        st = LATCH_ENOMEM;  // budget (or free memory) too small for the arena plus two lanes of 64 MB
+    if (st == LATCH_OK) {
+        s->lane_bytes = (s->budget - arena_bytes) / kLanes / 256 * 256;
         if (cudaMalloc(&s->arena, arena_bytes) != cudaSuccess) st = LATCH_ENOMEM;
     }
     if (st == LATCH_OK) {
@@ -316,8 +343,12 @@ latch_status latch_session_create(int device, size_t hbm_budget, int64_t max_gal
             L.done = DoneArg{s, i};
             L.mb = new (std::nothrow) MatchBatch;
             if (!L.mb || cudaMalloc(&L.region, s->lane_bytes) != cudaSuccess ||
+                cudaMalloc(&L.d_flags, 256) != cudaSuccess ||
+                cudaHostAlloc(&L.h_flags, sizeof(uint32_t), cudaHostAllocDefault) != cudaSuccess ||
                 cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking) != cudaSuccess)
                 st = LATCH_ENOMEM;
+            else
+                *L.h_flags = 0;
         }
     }
     if (st != LATCH_OK) {
@@ -344,6 +375,8 @@ latch_status latch_session_destroy(latch_session* s) {
             cudaStreamDestroy(L.stream);
         }
         if (L.region) cudaFree(L.region);
+        if (L.d_flags) cudaFree(L.d_flags);
+        if (L.h_flags) cudaFreeHost(L.h_flags);
         delete L.mb;
     }
     if (s->arena) cudaFree(s->arena);
@@ -384,6 +417,14 @@ latch_status latch_submit(latch_session* s, const latch_request* r, uint64_t* ti
     if (r->n < 0 || (r->n > 0 && (!r->h_kps || !r->h_matches))) return sfail(s, LATCH_EINVAL, "bad keypoints or output");
     if (r->k != 1 && r->k != 2) return sfail(s, LATCH_EINVAL, "k must be 1 or 2");
     if (!(r->ratio >= 0.0f && r->ratio <= 1.0f)) return sfail(s, LATCH_EINVAL, "ratio not in [0, 1]");
+    // a keypoint with a scale index outside the scale table is refused here, so that it
+    // cannot spoil the micro-batch it would share with other requests
+    for (int32_t i = 0; i < r->n; ++i)
+        if (r->h_kps[i].scale_idx >= s->ctx->nscales) {
+            std::lock_guard<std::mutex> lock(s->mu);
+            ++s->stats.rejected;
+            return sfail(s, LATCH_EINVAL, "keypoint scale index outside the scale table");
+        }
     Ticket* tk = new (std::nothrow) Ticket;
     if (!tk) return sfail(s, LATCH_ENOMEM, "host allocation failed");
     tk->req = *r;

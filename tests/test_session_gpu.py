@@ -148,3 +148,31 @@ def test_admission(served):
     with pytest.raises(P.LatchError):
         sess.submit(img, 64, 64, big[:10], 0, k=3)
     assert sess.stats()["rejected"] >= 2
+
+
+def test_bad_scale_is_refused_and_the_mix_stays_exact(served, gpu_ctx):
+    """A request holding one keypoint with a scale index outside the scale table is
+    refused at submit (LATCH_EINVAL), while requests submitted around it still
+    complete with the bytes of the plain calls."""
+    sess, gals = served
+    reqs = _requests(6, seed=45)
+    want = [_single_call(gpu_ctx, r, gals) for r in reqs]
+    tickets = []
+    for i, r in enumerate(reqs):
+        tickets.append(sess.submit(r["img"], r["w"], r["h"], r["kps"], r["gallery"], r["k"], r["ratio"],
+                                   want_desc=True))
+        if i == 2:
+            bad = reqs[3]["raw_kps"].copy() if len(reqs[3]["raw_kps"]) else np.array([[10, 10, 0, 0]], np.int32)
+            bad[len(bad) // 2, 3] = 3  # the session's scale table has 3 entries
+            with pytest.raises(P.LatchError) as e:
+                sess.submit(reqs[3]["img"], reqs[3]["w"], reqs[3]["h"], P.pack_keypoints(bad), 0)
+            assert e.value.status == 1
+            assert "scale" in P.latch_session_last_error(sess.handle)
+    for t, (wd, wm) in zip(tickets, want):
+        res, m, d = sess.wait(t)
+        assert res.status == 0
+        assert np.array_equal(d, wd)
+        _same(m, wm)
+    st = sess.stats()
+    assert st["failed"] == 0
+    assert 0 < st["hbm_budget"] <= st["hbm_free"]

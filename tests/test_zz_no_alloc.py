@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import paper_1609_03986_gb300 as P
 from paper_1609_03986_gb300 import synth
 
@@ -32,17 +33,24 @@ def test_noalloc_equals_allocating_path_twice():
     try:
         stream = int(torch.cuda.current_stream().cuda_stream)
         for call, (nq, nt) in enumerate(((3001, 5003), (700, 9999))):
-            q = torch.from_numpy(synth.random_descriptors(synth.seed(21, call, synth.KIND_GALLERY), nq)).cuda()
-            t = torch.from_numpy(synth.random_descriptors(synth.seed(22, call, synth.KIND_GALLERY), nt)).cuda()
-            t[::7] = q[0]  # ties: equal distances must resolve to the same lowest index
+            qh = synth.random_descriptors(synth.seed(21, call, synth.KIND_GALLERY), nq)
+            th = synth.random_descriptors(synth.seed(22, call, synth.KIND_GALLERY), nt)
+            th[::7] = qh[0]  # ties: equal distances must resolve to the same lowest index
+            q, t = torch.from_numpy(qh).cuda(), torch.from_numpy(th).cuda()
             want = torch.empty((nq, 16), dtype=torch.uint8, device="cuda")
             got = torch.full((nq, 16), 0xAB, dtype=torch.uint8, device="cuda")
             P.hamming_match(ctx, q, nq, t, nt, 2, 0.8, want, P.PATH_TENSOR, stream)
             P.hamming_match_noalloc(q, nq, t, nt, 2, 0.8, got, stream)
             torch.cuda.synchronize()
+            P.hamming_match_noalloc_status()  # no device-side wait gave up
             a, b = _records(want), _records(got)
             for f in ("idx1", "idx2", "dist1", "dist2", "accepted"):
                 assert np.array_equal(a[f], b[f]), (call, f)
+            # and a few rows straight against the oracle (row 0 is the planted tie)
+            rows = np.array([0, 1, nq // 2, nq - 1])
+            o = oracle.match(qh[rows], th, 2, 0.8)
+            for f in ("idx1", "idx2", "dist1", "dist2", "accepted"):
+                assert np.array_equal(b[f][rows].astype(np.int64), o[f].astype(np.int64)), (call, f)
         P.latch_check(ctx)
     finally:
         P.latch_context_destroy(ctx)

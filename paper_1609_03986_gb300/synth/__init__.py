@@ -193,7 +193,10 @@ def sfm_batch(n_images: int = BATCH_IMAGES, width: int = BATCH_W, height: int = 
     oriented, scaled keypoints (counts uniform in [kmin, kmax]) and the pair list of
     every image against its next `neighbours` images."""
     counts = batch_keypoint_counts(n_images, kmin, kmax, config)
-    imgs = [image(seed(config, i, KIND_IMAGE), width, height) for i in range(n_images)]
+    # the C generator releases the GIL (ctypes) and keeps no shared state: images in parallel
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max(1, os.cpu_count() or 1)) as ex:
+        imgs = list(ex.map(lambda i: image(seed(config, i, KIND_IMAGE), width, height), range(n_images)))
     kps = [keypoints(seed(config, i, KIND_KEYPOINTS), width, height, int(counts[i]), 32, True, 3)
            for i in range(n_images)]
     return {"images": imgs, "kps": kps, "pairs": batch_pairs(n_images, neighbours), "width": width,

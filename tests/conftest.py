@@ -41,3 +41,25 @@ def to_dev(a):
 def match_records(t):
     import paper_1609_03986_gb300 as P
     return P.matches_from_bytes(t.cpu().numpy())
+
+
+def same_matches(got, want, rows=None):
+    """Field-by-field equality of match records with oracle results (optionally on rows)."""
+    import numpy as np
+    for f in ("idx1", "idx2", "dist1", "dist2", "accepted"):
+        g = got[f] if rows is None else got[f][rows]
+        assert np.array_equal(g.astype(np.int64), np.asarray(want[f]).astype(np.int64)), f
+
+
+@pytest.fixture(scope="session")
+def oriented_pair_oracle(triplets):
+    """The oriented and scaled pair workload (2 x 1920x1080, 10,000 keypoints each)
+    with the oracle's descriptors of both images and its full 10k x 10k top-2 match,
+    computed once by the sharded oracle."""
+    import oracle_shards
+    from paper_1609_03986_gb300 import synth
+    wl = synth.pair("oriented_scaled_1920x1080_10k")
+    w, h = wl["width"], wl["height"]
+    descs = oracle_shards.extract_many([(im, w, h, k, triplets, synth.SCALES) for im, k in zip(wl["images"], wl["kps"])])
+    match = oracle_shards.match(descs[0], descs[1], 2, 0.8)
+    return {"wl": wl, "descs": descs, "match": match}

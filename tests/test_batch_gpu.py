@@ -7,7 +7,8 @@ import torch
 import oracle
 import paper_1609_03986_gb300 as P
 from paper_1609_03986_gb300 import synth
-from conftest import to_dev
+import oracle_shards
+from conftest import same_matches, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -52,14 +53,15 @@ def test_small_mixed_batch(gpu_ctx, triplets):
         kps.append(k)
     pairs = [(0, 1), (1, 0), (0, 0), (2, 3), (3, 2), (3, 5), (4, 4), (5, 1), (1, 3), (4, 2)]
     descs, matches = _run_batch(gpu_ctx, imgs, sizes, kps, pairs)
+    wants = [oracle.extract(imgs[i], sizes[i][0], sizes[i][1], kps[i], triplets, synth.SCALES)
+             for i in range(len(imgs))]
     for i in range(len(imgs)):
-        want = oracle.extract(imgs[i], sizes[i][0], sizes[i][1], kps[i], triplets, synth.SCALES)
-        assert np.array_equal(descs[i], want), i
+        assert np.array_equal(descs[i], wants[i]), i
     for p, (q, t) in enumerate(pairs):
         if counts[q] == 0:
             assert len(matches[p]) == 0
             continue
-        _same(matches[p], oracle.match(descs[q], descs[t], 2, 0.8))
+        _same(matches[p], oracle.match(wants[q], wants[t], 2, 0.8))
 
 
 def test_batch_equals_single_calls(gpu_ctx, triplets):
@@ -78,23 +80,29 @@ def test_batch_equals_single_calls(gpu_ctx, triplets):
         _same(matches[p], one)
 
 
-def test_sfm_batch_full_size_sampled(gpu_ctx, triplets):
+def test_sfm_batch_full_size(gpu_ctx, triplets):
     """The full batched workload (64 images of 4000x3000, 5k-50k oriented and scaled
-    keypoints each, 476 neighbour pairs) in one latch_batch_run: 64 sampled
-    descriptors per image against the oracle, and 3 sampled query rows of 40 pairs
-    matched by the oracle against the whole train image."""
+    keypoints each, 476 neighbour pairs) in one latch_batch_run: every descriptor of
+    every image equals the oracle's, and in every pair a seeded 1% of the query rows
+    (at least one) equals the oracle's matching of its own descriptors against the
+    whole train image.  The oracle runs sharded over the host cores."""
     wl = synth.sfm_batch()
-    sizes = [(wl["width"], wl["height"])] * len(wl["images"])
+    w, h = wl["width"], wl["height"]
+    sizes = [(w, h)] * len(wl["images"])
     descs, matches = _run_batch(gpu_ctx, wl["images"], sizes, wl["kps"], wl["pairs"])
-    rng = np.random.default_rng(7)
+    wants = oracle_shards.extract_many([(im, w, h, k, triplets, synth.SCALES) for im, k in zip(wl["images"], wl["kps"])],
+                                       per=1024)
     for i in range(len(wl["images"])):
-        sel = rng.choice(len(wl["kps"][i]), 64, replace=False)
-        want = oracle.extract(wl["images"][i], wl["width"], wl["height"], wl["kps"][i][sel], triplets, synth.SCALES)
-        assert np.array_equal(descs[i][sel], want), i
-    for p in rng.choice(len(wl["pairs"]), 40, replace=False):
-        q, t = wl["pairs"][p]
-        rows = rng.choice(len(wl["kps"][q]), 3, replace=False)
-        _same(matches[p][rows], oracle.match(descs[q][rows], descs[t], 2, 0.8))
+        assert np.array_equal(descs[i], wants[i]), i
+    rng = np.random.default_rng(7)
+    jobs, picks = [], []
+    for p, (q, t) in enumerate(wl["pairs"]):
+        nq = len(wl["kps"][q])
+        rows = np.sort(rng.choice(nq, max(1, -(-nq // 100)), replace=False))
+        picks.append(rows)
+        jobs.append((wants[q][rows], wants[t], 2, 0.8))
+    for p, want in enumerate(oracle_shards.match_many(jobs, per=16)):
+        same_matches(matches[p], want, picks[p])
 
 
 def test_more_pairs_than_one_launch(gpu_ctx, triplets):
@@ -127,8 +135,10 @@ def test_more_pairs_than_one_launch(gpu_ctx, triplets):
         torch.cuda.synchronize()
         _same(matches[p], P.matches_from_bytes(out.cpu().numpy()))
     assert np.all(matches[600]["idx1"] == -1) and np.all(matches[600]["dist1"] == 65535)
-    rows = rng.choice(counts[pairs[3][0]], min(5, counts[pairs[3][0]]), replace=False)
-    _same(matches[3][rows], oracle.match(descs[pairs[3][0]][rows], descs[pairs[3][1]], 2, 0.8))
+    q3, t3 = pairs[3]
+    wq, wt = (oracle.extract(imgs[i], 160, 120, kps[i], triplets, synth.SCALES) for i in (q3, t3))
+    assert np.array_equal(descs[q3], wq) and np.array_equal(descs[t3], wt)
+    _same(matches[3], oracle.match(wq, wt, 2, 0.8))
 
 
 def _pinned(a: np.ndarray) -> torch.Tensor:
@@ -180,21 +190,13 @@ def test_host_batch_pipelined_equals_device_batch(gpu_ctx, triplets):
             _same(recs[mo[p]:mo[p + 1]], matches[p])
 
 
-def test_bench_step_full_size(gpu_ctx, triplets):
-    """The bench's step exactly: latch_batch_run on the 2 x 1920x1080, 10,000-keypoint
-    oriented and scaled pair, 10k x 10k top-2 (ratio 0.8).  Every descriptor equals the
-    plain latch_extract; 400 sampled keypoints per image and 64 sampled query rows
-    (against the full train set) equal the oracle."""
-    wl = synth.pair("oriented_scaled_1920x1080_10k")
+def test_oriented_pair_batched(gpu_ctx, oriented_pair_oracle):
+    """The oriented and scaled pair as one latch_batch_run (2 x 1920x1080, 10,000
+    keypoints each, 10k x 10k top-2, ratio 0.8): all 20,000 descriptors and all
+    10,000 match records equal the oracle's."""
+    wl, descs_o, want = oriented_pair_oracle["wl"], oriented_pair_oracle["descs"], oriented_pair_oracle["match"]
     w, h = wl["width"], wl["height"]
     descs, matches = _run_batch(gpu_ctx, wl["images"], [(w, h)] * 2, wl["kps"], [(0, 1)])
-    rng = np.random.default_rng(37)
     for i in range(2):
-        plain = gpu_ctx.extract(to_dev(wl["images"][i]), w, h, to_dev(P.pack_keypoints(wl["kps"][i])))
-        torch.cuda.synchronize()
-        assert np.array_equal(descs[i], plain.cpu().numpy()), i
-        rows = rng.choice(len(wl["kps"][i]), 400, replace=False)
-        want = oracle.extract(wl["images"][i], w, h, wl["kps"][i][rows], triplets, synth.SCALES)
-        assert np.array_equal(descs[i][rows], want), i
-    rows = rng.choice(len(wl["kps"][0]), 64, replace=False)
-    _same(matches[0][rows], oracle.match(descs[0][rows], descs[1], 2, 0.8))
+        assert np.array_equal(descs[i], descs_o[i]), i
+    same_matches(matches[0], want)

@@ -8,7 +8,8 @@ import torch
 import oracle
 import paper_1609_03986_gb300 as P
 from paper_1609_03986_gb300 import synth
-from conftest import match_records, to_dev
+import oracle_shards
+from conftest import match_records, same_matches, to_dev
 
 pytestmark = pytest.mark.gpu
 PATHS = [P.PATH_POPC, P.PATH_TENSOR, P.PATH_AUTO]
@@ -73,30 +74,53 @@ def test_invalid_arguments(gpu_ctx):
 
 def test_pair_workload_parity(gpu_ctx, triplets):
     """Extract both images of the plain 640x480 workload on the GPU and match them
-    2,000 x 2,000; descriptors and matches equal the oracle's."""
+    2,000 x 2,000 on every path; descriptors equal the oracle's, and the matches equal
+    the oracle's matching of its own descriptors."""
     wl = synth.pair("plain_640x480_2k")
     descs = []
     for img, kps in zip(wl["images"], wl["kps"]):
         d = gpu_ctx.extract(to_dev(img), wl["width"], wl["height"], to_dev(P.pack_keypoints(kps)))
         descs.append(d)
     torch.cuda.synchronize()
-    q, t = (d.cpu().numpy() for d in descs)
-    assert np.array_equal(q, oracle.extract(wl["images"][0], wl["width"], wl["height"], wl["kps"][0], triplets))
-    want = oracle.match(q, t)
+    wq, wt = (oracle.extract(im, wl["width"], wl["height"], k, triplets) for im, k in zip(wl["images"], wl["kps"]))
+    assert np.array_equal(descs[0].cpu().numpy(), wq) and np.array_equal(descs[1].cpu().numpy(), wt)
+    want = oracle.match(wq, wt)
     for path in PATHS:
         _same(match_records(gpu_ctx.match(descs[0], descs[1], 2, 0.8, path)), want)
 
 
 @pytest.mark.parametrize("path", PATHS)
-def test_million_gallery_sampled(gpu_ctx, path):
+def test_oriented_pair_full_match(gpu_ctx, oriented_pair_oracle, path):
+    """The oriented and scaled pair: 10,000 x 10,000 top-2 on each path, every query
+    row equal to the oracle's matching of its own descriptors (sharded over the host
+    cores)."""
+    wl, descs, want = oriented_pair_oracle["wl"], oriented_pair_oracle["descs"], oriented_pair_oracle["match"]
+    got = [gpu_ctx.extract(to_dev(im), wl["width"], wl["height"], to_dev(P.pack_keypoints(k)))
+           for im, k in zip(wl["images"], wl["kps"])]
+    torch.cuda.synchronize()
+    for g, d in zip(got, descs):
+        assert np.array_equal(g.cpu().numpy(), d)
+    same_matches(match_records(gpu_ctx.match(got[0], got[1], 2, 0.8, path)), want)
+
+
+@pytest.fixture(scope="module")
+def gallery():
+    """The 16,384 x 1,048,576 gallery workload and the oracle's full records for 1%
+    of its query rows (a seeded sample of 168 rows), computed once for all paths."""
+    q, g, slots, hs = synth.gallery_workload()
+    rows = np.sort(np.random.default_rng(1).choice(q.shape[0], 168, replace=False))
+    return q, g, slots, hs, rows, oracle_shards.match(q[rows], g, 2, 0.8, per=1)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_million_gallery(gpu_ctx, gallery, path):
     """16,384 queries against the 1,048,576-descriptor gallery with planted
     near-duplicates: every planted match by closed form (idx1 = planted slot,
-    dist1 = h, accepted), plus 48 rows checked in full against the oracle."""
-    q, g, slots, hs = synth.gallery_workload()
+    dist1 = h, accepted), and 168 rows (1%) compared in full (idx1, idx2, dist1,
+    dist2, accepted) with the oracle."""
+    q, g, slots, hs, rows, want = gallery
     got = _match(gpu_ctx, q, g, path=path)
     assert np.array_equal(got["idx1"], slots)
     assert np.array_equal(got["dist1"].astype(np.int32), hs)
     assert got["accepted"].all()
-    rows = np.random.default_rng(1).choice(q.shape[0], 48, replace=False)
-    want = oracle.match(q[rows], g)
-    _same(got[rows], want)
+    same_matches(got, want, rows)

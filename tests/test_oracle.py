@@ -336,3 +336,24 @@ def test_planted_near_duplicates_closed_form():
     assert np.array_equal(m["dist1"], hs)
     assert m["accepted"].all()
     assert (m["dist2"] > 150).all()
+
+
+def test_sharded_oracle_equals_the_single_call(triplets):
+    """The tests' sharded runs of the oracle (slices of keypoints / query rows in host
+    threads, results concatenated in order) give exactly the single call's output."""
+    import oracle_shards
+    w, h = 200, 160
+    img = synth.image(synth.seed(60, 0, synth.KIND_IMAGE), w, h, n_ellipses=10)
+    kps = synth.keypoints(synth.seed(60, 0, synth.KIND_KEYPOINTS), w, h, 301, 8, True, 3)
+    one = oracle.extract(img, w, h, kps, triplets, synth.SCALES)
+    assert np.array_equal(oracle_shards.extract(img, w, h, kps, triplets, synth.SCALES, per=37), one)
+    both = oracle_shards.extract_many([(img, w, h, kps, triplets, synth.SCALES), (img, w, h, kps[:5], triplets,
+                                                                                  synth.SCALES)], per=16)
+    assert np.array_equal(both[0], one) and np.array_equal(both[1], one[:5])
+    q = synth.random_descriptors(61, 203)
+    t = synth.random_descriptors(62, 500)
+    t[::9] = q[3]
+    want = oracle.match(q, t, 2, 0.7)
+    for got in (oracle_shards.match(q, t, 2, 0.7, per=10), oracle_shards.match_many([(q, t, 2, 0.7)], per=7)[0]):
+        for f in want:
+            assert np.array_equal(got[f], want[f]), f

@@ -45,6 +45,12 @@ def _load():
         lib.oracle_hamming.argtypes = [P, P, I]
         lib.oracle_match.restype = I
         lib.oracle_match.argtypes = [P, I, P, I, I, F, P, P, P, P, P]
+        lib.oracle_fast_score.restype = I
+        lib.oracle_fast_score.argtypes = [P, I, I, I64, I, I, I]
+        lib.oracle_orientation_bin.restype = I
+        lib.oracle_orientation_bin.argtypes = [P, I64, I, I]
+        lib.oracle_detect.restype = I
+        lib.oracle_detect.argtypes = [P, I, I, I64, I, I, P, P, P]
         _lib = lib
     return _lib
 
@@ -118,3 +124,31 @@ def match(query: np.ndarray, train: np.ndarray, k: int = 2, ratio: float = 0.8):
     if rc != 0:
         raise ValueError("oracle_match: bad arguments")
     return {"idx1": idx1, "idx2": idx2, "dist1": d1, "dist2": d2, "accepted": acc}
+
+
+def fast_score(image: np.ndarray, width: int, height: int, x: int, y: int, t: int) -> int:
+    """FAST-9 score of pixel (x, y) at threshold t (0: not a corner)."""
+    image = _c(image, np.uint8)
+    return int(_load().oracle_fast_score(image.ctypes.data, width, height, image.shape[1], x, y, t))
+
+
+def orientation_bin(image: np.ndarray, x: int, y: int) -> int:
+    """Angle bin of the intensity centroid of the radius-15 disc around (x, y)."""
+    image = _c(image, np.uint8)
+    return int(_load().oracle_orientation_bin(image.ctypes.data, image.shape[1], x, y))
+
+
+def detect(image: np.ndarray, width: int, height: int, t: int) -> np.ndarray:
+    """Oriented FAST keypoints in raster order: (n, 3) int32 array of x, y, angle bin."""
+    image = _c(image, np.uint8)
+    lib = _load()
+    cap = 4096
+    while True:
+        xs, ys, bs = (np.zeros(cap, np.int32) for _ in range(3))
+        n = lib.oracle_detect(image.ctypes.data, width, height, image.shape[1], t, cap, xs.ctypes.data,
+                              ys.ctypes.data, bs.ctypes.data)
+        if n < 0:
+            raise ValueError("oracle_detect: bad arguments")
+        if n <= cap:
+            return np.stack([xs[:n], ys[:n], bs[:n]], axis=1)
+        cap = n

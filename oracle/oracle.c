@@ -30,8 +30,24 @@
  *   - matching: lowest distance, ties to the lowest train index; the second match
  *     is the best over the other train indices; accepted iff 1000*d1 < r*d2 with
  *     r = rha(1000*ratio); an absent second match has distance 65535.
+ *
+ * Keypoint detection (Sec. 3.2: keypoints come from the FAST detector, and the
+ * window is read at the keypoint's orientation).  The paper uses a library FAST
+ * and states no parameters; readings:
+ *   - FAST-9 segment test (Rosten and Drummond): the 16 pixels of the radius-3
+ *     Bresenham circle, in circular order; p is a corner at threshold t when 9
+ *     contiguous circle pixels are all brighter than I(p) + t or all darker than
+ *     I(p) - t;
+ *   - score: the largest t' >= t at which p is still a corner (0: not a corner);
+ *   - non-maximum suppression: a corner is kept when its score is strictly larger
+ *     than the score of each of its 8 neighbours;
+ *   - detection region: pixels at least 16 from every border;
+ *   - orientation: intensity centroid over the disc x^2 + y^2 <= 15^2 around p,
+ *     m10 = sum x I, m01 = sum y I (x right, y down, the frame of the window
+ *     rotation above), theta = atan2(m01, m10), angle bin = rha(theta * 16 / pi)
+ *     mod 32, in FP64; keypoints are reported in raster order.
  * Parity pins: every function here is pinned by tests (closed forms, invariants,
- * brute force against full sorting); none is unpinned.
+ * brute force against full sorting, hand-made images); none is unpinned.
  */
 #include <math.h>
 #include <stdint.h>
@@ -183,4 +199,97 @@ int oracle_match(const uint8_t *q, int nq, const uint8_t *t, int nt, int k, floa
     }
     free(dist);
     return 0;
+}
+
+/* ---------------------------------------------------------------------------
+ * Keypoint detection: FAST-9 corners with non-maximum suppression, oriented by
+ * the intensity centroid (Sec. 3.2).  Plain loops, one pixel at a time.
+ * ------------------------------------------------------------------------- */
+
+#define FAST_ARC 9
+#define CENTROID_R 15
+#define DETECT_BORDER 16
+
+/* The radius-3 Bresenham circle in circular order (x right, y down), from the pixel
+ * straight above the centre, clockwise. */
+static const int kCircle[16][2] = {{0, -3}, {1, -3}, {2, -2}, {3, -1}, {3, 0},  {3, 1},  {2, 2},  {1, 3},
+                                   {0, 3},  {-1, 3}, {-2, 2}, {-3, 1}, {-3, 0}, {-3, -1}, {-2, -2}, {-1, -3}};
+
+/* Segment test: 9 contiguous circle pixels (circularly) all > I(p) + t, or all
+ * < I(p) - t.  (x, y) must be at least 3 pixels from every border. */
+static int fast_is_corner(const uint8_t *img, int64_t pitch, int x, int y, int t) {
+    const int ip = img[(int64_t)y * pitch + x];
+    for (int start = 0; start < 16; ++start) {
+        int bright = 1, dark = 1;
+        for (int k = 0; k < FAST_ARC; ++k) {
+            const int *c = kCircle[(start + k) % 16];
+            const int q = img[(int64_t)(y + c[1]) * pitch + (x + c[0])];
+            if (!(q > ip + t)) bright = 0;
+            if (!(q < ip - t)) dark = 0;
+        }
+        if (bright || dark) return 1;
+    }
+    return 0;
+}
+
+/* FAST score of pixel (x, y) at threshold t: 0 when it is not a corner at t, else
+ * the largest t' >= t at which it is still a corner (found by trying t' = t, t+1,
+ * ... in turn). */
+int oracle_fast_score(const uint8_t *img, int width, int height, int64_t pitch, int x, int y, int t) {
+    if (x < 3 || y < 3 || x >= width - 3 || y >= height - 3) return 0;
+    if (!fast_is_corner(img, pitch, x, y, t)) return 0;
+    int s = t;
+    while (s < 255 && fast_is_corner(img, pitch, x, y, s + 1)) ++s;
+    return s;
+}
+
+/* Angle bin of the intensity centroid of the radius-15 disc around (x, y), which
+ * must be at least 15 pixels from every border. */
+int oracle_orientation_bin(const uint8_t *img, int64_t pitch, int x, int y) {
+    int64_t m10 = 0, m01 = 0;
+    for (int dy = -CENTROID_R; dy <= CENTROID_R; ++dy)
+        for (int dx = -CENTROID_R; dx <= CENTROID_R; ++dx)
+            if (dx * dx + dy * dy <= CENTROID_R * CENTROID_R) {
+                const int64_t v = img[(int64_t)(y + dy) * pitch + (x + dx)];
+                m10 += dx * v;
+                m01 += dy * v;
+            }
+    const double theta = atan2((double)m01, (double)m10);
+    const int b = (int)round(theta * 16.0 / M_PI);
+    return ((b % 32) + 32) % 32;
+}
+
+/*
+ * Oriented FAST keypoints of an image at threshold t (1 <= t <= 254), in raster
+ * order: every pixel of the detection region whose score is non-zero and strictly
+ * larger than each of its 8 neighbours' scores, with its orientation bin.  Writes
+ * at most `cap` keypoints to xs, ys, bins and returns the number found (which may
+ * exceed cap), or -1 on bad arguments.
+ */
+int oracle_detect(const uint8_t *img, int width, int height, int64_t pitch, int t, int cap, int32_t *xs,
+                  int32_t *ys, int32_t *bins) {
+    if (t < 1 || t > 254 || width < 1 || height < 1 || cap < 0) return -1;
+    int *score = (int *)calloc((size_t)width * (size_t)height, sizeof(int));
+    if (!score) return -1;
+    for (int y = 0; y < height; ++y)
+        for (int x = 0; x < width; ++x) score[(int64_t)y * width + x] = oracle_fast_score(img, width, height, pitch, x, y, t);
+    int n = 0;
+    for (int y = DETECT_BORDER; y <= height - 1 - DETECT_BORDER; ++y)
+        for (int x = DETECT_BORDER; x <= width - 1 - DETECT_BORDER; ++x) {
+            const int s = score[(int64_t)y * width + x];
+            if (s == 0) continue;
+            int keep = 1;
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx)
+                    if ((dx || dy) && !(s > score[(int64_t)(y + dy) * width + (x + dx)])) keep = 0;
+            if (!keep) continue;
+            if (n < cap) {
+                xs[n] = x;
+                ys[n] = y;
+                bins[n] = oracle_orientation_bin(img, pitch, x, y);
+            }
+            ++n;
+        }
+    free(score);
+    return n;
 }

@@ -45,6 +45,8 @@ def _load():
         lib.oracle_hamming.argtypes = [P, P, I]
         lib.oracle_match.restype = I
         lib.oracle_match.argtypes = [P, I, P, I, I, F, P, P, P, P, P]
+        lib.oracle_extract_weighted.restype = I
+        lib.oracle_extract_weighted.argtypes = [P, I, I, I64, P, P, P, P, I, P, P, I, P, P]
         lib.oracle_fast_score.restype = I
         lib.oracle_fast_score.argtypes = [P, I, I, I64, I, I, I]
         lib.oracle_orientation_bin.restype = I
@@ -68,9 +70,10 @@ def offsets(scale: float, angle_bin: int):
 
 
 def extract(image: np.ndarray, width: int, height: int, kps: np.ndarray, triplets: np.ndarray,
-            scales=(1.0,)) -> np.ndarray:
+            scales=(1.0,), weights=None) -> np.ndarray:
     """Descriptors (n, 64) uint8.  image: (H, pitch) uint8; kps: (n, 4) int32
-    (x, y, angle_bin, scale_idx); triplets (512, 6) uint8."""
+    (x, y, angle_bin, scale_idx); triplets (512, 6) uint8; weights: None for the
+    7x7 patches, or 64 uint8 weights of the 8x8 patches (row-major)."""
     image = _c(image, np.uint8)
     kps = _c(kps, np.int32).reshape(-1, 4)
     n = kps.shape[0]
@@ -79,6 +82,15 @@ def extract(image: np.ndarray, width: int, height: int, kps: np.ndarray, triplet
     assert trip.size == 512 * 6
     sc = _c(scales, np.float64)
     out = np.zeros((n, 64), dtype=np.uint8)
+    if weights is not None:
+        wt = _c(weights, np.uint8).reshape(-1)
+        assert wt.size == 64
+        rc = _load().oracle_extract_weighted(image.ctypes.data, width, height, image.shape[1], kx.ctypes.data,
+                                             ky.ctypes.data, kb.ctypes.data, ks.ctypes.data, n, trip.ctypes.data,
+                                             sc.ctypes.data, sc.size, wt.ctypes.data, out.ctypes.data)
+        if rc != 0:
+            raise ValueError("oracle_extract_weighted: invalid scale index or triplet")
+        return out
     rc = _load().oracle_extract(image.ctypes.data, width, height, image.shape[1], kx.ctypes.data, ky.ctypes.data,
                                 kb.ctypes.data, ks.ctypes.data, n, trip.ctypes.data, sc.ctypes.data, sc.size,
                                 out.ctypes.data)

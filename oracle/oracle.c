@@ -31,6 +31,13 @@
  *     is the best over the other train indices; accepted iff 1000*d1 < r*d2 with
  *     r = rha(1000*ratio); an absent second match has distance 65535.
  *
+ * Weighted patches (Sec. 3.2, "Weighing pixels in LATCH patches": 8x8 patches
+ * whose pixels each carry a weight; zero weights on the last row and column give
+ * the 7x7 result): pixel (i, j), i, j = 0..7, of the patch centred at (cx, cy) is
+ * window pixel (cx - 3 + j, cy - 3 + i) with weight w[8 i + j], a non-negative
+ * integer (0..255); the distance is the weighted sum of squared differences, so
+ * every triplet coordinate must lie in [3, 43].
+ *
  * Keypoint detection (Sec. 3.2: keypoints come from the FAST detector, and the
  * window is read at the keypoint's orientation).  The paper uses a library FAST
  * and states no parameters; readings:
@@ -145,6 +152,49 @@ int oracle_extract(const uint8_t *img, int width, int height, int64_t pitch, con
             const uint8_t *tr = triplets + 6 * t;
             int64_t d1 = patch_ssd(win, tr[0], tr[1], tr[2], tr[3]); /* ||P_A - P_1||^2 */
             int64_t d2 = patch_ssd(win, tr[0], tr[1], tr[4], tr[5]); /* ||P_A - P_2||^2 */
+            if (d1 > d2) d[t >> 3] |= (uint8_t)(1u << (t & 7));
+        }
+    }
+    return 0;
+}
+
+/* Weighted squared distance between two 8x8 patches of the window (Sec. 3.2,
+ * weighted patches): sum over i, j = 0..7 of w[8 i + j] times the squared
+ * difference of window pixels (px - 3 + j, py - 3 + i) and (qx - 3 + j, qy - 3 + i). */
+static int64_t patch_wssd(const int32_t *win, int px, int py, int qx, int qy, const uint8_t *w) {
+    int64_t acc = 0;
+    for (int i = 0; i < 8; ++i)
+        for (int j = 0; j < 8; ++j) {
+            const int64_t d = (int64_t)win[(py - PATCH_R + i) * WIN + (px - PATCH_R + j)] -
+                              (int64_t)win[(qy - PATCH_R + i) * WIN + (qx - PATCH_R + j)];
+            acc += (int64_t)w[8 * i + j] * d * d;
+        }
+    return acc;
+}
+
+/*
+ * LATCH descriptors with weighted 8x8 patches (Sec. 3.1 Eq. 1 with each squared
+ * Frobenius distance weighted pixel by pixel, Sec. 3.2).  As oracle_extract, with
+ * `weights` the 64 patch weights (row-major 8x8) and triplet coordinates in [3, 43].
+ * Returns 0, or -1 on an invalid scale index or triplet.
+ */
+int oracle_extract_weighted(const uint8_t *img, int width, int height, int64_t pitch, const int32_t *kx,
+                            const int32_t *ky, const int32_t *kbin, const int32_t *kscale, int n,
+                            const uint8_t *triplets, const double *scales, int nscales, const uint8_t *weights,
+                            uint8_t *out) {
+    int32_t dx[WIN * WIN], dy[WIN * WIN], win[WIN * WIN];
+    for (int t = 0; t < 6 * NBITS; ++t)
+        if (triplets[t] < PATCH_R || triplets[t] > WIN - 2 - PATCH_R) return -1;
+    for (int k = 0; k < n; ++k) {
+        if (kscale[k] < 0 || kscale[k] >= nscales) return -1;
+        oracle_offsets(scales[kscale[k]], kbin[k], dx, dy);
+        sample_window(img, width, height, pitch, kx[k], ky[k], dx, dy, win);
+        uint8_t *d = out + (int64_t)k * (NBITS / 8);
+        memset(d, 0, NBITS / 8);
+        for (int t = 0; t < NBITS; ++t) {
+            const uint8_t *tr = triplets + 6 * t;
+            const int64_t d1 = patch_wssd(win, tr[0], tr[1], tr[2], tr[3], weights);
+            const int64_t d2 = patch_wssd(win, tr[0], tr[1], tr[4], tr[5], weights);
             if (d1 > d2) d[t >> 3] |= (uint8_t)(1u << (t & 7));
         }
     }

@@ -1,16 +1,28 @@
-"""Roofline bookkeeping for the benchmark: algorithmic work per launch of each
-kernel and the peak it is bounded by.
+"""Roofline bookkeeping for the benchmark: the algorithmic work per launch of each
+kernel and the measured ceiling it is judged against.
 
 Algorithmic work (independent of how a kernel computes it):
-  extraction  per descriptor: 512 triplets x 2 patch distances x 49 pixels x
-              2 integer ops (subtract, multiply-add) = 100,352 int32 ops;
-              bytes: the 2,304 window samples it reads + 64 bytes written.
-  popc match  per pair: 16 x 32-bit population counts (512 bits), the
-              quarter-rate pipe that bounds the XOR+POPC kernel.
+  extraction   per descriptor: 512 triplets x 2 patch distances x 49 pixels x 2
+               integer ops (subtract, multiply-add) = 100,352 int32 ops (Eq. 1).
+  popc match   per pair: the 512-bit XOR and population count, 16 words each
+               (Sec. 4's Hamming distance).
   tensor match per pair: 2 x 512 multiply-adds of 0/1 values = 1,024 flop.
-Peaks: int32 issue = 152 SMs x 128 lanes x SM clock; POPC = 152 x 16 x clock;
-8-bit-float tensor = measured dense bf16 x 2 (nominal fp8/bf16 ratio);
-clock = the maximum SM clock measured by the driver.
+
+Ceilings:
+  int32 ops    the measured issue rate of the plain integer add (IADD3) per SM per
+               clock x SMs x the maximum SM clock; the extraction also reports the
+               same work against the measured dp4a rate (4 multiply-adds per lane).
+  popc match   the best split of a pair's 16 words between the population-count
+               pipe (one POPC per word) and the logic pipe (carry-save adders, which
+               fold words with LOP3 and leave fewer POPC), from the measured rates of
+               both pipes (`popc_pair_ceiling`).
+  tensor       8-bit float: the measured dense bf16 GEMM throughput x 2
+               (the nominal fp8 / bf16 ratio; the measured tcgen05 issue rates of
+               both kinds confirm the ratio), burst for a kernel timed alone and
+               sustained for one timed inside a long step.
+Per-clock pipe rates come from a throughput probe on this GPU, stored in
+``pipe_rates.json``; the clocks and the bf16 / HBM figures from the driver's
+measured-peaks file.
 """
 from __future__ import annotations
 
@@ -18,14 +30,17 @@ import hashlib
 import json
 import os
 
-SMS = 152
-INT_LANES_PER_SM = 128
-POPC_PER_SM = 16
 EXTRACT_OPS_PER_DESC = 512 * 2 * 49 * 2
-POPC_PER_PAIR = 16
+EXTRACT_DP4A_PER_DESC = 512 * 4 * 49 // 4  # D1 - D2 as four 49-term u8 dot products, 4 multiply-adds per dp4a
+POPC_WORDS_PER_PAIR = 16
 TENSOR_FLOP_PER_PAIR = 2 * 512
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
+RATES_PATH = os.path.join(HERE, "pipe_rates.json")
+
+# used only when pipe_rates.json is absent (marked "nominal" in every report)
+_NOMINAL_RATES = {"sm_count": 152, "per_sm_per_clock": {"iadd3": 128.0, "lop3": 128.0, "imad": 64.0, "dp4a": 64.0,
+                                                         "popc": 16.0}}
 
 
 def _peaks(path):
@@ -37,14 +52,41 @@ def _peaks(path):
             "fallback"
 
 
+def pipe_rates():
+    """(rates dict, source) with rates["per_sm_per_clock"][pipe] in lane operations."""
+    try:
+        with open(RATES_PATH) as f:
+            return json.load(f), "measured (pipe_rates.json)"
+    except OSError:
+        return _NOMINAL_RATES, "nominal (no pipe_rates.json)"
+
+
+def popc_pair_ceiling(logic: float, popc: float):
+    """Pairs per SM per clock for the best split of 16 words: w words counted by POPC
+    (1 XOR + 1 POPC + 1 add each), the other 16 - w folded by a carry-save adder tree
+    (1 XOR + 2 LOP3 per word folded, then one POPC and one shift-add per weight level
+    of the tree, ceil(log2(16 - w + 1)) levels).  The two pipes issue in parallel,
+    so a split costs max(logic ops / logic rate, POPC / POPC rate) clocks per pair."""
+    best, best_w = None, None
+    for w in range(0, 17):
+        f = 16 - w
+        levels = 0 if f == 0 else (f).bit_length()
+        logic_ops = 16 + w + 2 * f + levels
+        popc_ops = w + levels
+        clk = max(logic_ops / logic, popc_ops / popc)
+        if best is None or clk < best:
+            best, best_w = clk, w
+    return 1.0 / best, best_w
+
+
 def source_hash(name: str) -> str:
     with open(os.path.join(HERE, "csrc", name), "rb") as f:
         return hashlib.sha1(f.read()).hexdigest()[:12]
 
 
-def traffic(kernel: str, source: str):
-    """dram read+write bytes per launch from the committed ncu summary, if it was
-    taken on the current source of the kernel (else None)."""
+def traffic(kernel: str, source: str, workload: str):
+    """dram read+write bytes per launch from the committed ncu summary for this kernel
+    and workload, if it was taken on the current source of the kernel (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
         lines = open(p).read().splitlines()
@@ -53,35 +95,63 @@ def traffic(kernel: str, source: str):
     h = source_hash(source)
     for line in lines:
         parts = line.split("#", 1)[0].split()
-        if len(parts) >= 3 and parts[0] == kernel and parts[2] == h:
-            return float(parts[1])
+        if len(parts) >= 4 and parts[0] == kernel and parts[1] == workload and parts[3] == h:
+            return float(parts[2])
     return None
 
 
-def report(extract_ms: float, n_desc: int, match_ms: float, pairs: int, path: str, peaks_path: str):
-    """Roofline of the dominant phase (the other under "other").  extract_ms: time of
-    the extraction launches over n_desc descriptors; match_ms: time of the matching
-    launches over `pairs` pairs."""
-    peaks, kind = _peaks(peaks_path)
+def _finish(r, src):
+    r["frac"] = r["achieved"] / r["peak"]
+    r["peak_source"] = src
+    return r
+
+
+def extraction(ms: float, n_desc: int, workload: str, peaks_path: str):
+    """Extraction launch(es) of `ms` over n_desc descriptors."""
+    peaks, pk = _peaks(peaks_path)
+    rates, rk = pipe_rates()
     clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    ext = {"bound": "alu", "achieved": EXTRACT_OPS_PER_DESC * n_desc / (extract_ms / 1e3) / 1e12,
-           "peak": SMS * INT_LANES_PER_SM * clk / 1e12, "unit": "Tops/s (int32)",
-           "kernel": "extract", "units_per_launch": n_desc, "traffic": traffic("extract", "extract.cu"),
-           "note": "bound in practice by the shared-memory data pipe and instruction issue together (each about "
-                   "68-70% busy under ncu: conflict-free patch loads, 1,322 wavefronts per descriptor), not int32 "
-                   "throughput"}
-    if path == "tensor":
-        mat = {"bound": "tensor", "achieved": TENSOR_FLOP_PER_PAIR * pairs / (match_ms / 1e3) / 1e12,
-               "peak": 2.0 * float(peaks["bf16_tflops"]), "unit": "TFLOP/s (fp8 e4m3)", "kernel": "match_tensor",
-               "units_per_launch": pairs, "traffic": traffic("match_tensor", "match_tc.cu")}
-    else:
-        mat = {"bound": "alu", "achieved": POPC_PER_PAIR * pairs / (match_ms / 1e3) / 1e12,
-               "peak": SMS * POPC_PER_SM * clk / 1e12, "unit": "Tpopc/s", "kernel": "match_popc",
-               "units_per_launch": pairs, "traffic": traffic("match_popc", "match_popc.cu")}
-    for r in (ext, mat):
-        r["frac"] = r["achieved"] / r["peak"]
-        r["peak_source"] = f"{kind} (MEASURED_PEAKS.json clock / bf16)" if kind == "measured" else "fallback"
-    dominant = ext if extract_ms >= match_ms else mat
-    out = dict(dominant)
-    out["other"] = mat if dominant is ext else ext
+    sms = rates["sm_count"]
+    r = {"bound": "alu", "kernel": "extract_lanes", "unit": "Tops/s (int32)", "units_per_launch": n_desc,
+         "achieved": EXTRACT_OPS_PER_DESC * n_desc / (ms / 1e3) / 1e12,
+         "peak": rates["per_sm_per_clock"]["iadd3"] * sms * clk / 1e12,
+         "traffic": traffic("extract_lanes", "extract.cu", workload)}
+    dp4a_peak = rates["per_sm_per_clock"]["dp4a"] * sms * clk
+    r["dp4a_view"] = {"achieved_dp4a_per_s": EXTRACT_DP4A_PER_DESC * n_desc / (ms / 1e3),
+                      "peak_dp4a_per_s": dp4a_peak,
+                      "frac": EXTRACT_DP4A_PER_DESC * n_desc / (ms / 1e3) / dp4a_peak}
+    return _finish(r, f"{rk}; clock {pk} (measured-peaks file)")
+
+
+def tensor_match(ms: float, pairs: float, workload: str, peaks_path: str, sustained: bool):
+    peaks, pk = _peaks(peaks_path)
+    bf16 = float(peaks["bf16_tflops_sustained" if sustained else "bf16_tflops"])
+    r = {"bound": "tensor", "kernel": "match_tc", "unit": "TFLOP/s (fp8 e4m3)", "units_per_launch": pairs,
+         "achieved": TENSOR_FLOP_PER_PAIR * pairs / (ms / 1e3) / 1e12, "peak": 2.0 * bf16,
+         "traffic": traffic("match_tc", "match_tc.cu", workload)}
+    return _finish(r, f"{pk} bf16 {'sustained' if sustained else 'burst'} x 2 (nominal fp8/bf16)")
+
+
+def popc_match(ms: float, pairs: float, workload: str, peaks_path: str):
+    peaks, pk = _peaks(peaks_path)
+    rates, rk = pipe_rates()
+    clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    pr = rates["per_sm_per_clock"]
+    per_clk, w = popc_pair_ceiling(pr["lop3"], pr["popc"])
+    peak = per_clk * rates["sm_count"] * clk / 1e9
+    r = {"bound": "alu", "kernel": "match_popc", "unit": "Gpairs/s", "units_per_launch": pairs,
+         "achieved": pairs / (ms / 1e3) / 1e9, "peak": peak,
+         "peak_model": f"best split of 16 words between POPC ({pr['popc']:g}/clk/SM) and carry-save LOP3 "
+                       f"({pr['lop3']:g}/clk/SM): {w} words counted directly",
+         "popc_only_peak": pr["popc"] / POPC_WORDS_PER_PAIR * rates["sm_count"] * clk / 1e9,
+         "traffic": traffic("match_popc", "match_popc.cu", workload)}
+    return _finish(r, f"{rk}; clock {pk} (measured-peaks file)")
+
+
+def dominant(parts):
+    """The roofline record of the longest phase, with the others under "other"."""
+    parts = sorted(parts, key=lambda p: -p[0])
+    out = dict(parts[0][1])
+    if len(parts) > 1:
+        out["other"] = [p[1] for p in parts[1:]] if len(parts) > 2 else parts[1][1]
     return out

@@ -9,6 +9,8 @@ workloads, each timed on its own with its own roofline fraction and clocks:
   plain_640x480_2k        one upright pair, latch_extract x 2 + hamming_match in a graph
   oriented_1920x1080_10k  one oriented / scaled pair on both matching paths
   gallery_16k_x_1M        16,384 queries x 1,048,576 descriptors on both paths
+  detect_extract          oriented FAST on a 4000x3000 image, alone and fused with extraction
+  weighted_8x8            the oriented pair's extraction with Gaussian-weighted 8x8 patches
   serve_poisson           a Poisson request stream through the serving session and
                           through the plain per-request calls
 
@@ -51,7 +53,7 @@ def _args():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="latch", choices=["latch", "reference"])
     p.add_argument("--workload", default="all",
-                   choices=["all", "sfm_batch", "pair", "plain_pair", "gallery", "serve"])
+                   choices=["all", "sfm_batch", "pair", "plain_pair", "gallery", "detect", "weighted", "serve"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--rate", type=float, default=200.0, help="serve: Poisson arrivals per second")
     p.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
@@ -579,6 +581,83 @@ def bench_gallery(args, local):
     return res
 
 
+def bench_detect(args, local):
+    """Oriented FAST on one 4000x3000 image of the batched workload (threshold 20):
+    detection alone, and detection + extraction of every keypoint found in one call
+    (no host round trip)."""
+    import torch
+    import paper_1609_03986_gb300 as P
+    from paper_1609_03986_gb300 import roofline, synth
+    dev = torch.device("cuda", local)
+    name = "detect_extract_4000x3000_t20"
+    w, h = synth.BATCH_W, synth.BATCH_H
+    img = torch.from_numpy(synth.image(synth.seed(3, 0, synth.KIND_IMAGE), w, h)).to(dev)
+    ctx = P.Context(local, triplets=synth.triplets())
+    max_kps = 1 << 18
+    kps = torch.empty((max_kps, 12), dtype=torch.uint8, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+    desc = torch.empty((max_kps, 64), dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    s = int(torch.cuda.current_stream().cuda_stream)
+    P.latch_reserve(ctx.handle, max_kps, 0, 0)
+
+    def det():
+        P.latch_detect(ctx.handle, img, w, h, img.stride(0), 20, 0, max_kps, kps, cnt, s)
+
+    def det_ext():
+        P.latch_detect_extract(ctx.handle, img, w, h, img.stride(0), 20, 0, max_kps, kps, cnt, desc, s)
+
+    clocks = _sub_clocks(local)
+    ms_d = _timed(det, args.steps, args.warmup, flush)
+    ms_de = _timed(det_ext, args.steps, args.warmup, flush)
+    clk = clocks.stop()
+    n = int(cnt.item())
+    ctx.check()
+    ctx.close()
+    ext_ms = ms_de - ms_d
+    rf = roofline.dominant([
+        (ext_ms, roofline.extraction(ext_ms, n, name, PEAKS)),
+        (ms_d, roofline.detection(ms_d, w * h, name, PEAKS))])
+    return {"workload": name, "keypoints": n, "detect_ms": ms_d, "detect_extract_ms": ms_de,
+            "detect_mpix_per_s": w * h / (ms_d / 1e3) / 1e6, "desc_per_s": n / (ms_de / 1e3),
+            "entry": "latch_detect; latch_detect_extract", "roofline": rf, "clocks": clk}
+
+
+def bench_weighted(args, local):
+    """The oriented 1920x1080 pair's extraction with Gaussian-weighted 8x8 patches
+    against the plain 7x7 patches (triplets drawn in [3, 43] for both)."""
+    import torch
+    import paper_1609_03986_gb300 as P
+    from paper_1609_03986_gb300 import roofline, synth
+    dev = torch.device("cuda", local)
+    name = "weighted_8x8_oriented_1920x1080_10k"
+    wl = synth.pair("oriented_scaled_1920x1080_10k")
+    w, h = wl["width"], wl["height"]
+    ctx = P.Context(local, triplets=synth.triplets(synth.seed(2, 0, synth.KIND_TRIPLETS), hi=43))
+    n = sum(len(k) for k in wl["kps"])
+    imgs = [torch.from_numpy(im).to(dev) for im in wl["images"]]
+    kps = torch.from_numpy(np.concatenate([P.pack_keypoints(k) for k in wl["kps"]])).to(dev)
+    desc = torch.empty((n, 64), dtype=torch.uint8, device=dev)
+    b = P.BatchDesc([(t, w, h, t.stride(0)) for t in imgs], [len(k) for k in wl["kps"]], kps, desc, [], 2, 0.8, None)
+    P.latch_reserve_batch(ctx.handle, b)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    s = int(torch.cuda.current_stream().cuda_stream)
+    gauss = np.array([[int(round(255 * np.exp(-((i - 3.5) ** 2 + (j - 3.5) ** 2) / 8.0))) for j in range(8)]
+                      for i in range(8)], np.uint8)
+    clocks = _sub_clocks(local)
+    ms7 = _timed(lambda: P.latch_batch_run(ctx.handle, b, s), args.steps, args.warmup, flush)
+    P.latch_set_patch_weights(ctx.handle, gauss)
+    ms8 = _timed(lambda: P.latch_batch_run(ctx.handle, b, s), args.steps, args.warmup, flush)
+    P.latch_set_patch_weights(ctx.handle, None)
+    clk = clocks.stop()
+    ctx.check()
+    ctx.close()
+    rf = roofline.extraction_weighted(ms8, n, name, PEAKS)
+    return {"workload": name, "entry": "latch_batch_run (2 images, extraction only)", "weights": "Gaussian 8x8",
+            "ms_weighted": ms8, "ms_7x7": ms7, "desc_per_s_weighted": n / (ms8 / 1e3), "desc_per_s_7x7": n / (ms7 / 1e3),
+            "roofline": rf, "clocks": clk}
+
+
 def _serve_inputs(args):
     import paper_1609_03986_gb300 as P
     from paper_1609_03986_gb300 import synth
@@ -761,7 +840,7 @@ def run_latch(args):
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
     single = {"pair": bench_oriented_pair, "plain_pair": bench_plain_pair, "gallery": bench_gallery,
-              "serve": bench_serve}
+              "detect": bench_detect, "weighted": bench_weighted, "serve": bench_serve}
     if args.workload in single:
         print(json.dumps({"metric": METRIC, **single[args.workload](args, local)}))
         return 0
@@ -771,7 +850,8 @@ def run_latch(args):
     if ws == 1 and args.workload == "all":
         torch.cuda.empty_cache()
         for key, fn in (("plain_640x480_2k", bench_plain_pair), ("oriented_scaled_1920x1080_10k", bench_oriented_pair),
-                        ("gallery_16384x1048576", bench_gallery), ("serve", bench_serve)):
+                        ("gallery_16384x1048576", bench_gallery), ("detect_extract_4000x3000", bench_detect),
+                        ("weighted_8x8_1920x1080", bench_weighted), ("serve", bench_serve)):
             sub[key] = fn(args, local)
             torch.cuda.empty_cache()
     if rank != 0:

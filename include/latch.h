@@ -130,6 +130,18 @@ latch_status latch_set_scales(latch_context *ctx, const double *h_scales, int32_
  * after latch_set_triplets or latch_set_scales. */
 latch_status latch_set_triplets(latch_context *ctx, const latch_triplet *h_triplets);
 
+/* Weighted patches (Sec. 3.2, "Weighing pixels in LATCH patches"): with a table of
+ * 64 weights, every later extraction on this context compares 8x8 patches, pixel
+ * (i, j), i, j = 0..7 (row, column), of the patch centred at (cx, cy) being window
+ * pixel (cx - 3 + j, cy - 3 + i) with weight h_weights[8 i + j]:
+ *   bit t = sum w (P_A - P_1)^2 > sum w (P_A - P_2)^2   (strict, exact integers).
+ * Zero weights on row 7 and column 7 and ones elsewhere give exactly the 7x7
+ * descriptor; a Gaussian table weighs the patch centres more.  Triplet coordinates
+ * must then lie in [3, 43] (checked now against the loaded table, and on every
+ * later table).  NULL returns to the plain 7x7 patches.  Synchronous; as with the
+ * triplet table, a captured CUDA graph keeps the weights of its capture. */
+latch_status latch_set_patch_weights(latch_context *ctx, const uint8_t *h_weights);
+
 /* Pre-size the context's scratch memory so that later calls up to these sizes
  * allocate nothing (required before capturing calls in a CUDA graph). */
 latch_status latch_reserve(latch_context *ctx, int64_t max_keypoints, int64_t max_query, int64_t max_train);
@@ -149,6 +161,39 @@ latch_status latch_reserve(latch_context *ctx, int64_t max_keypoints, int64_t ma
  */
 latch_status latch_extract(latch_context *ctx, const latch_image *img, const latch_keypoint *d_kps, int32_t n,
                            const latch_triplet *h_triplets, uint8_t *d_out, latch_stream_t stream);
+
+/*
+ * Oriented keypoints (Sec. 3.2: the keypoints come from the FAST detector, and each
+ * keypoint's orientation sets the angle at which its window is read).  The paper
+ * names the detector only; this library reads it as:
+ *   - FAST-9: the 16 pixels of the radius-3 Bresenham circle around p; p is a corner
+ *     at `threshold` t when 9 contiguous of them (circularly) are all > I(p) + t or
+ *     all < I(p) - t;
+ *   - score: the largest t' >= t at which p is still a corner;
+ *   - a corner is kept when its score is strictly larger than each of its 8
+ *     neighbours' scores (equal neighbours suppress each other);
+ *   - only pixels at least 16 from every border are detected;
+ *   - angle_bin = round_half_away(theta * 16 / pi) mod 32 with theta = atan2(m01,
+ *     m10) of the intensity centroid of the disc dx^2 + dy^2 <= 15^2 (FP64; x right,
+ *     y down, the frame of the window rotation); scale_idx = `scale_idx`.
+ * Keypoints are written in 32x32-pixel cell order (cells row by row from the image
+ * origin, then row by row inside a cell), the first max_kps of them.
+ *   img        image in device memory (see latch_image)
+ *   threshold  1..254;  scale_idx: index into the scale table, given to every keypoint
+ *   d_kps      device out: min(count, max_kps) keypoints
+ *   d_count    device out: one int32, the number of keypoints found (may exceed max_kps)
+ * Asynchronous like every call; read *d_count after synchronising the stream.
+ */
+latch_status latch_detect(latch_context *ctx, const latch_image *img, int32_t threshold, int32_t scale_idx,
+                          int32_t max_kps, latch_keypoint *d_kps, int32_t *d_count, latch_stream_t stream);
+
+/* latch_detect, then the descriptors of the keypoints it wrote (as latch_extract on
+ * d_kps[0 .. min(count, max_kps)) with the context's triplet table), without a host
+ * round trip: the extraction reads the count from d_count.  d_desc: max_kps * 64
+ * bytes, 16-byte aligned; rows from min(count, max_kps) on are left untouched. */
+latch_status latch_detect_extract(latch_context *ctx, const latch_image *img, int32_t threshold, int32_t scale_idx,
+                                  int32_t max_kps, latch_keypoint *d_kps, int32_t *d_count, uint8_t *d_desc,
+                                  latch_stream_t stream);
 
 /*
  * Brute-force Hamming matching (Sec. 4): for every query descriptor the nearest

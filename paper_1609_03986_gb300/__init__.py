@@ -122,6 +122,9 @@ EXPORTS = [
     ("latch_session_last_error", ctypes.c_char_p, [_P]),
     ("hamming_match_noalloc", ctypes.c_int, [_P, _I32, _P, _I32, _I32, _F, _P, _P]),
     ("hamming_match_noalloc_status", ctypes.c_int, []),
+    ("latch_set_patch_weights", ctypes.c_int, [_P, _P]),
+    ("latch_detect", ctypes.c_int, [_P, ctypes.POINTER(latch_image), _I32, _I32, _I32, _P, _P, _P]),
+    ("latch_detect_extract", ctypes.c_int, [_P, ctypes.POINTER(latch_image), _I32, _I32, _I32, _P, _P, _P, _P]),
 ]
 
 
@@ -189,6 +192,17 @@ def latch_set_triplets(ctx, triplets) -> None:
     _check(ctx, library().latch_set_triplets(ctx, t.ctypes.data))
 
 
+def latch_set_patch_weights(ctx, weights) -> None:
+    """64 uint8 weights of the 8x8 patches (row-major), or None for the 7x7 patches."""
+    if weights is None:
+        _check(ctx, library().latch_set_patch_weights(ctx, None))
+        return
+    w = np.ascontiguousarray(weights, dtype=np.uint8).reshape(-1)
+    if w.size != 64:
+        raise ValueError("the weight table holds 8 x 8 bytes")
+    _check(ctx, library().latch_set_patch_weights(ctx, w.ctypes.data))
+
+
 def latch_reserve(ctx, max_keypoints: int, max_query: int, max_train: int) -> None:
     _check(ctx, library().latch_reserve(ctx, max_keypoints, max_query, max_train))
 
@@ -205,6 +219,22 @@ def latch_extract(ctx, image, width: int, height: int, pitch: int, kps, n: int, 
             raise ValueError("triplet table must hold 512 x 6 bytes")
         tp = t.ctypes.data
     _check(ctx, library().latch_extract(ctx, ctypes.byref(img), _ptr(kps), n, tp, _ptr(out), stream))
+
+
+def latch_detect(ctx, image, width: int, height: int, pitch: int, threshold: int, scale_idx: int, max_kps: int,
+                 kps_out, count_out, stream: int = 0) -> None:
+    """Oriented FAST keypoints (device pointers image, kps_out, count_out)."""
+    img = latch_image(_ptr(image), width, height, pitch)
+    _check(ctx, library().latch_detect(ctx, ctypes.byref(img), threshold, scale_idx, max_kps, _ptr(kps_out),
+                                       _ptr(count_out), stream))
+
+
+def latch_detect_extract(ctx, image, width: int, height: int, pitch: int, threshold: int, scale_idx: int,
+                         max_kps: int, kps_out, count_out, desc_out, stream: int = 0) -> None:
+    """Oriented FAST keypoints and their descriptors, no host round trip."""
+    img = latch_image(_ptr(image), width, height, pitch)
+    _check(ctx, library().latch_detect_extract(ctx, ctypes.byref(img), threshold, scale_idx, max_kps, _ptr(kps_out),
+                                               _ptr(count_out), _ptr(desc_out), stream))
 
 
 def hamming_match(ctx, query, nq: int, train, nt: int, k: int, ratio: float, out, path: int = PATH_AUTO,
@@ -458,6 +488,12 @@ def pack_keypoints(kps: np.ndarray) -> np.ndarray:
     return rec.view(np.uint8).reshape(-1, 12)
 
 
+def unpack_keypoints(raw: np.ndarray) -> np.ndarray:
+    """(n, 12) uint8 latch_keypoint records -> (n, 4) int32 (x, y, angle_bin, scale_idx)."""
+    rec = np.ascontiguousarray(raw, dtype=np.uint8).reshape(-1).view(KEYPOINT_DTYPE)
+    return np.stack([rec["x"], rec["y"], rec["angle_bin"], rec["scale_idx"]], axis=1).astype(np.int32)
+
+
 def matches_from_bytes(raw: np.ndarray) -> np.ndarray:
     """(nq, 16) uint8 -> structured array of latch_match records."""
     return np.ascontiguousarray(raw, dtype=np.uint8).reshape(-1).view(MATCH_DTYPE)
@@ -504,6 +540,23 @@ class Context:
         latch_extract(self.handle, image, width, height, image.stride(0), kps, n, triplets, out,
                       self._stream(stream))
         return out
+
+    def detect(self, image, width: int, height: int, threshold: int = 20, max_kps: int = 1 << 16, scale_idx: int = 0,
+               with_descriptors: bool = False, stream=None):
+        """image: (H, pitch) uint8 CUDA tensor.  Returns (keypoints (max_kps, 12) uint8
+        tensor, count (1,) int32 tensor[, descriptors (max_kps, 64) uint8 tensor]); the
+        first min(count, max_kps) rows are valid once the stream is synchronised."""
+        import torch
+        kps = torch.empty((max(max_kps, 1), 12), dtype=torch.uint8, device=image.device)
+        cnt = torch.zeros(1, dtype=torch.int32, device=image.device)
+        if with_descriptors:
+            desc = torch.empty((max(max_kps, 1), DESC_BYTES), dtype=torch.uint8, device=image.device)
+            latch_detect_extract(self.handle, image, width, height, image.stride(0), threshold, scale_idx, max_kps,
+                                 kps, cnt, desc, self._stream(stream))
+            return kps, cnt, desc
+        latch_detect(self.handle, image, width, height, image.stride(0), threshold, scale_idx, max_kps, kps, cnt,
+                     self._stream(stream))
+        return kps, cnt
 
     def match(self, query, train, k: int = 2, ratio: float = 0.8, path: int = PATH_AUTO, out=None, stream=None):
         """query (nq, 64), train (nt, 64) uint8 CUDA tensors -> (nq, 16) uint8 tensor of latch_match."""

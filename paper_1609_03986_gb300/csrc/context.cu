@@ -126,12 +126,15 @@ static int choose_match_path(const latch_context* ctx, int64_t nq, int64_t nt) {
     return nq * nt >= ctx->tensor_min_pairs ? LATCH_PATH_TENSOR : LATCH_PATH_POPC;
 }
 
-static latch_status validate_triplets(latch_context* ctx, const latch_triplet* t) {
+// Triplet coordinates must keep every patch inside the 48x48 window: [3, 44] for the
+// 7x7 patches, [3, 43] for the weighted 8x8 ones (one more pixel right and down).
+static latch_status validate_triplets(latch_context* ctx, const latch_triplet* t, bool weighted) {
+    const int hi = weighted ? kWin - 2 - kPatchR : kWin - 1 - kPatchR;
     for (int i = 0; i < kBits; ++i) {
         const uint8_t* c = &t[i].ax;
         for (int j = 0; j < 6; ++j)
-            if (c[j] < kPatchR || c[j] > kWin - 1 - kPatchR)
-                return fail(ctx, LATCH_EINVAL, "triplet %d coordinate %d = %d outside [3, 44]", i, j, c[j]);
+            if (c[j] < kPatchR || c[j] > hi)
+                return fail(ctx, LATCH_EINVAL, "triplet %d coordinate %d = %d outside [3, %d]", i, j, c[j], hi);
     }
     return LATCH_OK;
 }
@@ -140,7 +143,7 @@ static latch_status validate_triplets(latch_context* ctx, const latch_triplet* t
 // loading one needs no device copy and orders itself with the calls that follow.
 static latch_status load_triplets(latch_context* ctx, const latch_triplet* t) {
     if (ctx->has_trip && memcmp(ctx->h_trip, t, sizeof(ctx->h_trip)) == 0) return LATCH_OK;
-    latch_status st = validate_triplets(ctx, t);
+    latch_status st = validate_triplets(ctx, t, ctx->weighted);
     if (st != LATCH_OK) return st;
     memcpy(ctx->h_trip, t, sizeof(ctx->h_trip));
     build_triplet_offsets(ctx->h_trip, ctx->h_trip_offsets);
@@ -271,6 +274,21 @@ latch_status latch_set_triplets(latch_context* ctx, const latch_triplet* h_tripl
     return load_triplets(ctx, h_triplets);
 }
 
+latch_status latch_set_patch_weights(latch_context* ctx, const uint8_t* h_weights) {
+    if (!ctx) return fail(ctx, LATCH_EINVAL, "NULL context");
+    if (!h_weights) {
+        ctx->weighted = false;
+        return LATCH_OK;
+    }
+    if (ctx->has_trip) {
+        latch_status st = validate_triplets(ctx, ctx->h_trip, true);
+        if (st != LATCH_OK) return st;
+    }
+    for (int i = 0; i < 64; ++i) ctx->patch_weights[i] = h_weights[i];
+    ctx->weighted = true;
+    return LATCH_OK;
+}
+
 latch_status latch_reserve(latch_context* ctx, int64_t max_keypoints, int64_t max_query, int64_t max_train) {
     if (!ctx) return fail(ctx, LATCH_EINVAL, "NULL context");
     if (max_keypoints < 0 || max_query < 0 || max_train < 0) return fail(ctx, LATCH_EINVAL, "negative size");
@@ -337,6 +355,68 @@ latch_status latch_extract(latch_context* ctx, const latch_image* img, const lat
     latch_status st = scratch_reserve(ctx, 0, extract_scratch_bytes(img, n), &scratch);
     if (st != LATCH_OK) return st;
     return cuda_check(ctx, launch_extract(ctx, img, d_kps, n, d_out, scratch, s), "extract kernel launch");
+}
+
+static latch_status validate_image(latch_context* ctx, const latch_image* img) {
+    if (!img) return fail(ctx, LATCH_EINVAL, "NULL image");
+    if (img->width < 1 || img->height < 1 || img->width > 32768 || img->height > 32768)
+        return fail(ctx, LATCH_EINVAL, "image size %dx%d outside [1, 32768]", img->width, img->height);
+    if (img->pitch < img->width || img->pitch % 16 != 0)
+        return fail(ctx, LATCH_EINVAL, "pitch %lld must be >= width and a multiple of 16", (long long)img->pitch);
+    if (!img->data || (reinterpret_cast<uintptr_t>(img->data) & 15))
+        return fail(ctx, LATCH_EINVAL, "image data must be non-NULL and 16-byte aligned");
+    return LATCH_OK;
+}
+
+static latch_status validate_detect(latch_context* ctx, const latch_image* img, int32_t threshold, int32_t scale_idx,
+                                    int32_t max_kps, const latch_keypoint* d_kps, const int32_t* d_count) {
+    if (!ctx) return fail(ctx, LATCH_EINVAL, "NULL context");
+    latch_status st = validate_image(ctx, img);
+    if (st != LATCH_OK) return st;
+    if (threshold < 1 || threshold > 254) return fail(ctx, LATCH_EINVAL, "FAST threshold %d not in [1, 254]", threshold);
+    if (scale_idx < 0 || scale_idx >= ctx->nscales)
+        return fail(ctx, LATCH_EINVAL, "scale index %d outside the scale table (%d entries)", scale_idx, ctx->nscales);
+    if (max_kps < 0) return fail(ctx, LATCH_EINVAL, "max_kps = %d < 0", max_kps);
+    if (!d_count || (reinterpret_cast<uintptr_t>(d_count) & 3)) return fail(ctx, LATCH_EINVAL, "bad d_count");
+    if (max_kps > 0 && (!d_kps || (reinterpret_cast<uintptr_t>(d_kps) & 3)))
+        return fail(ctx, LATCH_EINVAL, "NULL or misaligned keypoint output");
+    return LATCH_OK;
+}
+
+latch_status latch_detect(latch_context* ctx, const latch_image* img, int32_t threshold, int32_t scale_idx,
+                          int32_t max_kps, latch_keypoint* d_kps, int32_t* d_count, latch_stream_t stream) {
+    latch_status st = validate_detect(ctx, img, threshold, scale_idx, max_kps, d_kps, d_count);
+    if (st != LATCH_OK) return st;
+    LATCH_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    void* scratch = nullptr;
+    st = scratch_reserve(ctx, 4, detect_scratch_bytes(img), &scratch);
+    if (st != LATCH_OK) return st;
+    return cuda_check(ctx,
+                      launch_detect(img, threshold, scale_idx, max_kps, d_kps, d_count, scratch,
+                                    static_cast<cudaStream_t>(stream)),
+                      "detection launch");
+}
+
+latch_status latch_detect_extract(latch_context* ctx, const latch_image* img, int32_t threshold, int32_t scale_idx,
+                                  int32_t max_kps, latch_keypoint* d_kps, int32_t* d_count, uint8_t* d_desc,
+                                  latch_stream_t stream) {
+    latch_status st = validate_detect(ctx, img, threshold, scale_idx, max_kps, d_kps, d_count);
+    if (st != LATCH_OK) return st;
+    if (max_kps > 0 && (!d_desc || (reinterpret_cast<uintptr_t>(d_desc) & 15)))
+        return fail(ctx, LATCH_EINVAL, "NULL or misaligned descriptor output");
+    if (!ctx->has_trip) return fail(ctx, LATCH_EINVAL, "no triplet table: call latch_set_triplets");
+    LATCH_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void* dscratch = nullptr;
+    void* escratch = nullptr;
+    st = scratch_reserve(ctx, 4, detect_scratch_bytes(img), &dscratch);
+    if (st == LATCH_OK) st = scratch_reserve(ctx, 0, extract_scratch_bytes(img, max_kps), &escratch);
+    if (st != LATCH_OK) return st;
+    st = cuda_check(ctx, launch_detect(img, threshold, scale_idx, max_kps, d_kps, d_count, dscratch, s),
+                    "detection launch");
+    if (st != LATCH_OK) return st;
+    return cuda_check(ctx, launch_extract_dev_count(ctx, img, d_kps, max_kps, d_count, d_desc, escratch, s),
+                      "extraction launch");
 }
 
 latch_status hamming_match(latch_context* ctx, const uint8_t* d_query, int32_t nq, const uint8_t* d_train,

@@ -99,7 +99,17 @@ struct ExtractParams {
     int32_t count;        // images in this launch
     int32_t nscales;
     TileGeom tg;
+    const int32_t* n_dev;  // single-image launches: the keypoint count on the device (n[0] is its bound), or NULL
 };
+
+// Keypoints of image `img` in this launch.
+template <int NI>
+__device__ __forceinline__ int keypoints_of(const ExtractParams<NI>& prm, int img) {
+    const int n = prm.n[img];
+    if (!prm.n_dev) return n;
+    const int d = *prm.n_dev;
+    return d < n ? (d > 0 ? d : 0) : n;
+}
 
 // Sorted keypoint record: x, y, output row (the keypoint's index), table (scale *
 // 32 + bin) | launch-local image << 16.
@@ -134,7 +144,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_count_kernel(
     griddep_launch_dependents();
     const int img = image_of_block(prm, blockIdx.x);
     const CellGrid g = prm.grid[img];
-    const int n = prm.n[img], kp0 = prm.kp0[img];
+    const int n = keypoints_of(prm, img), kp0 = prm.kp0[img];
     int* cnt = cells + prm.cell0[img];
     const int i0 = (blockIdx.x - prm.blk0[img]) * kSortKps + threadIdx.x;
     // all loads first, then the atomics
@@ -178,7 +188,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_count_kernel(
         // release: the block's count increments (ordered before this by the barrier
         // above) and its total, before its arrival
         __threadfence();
-        const int nblk = (n + kSortKps - 1) / kSortKps;
+        const int nblk = (prm.n[img] + kSortKps - 1) / kSortKps;  // every launched block of the image arrives
         s_flag = atomicAdd(&img_done[img], 1) == nblk - 1;
     }
     __syncthreads();
@@ -235,7 +245,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(
     griddep_launch_dependents();
     const int img = image_of_block(prm, blockIdx.x);
     const CellGrid g = prm.grid[img];
-    const int n = prm.n[img], kp0 = prm.kp0[img];
+    const int n = keypoints_of(prm, img), kp0 = prm.kp0[img];
     const int* start = cells + prm.cell0[img];
     const int i0 = (blockIdx.x - prm.blk0[img]) * kSortKps + threadIdx.x;
     latch_keypoint kp[kSortKps / kSortThreads];
@@ -323,6 +333,53 @@ __device__ __forceinline__ uint32_t eval_chunk(const uint2* trip, const uint32_t
     return byte;
 }
 
+// Weights of the 8x8 patch pixels (row-major), a kernel parameter: with the pixel
+// loops unrolled, every weight is a constant-bank operand of its multiply-add.
+struct PatchWeights {
+    int32_t w[64];
+};
+
+// One 8-pixel patch row: the 8 bytes at byte `sh` of word p[0] onwards, as two words.
+__device__ __forceinline__ void patch_row8(const uint32_t* p, uint32_t sh, uint32_t& lo, uint32_t& hi) {
+    const uint32_t w0 = p[0], w1 = p[1];
+    const uint32_t w2 = sh != 0 ? p[2] : 0u;
+    lo = __funnelshift_r(w0, w1, 8 * sh);
+    hi = __funnelshift_r(w1, w2, 8 * sh);
+}
+
+// Eq. 1 with weighted 8x8 patches (Sec. 3.2, weighing pixels in LATCH patches) for
+// triplets 8 c .. 8 c + 7: D1 - D2 = sum w (C1 - C2)(C1 + C2 - 2 A), exact in int32
+// (|w (C1 - C2)(C1 + C2 - 2 A)| <= 255 * 255^2 per pixel, 64 pixels).
+__device__ __forceinline__ uint32_t eval_chunk_weighted(const uint2* trip, const uint32_t* wl, int c,
+                                                        const PatchWeights& pw) {
+    uint32_t byte = 0;
+#pragma unroll 1
+    for (int i = 0; i < 8; ++i) {
+        const uint2 e = trip[8 * c + i];
+        const uint32_t* pa = wl + (e.x & 0xffffu);
+        const uint32_t* p1 = wl + (e.x >> 16);
+        const uint32_t* p2 = wl + (e.y & 0xffffu);
+        const uint32_t sa = (e.y >> 16) & 3u, s1 = (e.y >> 18) & 3u, s2 = (e.y >> 20) & 3u;
+        int acc = 0;
+#pragma unroll
+        for (int rr = 0; rr < 8; ++rr) {
+            uint32_t a[2], c1[2], c2[2];
+            patch_row8(pa + rr * kRowWords, sa, a[0], a[1]);
+            patch_row8(p1 + rr * kRowWords, s1, c1[0], c1[1]);
+            patch_row8(p2 + rr * kRowWords, s2, c2[0], c2[1]);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int av = static_cast<int>((a[j >> 2] >> (8 * (j & 3))) & 0xffu);
+                const int cv = static_cast<int>((c1[j >> 2] >> (8 * (j & 3))) & 0xffu);
+                const int dv = static_cast<int>((c2[j >> 2] >> (8 * (j & 3))) & 0xffu);
+                acc += pw.w[rr * 8 + j] * ((cv - dv) * (cv + dv - 2 * av));
+            }
+        }
+        byte |= (acc > 0 ? 1u : 0u) << i;
+    }
+    return byte;
+}
+
 // Expanded row segment for 16 descriptor bits: byte q is 0x38 (E4M3 1.0) when bit q
 // is set.  x * 0x00204081 moves bit q of a 4-bit x to bit 8q (no two partial
 // products overlap).
@@ -343,9 +400,10 @@ struct LanesSmem {  // static part
 // Block b takes chunks [b U / G, (b+1) U / G) of the U = 64 * ceil(V / 32) chunks
 // of the launch's V records (cell-sorted), batch by batch.  Warps 0-11 build the
 // windows of batch i into buffer i % 2 while warps 12-27 evaluate batch i - 1.
-template <int NI>
+template <int NI, bool kWeighted>
 __global__ void __launch_bounds__(kThreads, 1) extract_lanes_kernel(
     const __grid_constant__ ExtractParams<NI> prm, const __grid_constant__ LaneTriplets tt,
+    const __grid_constant__ PatchWeights pw,
     const int4* __restrict__ recs, const int* __restrict__ counters, const int16_t* __restrict__ toff,
     uint8_t* __restrict__ out, uint8_t* __restrict__ exp_out, int32_t* __restrict__ pop_out,
     uint32_t* __restrict__ flags) {
@@ -527,7 +585,12 @@ __global__ void __launch_bounds__(kThreads, 1) extract_lanes_kernel(
         const uint32_t* wl = s_win0 + buf * (kBatch * kLaneWords) + lane * kLaneWords;
         uint32_t v = 0;  // byte c - wa: chunk c
 #pragma unroll 1
-        for (int c = wa; c < wb; ++c) v |= eval_chunk(S.trip, wl, c) << (8 * (c - wa));
+        for (int c = wa; c < wb; ++c) {
+            if constexpr (kWeighted)
+                v |= eval_chunk_weighted(S.trip, wl, c, pw) << (8 * (c - wa));
+            else
+                v |= eval_chunk(S.trip, wl, c) << (8 * (c - wa));
+        }
         // output rows: this lane's keypoint, and the keypoints whose expanded sector
         // this lane writes (lane / 2 and 16 + lane / 2)
         const int32_t row = S.row[buf][lane];
@@ -674,12 +737,14 @@ size_t extract_batch_scratch_bytes(const latch_image* imgs, const int64_t* n, in
 
 size_t extract_scratch_bytes(const latch_image* img, int64_t n) { return extract_batch_scratch_bytes(img, &n, 1); }
 
-template <int NI>
+template <int NI, bool kWeighted>
 static cudaError_t set_extract_attributes() {
-    cudaError_t e = cudaFuncSetAttribute(extract_lanes_kernel<NI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(extract_lanes_kernel<NI, kWeighted>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(extract_smem_bytes(tile_geom(kMaxReach + 1))));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(extract_lanes_kernel<NI>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        e = cudaFuncSetAttribute(extract_lanes_kernel<NI, kWeighted>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 100);
     return e;
 }
 
@@ -687,10 +752,11 @@ template <int NI>
 static cudaError_t launch_chunk(const latch_context* ctx, const latch_image* imgs, const int64_t* kp0,
                                 const int64_t* n, int i0, int i1, const latch_keypoint* d_kps, uint8_t* d_out,
                                 uint8_t* exp_out, int32_t* pop_out, uint8_t* scratch, cudaStream_t stream,
-                                uint32_t* flags) {
-    static unsigned long long attr_done = 0;
+                                uint32_t* flags, const int32_t* n_dev) {
+    static unsigned long long attr_done[2] = {0, 0};
     const TileGeom tg = tile_geom(ctx->reach);
-    cudaError_t e = once_per_device(&attr_done, set_extract_attributes<NI>);
+    cudaError_t e = ctx->weighted ? once_per_device(&attr_done[1], set_extract_attributes<NI, true>)
+                                  : once_per_device(&attr_done[0], set_extract_attributes<NI, false>);
     if (e != cudaSuccess) return e;
     EncodeTiledFn enc = extract_encode_fn();
     if (!enc) return cudaErrorNotSupported;
@@ -706,6 +772,7 @@ static cudaError_t launch_chunk(const latch_context* ctx, const latch_image* img
     prm->count = i1 - i0;
     prm->nscales = ctx->nscales;
     prm->tg = tg;
+    prm->n_dev = n_dev;
     int64_t cell0 = 0;
     int blocks = 0;
     for (int i = i0; i < i1; ++i) {
@@ -745,9 +812,12 @@ static cudaError_t launch_chunk(const latch_context* ctx, const latch_image* img
         // the chunks are split evenly over the blocks, at least item_kps keypoints' worth each
         const int64_t want = (l.nkp + ctx->item_kps - 1) / ctx->item_kps;
         const int64_t grid = want < ctx->sm_count ? want : ctx->sm_count;
-        e = launch_chained(extract_lanes_kernel<NI>, dim3(static_cast<unsigned>(grid)), dim3(kThreads),
-                           extract_smem_bytes(tg), stream, *prm, *tt, static_cast<const int4*>(recs),
-                           static_cast<const int*>(counters), ctx->d_tile_offsets, d_out, exp_out, pop_out, flags);
+        PatchWeights pw;
+        for (int i = 0; i < 64; ++i) pw.w[i] = ctx->patch_weights[i];
+        e = launch_chained(ctx->weighted ? extract_lanes_kernel<NI, true> : extract_lanes_kernel<NI, false>,
+                           dim3(static_cast<unsigned>(grid)), dim3(kThreads), extract_smem_bytes(tg), stream, *prm, *tt,
+                           pw, static_cast<const int4*>(recs), static_cast<const int*>(counters), ctx->d_tile_offsets,
+                           d_out, exp_out, pop_out, flags);
         delete tt;
     }
     delete prm;
@@ -769,11 +839,11 @@ cudaError_t launch_extract_batch(const latch_context* ctx, const latch_image* im
             // instance that fits keeps the launch's parameter block small
             const int ni = i1 - i0;
             const cudaError_t e =
-                ni == 1    ? launch_chunk<1>(ctx, imgs, kp0, n, i0, i1, d_kps, d_out, exp_out, pop_out, base, stream, flags)
-                : ni <= 4  ? launch_chunk<4>(ctx, imgs, kp0, n, i0, i1, d_kps, d_out, exp_out, pop_out, base, stream, flags)
-                : ni <= 16 ? launch_chunk<16>(ctx, imgs, kp0, n, i0, i1, d_kps, d_out, exp_out, pop_out, base, stream, flags)
+                ni == 1    ? launch_chunk<1>(ctx, imgs, kp0, n, i0, i1, d_kps, d_out, exp_out, pop_out, base, stream, flags, nullptr)
+                : ni <= 4  ? launch_chunk<4>(ctx, imgs, kp0, n, i0, i1, d_kps, d_out, exp_out, pop_out, base, stream, flags, nullptr)
+                : ni <= 16 ? launch_chunk<16>(ctx, imgs, kp0, n, i0, i1, d_kps, d_out, exp_out, pop_out, base, stream, flags, nullptr)
                            : launch_chunk<kBatchImages>(ctx, imgs, kp0, n, i0, i1, d_kps, d_out, exp_out, pop_out,
-                                                        base, stream, flags);
+                                                        base, stream, flags, nullptr);
             if (e != cudaSuccess) return e;
         }
         base += chunk_layout(imgs, n, i0, i1).total;
@@ -785,6 +855,15 @@ cudaError_t launch_extract(const latch_context* ctx, const latch_image* img, con
                            uint8_t* d_out, void* scratch, cudaStream_t stream) {
     const int64_t kp0 = 0, nn = n;
     return launch_extract_batch(ctx, img, &kp0, &nn, 1, d_kps, d_out, scratch, stream, nullptr, nullptr);
+}
+
+cudaError_t launch_extract_dev_count(const latch_context* ctx, const latch_image* img, const latch_keypoint* d_kps,
+                                     int32_t max_n, const int32_t* d_n, uint8_t* d_out, void* scratch,
+                                     cudaStream_t stream) {
+    if (max_n <= 0) return cudaSuccess;
+    const int64_t kp0 = 0, nn = max_n;
+    return launch_chunk<1>(ctx, img, &kp0, &nn, 0, 1, d_kps, d_out, nullptr, nullptr, static_cast<uint8_t*>(scratch),
+                           stream, ctx->d_flags, d_n);
 }
 
 }  // namespace latch

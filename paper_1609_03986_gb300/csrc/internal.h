@@ -60,6 +60,8 @@ struct latch_context {
     latch_triplet h_trip[LATCH_TRIPLETS] = {};
     bool has_trip = false;
     uint32_t h_trip_offsets[2 * LATCH_TRIPLETS] = {};
+    bool weighted = false;               // 8x8 weighted patches (latch_set_patch_weights) instead of 7x7
+    int32_t patch_weights[64] = {};
     uint32_t* d_flags = nullptr;         // device error word
     int32_t item_kps = 16;               // extraction: fewest keypoints per block (latch_autotune)
     // tracing (latch_trace_enable): per batch run, events before extraction, between
@@ -67,7 +69,7 @@ struct latch_context {
     cudaEvent_t* trace_ev = nullptr;
     int32_t trace_cap = 0, trace_n = 0;
     int64_t tensor_min_pairs = int64_t(1) << 22;  // matching: AUTO uses the tensor path from here
-    latch::Scratch scratch[4];           // grow-only scratch regions
+    latch::Scratch scratch[5];           // grow-only scratch regions (4: detection)
     // latch_batch_run_host: two staging sets used alternately, upload stream
     latch::HostStaging staging[2];
     cudaStream_t up_stream = nullptr;
@@ -127,6 +129,16 @@ cudaError_t launch_extract_batch(const latch_context* ctx, const latch_image* im
                                  void* scratch, cudaStream_t stream, uint8_t* exp_out, int32_t* pop_out,
                                  uint32_t* flags = nullptr);
 size_t extract_batch_scratch_bytes(const latch_image* imgs, const int64_t* n, int count);
+// One image whose keypoint count is on the device (*d_n, at most max_n keypoints in
+// d_kps); scratch as extract_scratch_bytes(img, max_n).
+cudaError_t launch_extract_dev_count(const latch_context* ctx, const latch_image* img, const latch_keypoint* d_kps,
+                                     int32_t max_n, const int32_t* d_n, uint8_t* d_out, void* scratch,
+                                     cudaStream_t stream);
+
+// Oriented FAST keypoints (detect.cu): up to max_kps into d_kps, the number found into *d_count.
+cudaError_t launch_detect(const latch_image* img, int32_t threshold, int32_t scale_idx, int32_t max_kps,
+                          latch_keypoint* d_kps, int32_t* d_count, void* scratch, cudaStream_t stream);
+size_t detect_scratch_bytes(const latch_image* img);
 
 cudaError_t launch_match_popc(const latch_context* ctx, const uint8_t* q, int32_t nq, const uint8_t* t, int32_t nt,
                               int32_t k, int32_t r_milli, latch_match* out, void* scratch, cudaStream_t stream);

@@ -31,6 +31,7 @@ import json
 import os
 
 EXTRACT_OPS_PER_DESC = 512 * 2 * 49 * 2
+EXTRACT_WEIGHTED_OPS_PER_DESC = 512 * 2 * 64 * 3
 EXTRACT_DP4A_PER_DESC = 512 * 4 * 49 // 4  # D1 - D2 as four 49-term u8 dot products, 4 multiply-adds per dp4a
 POPC_WORDS_PER_PAIR = 16
 TENSOR_FLOP_PER_PAIR = 2 * 512
@@ -121,6 +122,27 @@ def extraction(ms: float, n_desc: int, workload: str, peaks_path: str):
                       "peak_dp4a_per_s": dp4a_peak,
                       "frac": EXTRACT_DP4A_PER_DESC * n_desc / (ms / 1e3) / dp4a_peak}
     return _finish(r, f"{rk}; clock {pk} (measured-peaks file)")
+
+
+def extraction_weighted(ms: float, n_desc: int, workload: str, peaks_path: str):
+    """Weighted 8x8 extraction: per descriptor 512 triplets x 2 distances x 64 pixels x
+    3 int32 ops (subtract, square, weight-multiply-add) = 196,608 ops."""
+    peaks, pk = _peaks(peaks_path)
+    rates, rk = pipe_rates()
+    clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    r = {"bound": "alu", "kernel": "extract_lanes (weighted)", "unit": "Tops/s (int32)", "units_per_launch": n_desc,
+         "achieved": EXTRACT_WEIGHTED_OPS_PER_DESC * n_desc / (ms / 1e3) / 1e12,
+         "peak": rates["per_sm_per_clock"]["iadd3"] * rates["sm_count"] * clk / 1e12, "traffic": None}
+    return _finish(r, f"{rk}; clock {pk} (measured-peaks file)")
+
+
+def detection(ms: float, pixels: int, workload: str, peaks_path: str):
+    """FAST detection: reads every pixel of the image once (1 byte) from HBM."""
+    peaks, pk = _peaks(peaks_path)
+    r = {"bound": "hbm", "kernel": "detect_cells", "unit": "GB/s", "units_per_launch": pixels,
+         "achieved": pixels / (ms / 1e3) / 1e9, "peak": float(peaks["hbm_gbs"]),
+         "traffic": traffic("detect_cells", "detect.cu", workload)}
+    return _finish(r, f"{pk} HBM copy bandwidth")
 
 
 def tensor_match(ms: float, pairs: float, workload: str, peaks_path: str, sustained: bool):

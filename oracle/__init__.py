@@ -53,6 +53,10 @@ def _load():
         lib.oracle_orientation_bin.argtypes = [P, I64, I, I]
         lib.oracle_detect.restype = I
         lib.oracle_detect.argtypes = [P, I, I, I64, I, I, P, P, P]
+        lib.oracle_pyramid_level.restype = None
+        lib.oracle_pyramid_level.argtypes = [P, I, I, I64, D, P, I64, P, P]
+        lib.oracle_detect_pyramid.restype = I
+        lib.oracle_detect_pyramid.argtypes = [P, I, I, I64, I, P, I, I, P, P, P, P]
         _lib = lib
     return _lib
 
@@ -163,4 +167,33 @@ def detect(image: np.ndarray, width: int, height: int, t: int) -> np.ndarray:
             raise ValueError("oracle_detect: bad arguments")
         if n <= cap:
             return np.stack([xs[:n], ys[:n], bs[:n]], axis=1)
+        cap = n
+
+
+def pyramid_level(image: np.ndarray, width: int, height: int, scale: float) -> np.ndarray:
+    """Level image of scale >= 1, (floor(H / s), floor(W / s)) uint8."""
+    image = _c(image, np.uint8)
+    w, h = int(np.floor(width / scale)), int(np.floor(height / scale))
+    out = np.zeros((max(h, 1), max(w, 1)), np.uint8)
+    lw, lh = ctypes.c_int(), ctypes.c_int()
+    _load().oracle_pyramid_level(image.ctypes.data, width, height, image.shape[1], float(scale), out.ctypes.data,
+                                 out.shape[1], ctypes.byref(lw), ctypes.byref(lh))
+    return out[:lh.value, :lw.value]
+
+
+def detect_pyramid(image: np.ndarray, width: int, height: int, t: int, scales) -> np.ndarray:
+    """Oriented FAST keypoints of every pyramid level, level after level (raster order
+    of the level's image), in base coordinates: (n, 4) int32 x, y, angle bin, level."""
+    image = _c(image, np.uint8)
+    sc = _c(scales, np.float64)
+    lib = _load()
+    cap = 4096
+    while True:
+        arrs = [np.zeros(cap, np.int32) for _ in range(4)]
+        n = lib.oracle_detect_pyramid(image.ctypes.data, width, height, image.shape[1], t, sc.ctypes.data, sc.size,
+                                      cap, *[a.ctypes.data for a in arrs])
+        if n < 0:
+            raise ValueError("oracle_detect_pyramid: bad arguments")
+        if n <= cap:
+            return np.stack([a[:n] for a in arrs], axis=1)
         cap = n

@@ -53,6 +53,14 @@
  *     m10 = sum x I, m01 = sum y I (x right, y down, the frame of the window
  *     rotation above), theta = atan2(m01, m10), angle bin = rha(theta * 16 / pi)
  *     mod 32, in FP64; keypoints are reported in raster order.
+ *
+ * Multi-scale pyramid (Sec. 6: CLATCH extracted at multiple scales).  Reading: the
+ * levels are the scale table's entries s >= 1; level s is the base image sampled at
+ * spacing s, I_s(x, y) = I(rha(s x), rha(s y)) for x < floor(W / s), y < floor(H / s)
+ * (the nearest-pixel rule of the scaled window); keypoints are detected on every
+ * level, a level keypoint (x, y) becomes the base keypoint (rha(s x), rha(s y)) with
+ * the level's orientation bin and the level's scale index; levels follow one another
+ * in table order.
  * Parity pins: every function here is pinned by tests (closed forms, invariants,
  * brute force against full sorting, hand-made images); none is unpinned.
  */
@@ -342,4 +350,66 @@ int oracle_detect(const uint8_t *img, int width, int height, int64_t pitch, int 
         }
     free(score);
     return n;
+}
+
+/* ---------------------------------------------------------------------------
+ * Multi-scale pyramid (Sec. 6).
+ * ------------------------------------------------------------------------- */
+
+/* Level image of scale s >= 1: out[y * out_pitch + x] = I(rha(s x), rha(s y)) for
+ * x < floor(W / s), y < floor(H / s).  Writes the level's size to *lw, *lh. */
+void oracle_pyramid_level(const uint8_t *img, int width, int height, int64_t pitch, double s, uint8_t *out,
+                          int64_t out_pitch, int *lw, int *lh) {
+    const int w = (int)floor((double)width / s), h = (int)floor((double)height / s);
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            const int64_t sx = (int64_t)round(s * (double)x), sy = (int64_t)round(s * (double)y);
+            out[(int64_t)y * out_pitch + x] = img[sy * pitch + sx];
+        }
+    *lw = w;
+    *lh = h;
+}
+
+/*
+ * Oriented FAST keypoints of every pyramid level (scales[0 .. n) each >= 1), level
+ * after level, each level in raster order of its own image, mapped to the base
+ * image: (rha(s x), rha(s y)), the level's bin, scale index = the level.  Writes at
+ * most `cap` keypoints and returns the number found, or -1 on bad arguments.
+ */
+int oracle_detect_pyramid(const uint8_t *img, int width, int height, int64_t pitch, int t, const double *scales,
+                          int n, int cap, int32_t *xs, int32_t *ys, int32_t *bins, int32_t *levels) {
+    if (n < 1 || cap < 0) return -1;
+    int total = 0;
+    for (int l = 0; l < n; ++l) {
+        const double s = scales[l];
+        if (!(s >= 1.0)) return -1;
+        const int w = (int)floor((double)width / s), h = (int)floor((double)height / s);
+        if (w < 1 || h < 1) continue;
+        const int64_t lp = w;
+        uint8_t *lev = (uint8_t *)malloc((size_t)w * (size_t)h);
+        int32_t *lx = (int32_t *)malloc(sizeof(int32_t) * ((size_t)w * (size_t)h / 4 + 1));
+        int32_t *ly = (int32_t *)malloc(sizeof(int32_t) * ((size_t)w * (size_t)h / 4 + 1));
+        int32_t *lb = (int32_t *)malloc(sizeof(int32_t) * ((size_t)w * (size_t)h / 4 + 1));
+        if (!lev || !lx || !ly || !lb) {
+            free(lev), free(lx), free(ly), free(lb);
+            return -1;
+        }
+        int lw = 0, lh = 0;
+        oracle_pyramid_level(img, width, height, pitch, s, lev, lp, &lw, &lh);
+        /* strict suppression keeps at most one pixel of every 2x2 block */
+        const int m = oracle_detect(lev, lw, lh, lp, t, w * h / 4 + 1, lx, ly, lb);
+        if (m < 0) {
+            free(lev), free(lx), free(ly), free(lb);
+            return -1;
+        }
+        for (int i = 0; i < m; ++i, ++total)
+            if (total < cap) {
+                xs[total] = (int32_t)round(s * (double)lx[i]);
+                ys[total] = (int32_t)round(s * (double)ly[i]);
+                bins[total] = lb[i];
+                levels[total] = l;
+            }
+        free(lev), free(lx), free(ly), free(lb);
+    }
+    return total;
 }

@@ -607,7 +607,12 @@ def bench_detect(args, local):
     def det_ext():
         P.latch_detect_extract(ctx.handle, img, w, h, img.stride(0), 20, 0, max_kps, kps, cnt, desc, s)
 
+    def pyr_ext():
+        P.latch_detect_pyramid(ctx.handle, img, w, h, img.stride(0), 20, 3, max_kps, kps, cnt, desc, s)
+
     clocks = _sub_clocks(local)
+    ms_p = _timed(pyr_ext, args.steps, args.warmup, flush)
+    n_p = int(cnt.item())
     ms_d = _timed(det, args.steps, args.warmup, flush)
     ms_de = _timed(det_ext, args.steps, args.warmup, flush)
     clk = clocks.stop()
@@ -620,6 +625,8 @@ def bench_detect(args, local):
         (ms_d, roofline.detection(ms_d, w * h, name, PEAKS))])
     return {"workload": name, "keypoints": n, "detect_ms": ms_d, "detect_extract_ms": ms_de,
             "detect_mpix_per_s": w * h / (ms_d / 1e3) / 1e6, "desc_per_s": n / (ms_de / 1e3),
+            "pyramid": {"levels": "scales 1, 1.5, 2.25", "keypoints": n_p, "detect_extract_ms": ms_p,
+                        "desc_per_s": n_p / (ms_p / 1e3), "entry": "latch_detect_pyramid with descriptors"},
             "entry": "latch_detect; latch_detect_extract", "roofline": rf, "clocks": clk}
 
 

@@ -195,6 +195,23 @@ latch_status latch_detect_extract(latch_context *ctx, const latch_image *img, in
                                   int32_t max_kps, latch_keypoint *d_kps, int32_t *d_count, uint8_t *d_desc,
                                   latch_stream_t stream);
 
+/* Multi-scale keypoints (Sec. 6: CLATCH extracted at multiple scales; FAST alone has
+ * no scale).  Reading: pyramid level l uses the context's scale s_l = scale table
+ * entry l (l < n_levels; each must be >= 1): the level image is the input sampled
+ * at spacing s_l, I_l(x, y) = I(round_half_away(s_l x), round_half_away(s_l y)) for
+ * x < floor(W / s_l), y < floor(H / s_l), the nearest-pixel rule of the scaled
+ * window.  Keypoints are detected on every level as by latch_detect (orientation
+ * from the level image), and a level keypoint (x, y) is written as
+ * (round_half_away(s_l x), round_half_away(s_l y)) with scale_idx = l: its
+ * descriptor then samples the input at the same spacing s_l.  Levels follow one
+ * another (level 0 first), each in the cell order of its own image; the first
+ * max_kps are written and *d_count receives the total.  d_desc: NULL, or max_kps * 64
+ * bytes (16-byte aligned) that receive the descriptors as latch_detect_extract does,
+ * with no host round trip. */
+latch_status latch_detect_pyramid(latch_context *ctx, const latch_image *img, int32_t threshold, int32_t n_levels,
+                                  int32_t max_kps, latch_keypoint *d_kps, int32_t *d_count, uint8_t *d_desc,
+                                  latch_stream_t stream);
+
 /*
  * Brute-force Hamming matching (Sec. 4): for every query descriptor the nearest
  * train descriptor and, for k == 2, the nearest among the others, with the ratio

@@ -123,6 +123,7 @@ EXPORTS = [
     ("hamming_match_noalloc", ctypes.c_int, [_P, _I32, _P, _I32, _I32, _F, _P, _P]),
     ("hamming_match_noalloc_status", ctypes.c_int, []),
     ("latch_set_patch_weights", ctypes.c_int, [_P, _P]),
+    ("latch_detect_pyramid", ctypes.c_int, [_P, ctypes.POINTER(latch_image), _I32, _I32, _I32, _P, _P, _P, _P]),
     ("latch_detect", ctypes.c_int, [_P, ctypes.POINTER(latch_image), _I32, _I32, _I32, _P, _P, _P]),
     ("latch_detect_extract", ctypes.c_int, [_P, ctypes.POINTER(latch_image), _I32, _I32, _I32, _P, _P, _P, _P]),
 ]
@@ -234,6 +235,15 @@ def latch_detect_extract(ctx, image, width: int, height: int, pitch: int, thresh
     """Oriented FAST keypoints and their descriptors, no host round trip."""
     img = latch_image(_ptr(image), width, height, pitch)
     _check(ctx, library().latch_detect_extract(ctx, ctypes.byref(img), threshold, scale_idx, max_kps, _ptr(kps_out),
+                                               _ptr(count_out), _ptr(desc_out), stream))
+
+
+def latch_detect_pyramid(ctx, image, width: int, height: int, pitch: int, threshold: int, n_levels: int,
+                         max_kps: int, kps_out, count_out, desc_out=None, stream: int = 0) -> None:
+    """Oriented FAST keypoints of every pyramid level (the scale table's first n_levels
+    entries), level after level, optionally with their descriptors."""
+    img = latch_image(_ptr(image), width, height, pitch)
+    _check(ctx, library().latch_detect_pyramid(ctx, ctypes.byref(img), threshold, n_levels, max_kps, _ptr(kps_out),
                                                _ptr(count_out), _ptr(desc_out), stream))
 
 

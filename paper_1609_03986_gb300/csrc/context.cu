@@ -388,13 +388,52 @@ latch_status latch_detect(latch_context* ctx, const latch_image* img, int32_t th
     latch_status st = validate_detect(ctx, img, threshold, scale_idx, max_kps, d_kps, d_count);
     if (st != LATCH_OK) return st;
     LATCH_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    const double one = 1.0;
     void* scratch = nullptr;
-    st = scratch_reserve(ctx, 4, detect_scratch_bytes(img), &scratch);
+    st = scratch_reserve(ctx, 4, detect_scratch_bytes(img, &one, 1), &scratch);
     if (st != LATCH_OK) return st;
     return cuda_check(ctx,
-                      launch_detect(img, threshold, scale_idx, max_kps, d_kps, d_count, scratch,
+                      launch_detect(img, &one, &scale_idx, 1, threshold, max_kps, d_kps, d_count, scratch,
                                     static_cast<cudaStream_t>(stream)),
                       "detection launch");
+}
+
+// Detection over the pyramid levels of the first n_levels scales (each >= 1), then
+// optionally the descriptors (level l's keypoints carry scale index l).
+static latch_status detect_levels(latch_context* ctx, const latch_image* img, const double* scales,
+                                  const int32_t* idx, int nlev, int32_t threshold, int32_t max_kps,
+                                  latch_keypoint* d_kps, int32_t* d_count, uint8_t* d_desc, cudaStream_t s) {
+    void* dscratch = nullptr;
+    void* escratch = nullptr;
+    latch_status st = scratch_reserve(ctx, 4, detect_scratch_bytes(img, scales, nlev), &dscratch);
+    if (st == LATCH_OK && d_desc) st = scratch_reserve(ctx, 0, extract_scratch_bytes(img, max_kps), &escratch);
+    if (st != LATCH_OK) return st;
+    st = cuda_check(ctx, launch_detect(img, scales, idx, nlev, threshold, max_kps, d_kps, d_count, dscratch, s),
+                    "detection launch");
+    if (st != LATCH_OK || !d_desc) return st;
+    return cuda_check(ctx, launch_extract_dev_count(ctx, img, d_kps, max_kps, d_count, d_desc, escratch, s),
+                      "extraction launch");
+}
+
+latch_status latch_detect_pyramid(latch_context* ctx, const latch_image* img, int32_t threshold, int32_t n_levels,
+                                  int32_t max_kps, latch_keypoint* d_kps, int32_t* d_count, uint8_t* d_desc,
+                                  latch_stream_t stream) {
+    latch_status st = validate_detect(ctx, img, threshold, 0, max_kps, d_kps, d_count);
+    if (st != LATCH_OK) return st;
+    if (n_levels < 1 || n_levels > ctx->nscales)
+        return fail(ctx, LATCH_EINVAL, "n_levels = %d not in [1, %d] (the scale table)", n_levels, ctx->nscales);
+    int32_t idx[LATCH_MAX_SCALES];
+    for (int l = 0; l < n_levels; ++l) {
+        if (!(ctx->scales[l] >= 1.0))
+            return fail(ctx, LATCH_EINVAL, "pyramid level %d has scale %g < 1", l, ctx->scales[l]);
+        idx[l] = l;
+    }
+    if (d_desc && max_kps > 0 && (reinterpret_cast<uintptr_t>(d_desc) & 15))
+        return fail(ctx, LATCH_EINVAL, "misaligned descriptor output");
+    if (d_desc && !ctx->has_trip) return fail(ctx, LATCH_EINVAL, "no triplet table: call latch_set_triplets");
+    LATCH_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    return detect_levels(ctx, img, ctx->scales, idx, n_levels, threshold, max_kps, d_kps, d_count,
+                         max_kps > 0 ? d_desc : nullptr, static_cast<cudaStream_t>(stream));
 }
 
 latch_status latch_detect_extract(latch_context* ctx, const latch_image* img, int32_t threshold, int32_t scale_idx,
@@ -406,17 +445,9 @@ latch_status latch_detect_extract(latch_context* ctx, const latch_image* img, in
         return fail(ctx, LATCH_EINVAL, "NULL or misaligned descriptor output");
     if (!ctx->has_trip) return fail(ctx, LATCH_EINVAL, "no triplet table: call latch_set_triplets");
     LATCH_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    void* dscratch = nullptr;
-    void* escratch = nullptr;
-    st = scratch_reserve(ctx, 4, detect_scratch_bytes(img), &dscratch);
-    if (st == LATCH_OK) st = scratch_reserve(ctx, 0, extract_scratch_bytes(img, max_kps), &escratch);
-    if (st != LATCH_OK) return st;
-    st = cuda_check(ctx, launch_detect(img, threshold, scale_idx, max_kps, d_kps, d_count, dscratch, s),
-                    "detection launch");
-    if (st != LATCH_OK) return st;
-    return cuda_check(ctx, launch_extract_dev_count(ctx, img, d_kps, max_kps, d_count, d_desc, escratch, s),
-                      "extraction launch");
+    const double one = 1.0;
+    return detect_levels(ctx, img, &one, &scale_idx, 1, threshold, max_kps, d_kps, d_count,
+                         max_kps > 0 ? d_desc : nullptr, static_cast<cudaStream_t>(stream));
 }
 
 latch_status hamming_match(latch_context* ctx, const uint8_t* d_query, int32_t nq, const uint8_t* d_train,

@@ -8,7 +8,14 @@
 // the orientation is the intensity centroid of the radius-15 disc quantised to the
 // 32 angle bins (round half away from zero of theta * 16 / pi, FP64).
 //
-// Three chained kernels per image:
+// Pyramid (Sec. 6, CLATCH at multiple scales; reading: level s is the base image
+// sampled at spacing s, I_s(x, y) = I(rha(s x), rha(s y)), x < floor(W / s), the
+// nearest-pixel rule of the scaled window): pyramid_level_kernel writes the levels
+// with s != 1, and one launch of each kernel below covers every level; a level
+// keypoint (x, y) is written as the base keypoint (rha(s x), rha(s y)) with the
+// level's scale index, levels one after another.
+//
+// Three chained kernels per image (all levels):
 //   detect_cells_kernel   one block per 32x32 cell: the cell plus a 16-pixel halo
 //                         (64 x 64 bytes) is staged in shared memory; scores of the
 //                         cell and a 1-pixel apron; suppression; the cell's survivors
@@ -18,6 +25,8 @@
 //   detect_expand_kernel  one warp per cell: keypoint records at the cell's offset
 //                         (cells row by row, raster order inside a cell), the first
 //                         max_kps of them.
+#include <algorithm>
+#include <cmath>
 #include <cstdint>
 
 #include "internal.h"
@@ -82,15 +91,31 @@ __device__ __forceinline__ int fast_score(const uint8_t (*tile)[kTileD], int tx,
     return s >= t ? s : 0;
 }
 
-struct DetectParams {
-    const uint8_t* img;
+struct DetectLevel {
+    const uint8_t* img;  // the level image (the base image for scale 1)
     int64_t pitch;
     int32_t width, height;
     int32_t gx, gy;      // cells per row / column
+    int32_t cell0;       // the level's first cell in the launch's cell numbering
+    int32_t scale_idx;   // written into the level's keypoints
+    double scale;        // base coordinate = rha(scale * level coordinate)
+};
+
+struct DetectParams {
+    DetectLevel lv[kMaxDetectLevels];
+    int32_t nlev;
+    int32_t ncells;      // cells of all levels
     int32_t t;           // FAST threshold
-    int32_t scale_idx;   // written into every keypoint
     int32_t max_kps;
 };
+
+// Level of global cell `cell` (largest l with lv[l].cell0 <= cell).
+__device__ __forceinline__ int level_of_cell(const DetectParams& prm, int cell) {
+    int l = 0;
+    for (int i = 1; i < prm.nlev; ++i)
+        if (prm.lv[i].cell0 <= cell) l = i;
+    return l;
+}
 
 __global__ void __launch_bounds__(kDetThreads) detect_cells_kernel(const DetectParams prm, int32_t* __restrict__ counts,
                                                                    uint16_t* __restrict__ slots) {
@@ -101,9 +126,11 @@ __global__ void __launch_bounds__(kDetThreads) detect_cells_kernel(const DetectP
     griddep_wait();
     griddep_launch_dependents();
     const int cell = blockIdx.x;
-    const int cx = cell % prm.gx, cy = cell / prm.gx;
+    const DetectLevel& L = prm.lv[level_of_cell(prm, cell)];
+    const int lc = cell - L.cell0;
+    const int cx = lc % L.gx, cy = lc / L.gx;
     const int x0 = cx * kCellD, y0 = cy * kCellD;
-    const int W = prm.width, H = prm.height;
+    const int W = L.width, H = L.height;
     // the detection region [16, W-17] x [16, H-17] meets this cell?
     const int rx0 = max(x0, kHaloD), rx1 = min(x0 + kCellD - 1, W - 1 - kHaloD);
     const int ry0 = max(y0, kHaloD), ry1 = min(y0 + kCellD - 1, H - 1 - kHaloD);
@@ -117,7 +144,7 @@ __global__ void __launch_bounds__(kDetThreads) detect_cells_kernel(const DetectP
         const int gy = y0 - kHaloD + r, gx = x0 - kHaloD + 16 * q;
         uint4 v = make_uint4(0, 0, 0, 0);
         if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
-            const uint8_t* src = prm.img + static_cast<int64_t>(gy) * prm.pitch + gx;
+            const uint8_t* src = L.img + static_cast<int64_t>(gy) * L.pitch + gx;
             if (gx + 16 <= W) {
                 v = *reinterpret_cast<const uint4*>(src);
             } else {  // the image's last bytes of the row: no read past the width
@@ -256,55 +283,167 @@ __global__ void __launch_bounds__(256) detect_expand_kernel(const DetectParams p
                                                             latch_keypoint* __restrict__ out) {
     griddep_wait();
     griddep_launch_dependents();
-    const int ncells = prm.gx * prm.gy;
+    const int ncells = prm.ncells;
     const int cell = blockIdx.x * 8 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (cell >= ncells) return;
+    const DetectLevel& L = prm.lv[level_of_cell(prm, cell)];
     const int o = offsets[cell];
     const int n = (cell + 1 < ncells ? offsets[cell + 1] : *d_count) - o;
-    const int x0 = (cell % prm.gx) * kCellD, y0 = (cell / prm.gx) * kCellD;
+    const int lc = cell - L.cell0;
+    const int x0 = (lc % L.gx) * kCellD, y0 = (lc / L.gx) * kCellD;
     for (int i = lane; i < n && o + i < prm.max_kps; i += 32) {
         const uint32_t v = slots[static_cast<int64_t>(cell) * kMaxPerCell + i];
+        const int32_t lx = x0 + static_cast<int32_t>(v & 31u), ly = y0 + static_cast<int32_t>((v >> 5) & 31u);
         latch_keypoint k;
-        k.x = x0 + static_cast<int32_t>(v & 31u);
-        k.y = y0 + static_cast<int32_t>((v >> 5) & 31u);
+        if (L.scale == 1.0) {
+            k.x = lx;
+            k.y = ly;
+        } else {  // FP64 product, rounded half away from zero (non-negative here)
+            k.x = static_cast<int32_t>(round(L.scale * static_cast<double>(lx)));
+            k.y = static_cast<int32_t>(round(L.scale * static_cast<double>(ly)));
+        }
         k.angle_bin = static_cast<uint8_t>(v >> 10);
-        k.scale_idx = static_cast<uint8_t>(prm.scale_idx);
+        k.scale_idx = static_cast<uint8_t>(L.scale_idx);
         k.reserved = 0;
         out[o + i] = k;
     }
 }
 
-}  // namespace
+// Level images of the levels with scale != 1: one thread per 16 output bytes of a
+// row, rows of all levels in one grid (row r of the launch is level `lev`'s row
+// r - row0[lev]).  out(x, y) = base(rha(s x), rha(s y)).
+struct ResampleParams {
+    const uint8_t* base;
+    int64_t base_pitch;
+    uint8_t* out[kMaxDetectLevels];
+    int64_t pitch[kMaxDetectLevels];
+    int32_t width[kMaxDetectLevels];
+    int32_t row0[kMaxDetectLevels + 1];  // first launch row of each level; row0[n] = rows of all levels
+    double scale[kMaxDetectLevels];
+    int32_t n;
+    int32_t chunks;  // 16-byte chunks per launch row: those of the widest level
+};
 
-size_t detect_scratch_bytes(const latch_image* img) {
-    const int64_t gx = (img->width + kCellD - 1) / kCellD, gy = (img->height + kCellD - 1) / kCellD;
-    const int64_t ncells = gx * gy;
-    return (static_cast<size_t>(ncells) * 4 + 255) / 256 * 256 +
-           static_cast<size_t>(ncells) * kMaxPerCell * sizeof(uint16_t) + 256;
+__global__ void __launch_bounds__(256) pyramid_level_kernel(const ResampleParams prm) {
+    griddep_wait();
+    griddep_launch_dependents();
+    const int64_t gid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t chunks_per_row = prm.chunks;
+    const int64_t row = gid / chunks_per_row;
+    if (row >= prm.row0[prm.n]) return;
+    int l = 0;
+    while (l + 1 < prm.n && prm.row0[l + 1] <= row) ++l;
+    const int y = static_cast<int>(row - prm.row0[l]);
+    const int x0 = static_cast<int>(gid % chunks_per_row) * 16;
+    const int w = prm.width[l];
+    if (x0 >= w) return;
+    const double s = prm.scale[l];
+    const uint8_t* src = prm.base + static_cast<int64_t>(round(s * static_cast<double>(y))) * prm.base_pitch;
+    union {
+        uint4 v;
+        uint8_t b[16];
+    } u;
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+        u.b[i] = x0 + i < w ? src[static_cast<int64_t>(round(s * static_cast<double>(x0 + i)))] : 0;
+    *reinterpret_cast<uint4*>(prm.out[l] + static_cast<int64_t>(y) * prm.pitch[l] + x0) = u.v;
 }
 
-cudaError_t launch_detect(const latch_image* img, int32_t threshold, int32_t scale_idx, int32_t max_kps,
-                          latch_keypoint* d_kps, int32_t* d_count, void* scratch, cudaStream_t stream) {
+}  // namespace
+
+// Size of pyramid level s of a W x H image (the same expression as the reading).
+static void level_size(int32_t w, int32_t h, double s, int32_t* lw, int32_t* lh) {
+    *lw = static_cast<int32_t>(std::floor(static_cast<double>(w) / s));
+    *lh = static_cast<int32_t>(std::floor(static_cast<double>(h) / s));
+}
+
+static int64_t level_pitch(int32_t lw) { return (static_cast<int64_t>(lw) + 15) / 16 * 16; }
+
+static int64_t cells_of(int32_t w, int32_t h) {
+    return static_cast<int64_t>((w + kCellD - 1) / kCellD) * ((h + kCellD - 1) / kCellD);
+}
+
+size_t detect_scratch_bytes(const latch_image* img, const double* scales, int nlev) {
+    int64_t ncells = 0;
+    size_t level_bytes = 0;
+    for (int l = 0; l < nlev; ++l) {
+        int32_t lw, lh;
+        level_size(img->width, img->height, scales[l], &lw, &lh);
+        if (lw < 1 || lh < 1) continue;
+        ncells += cells_of(lw, lh);
+        if (scales[l] != 1.0) level_bytes += (static_cast<size_t>(lh) * level_pitch(lw) + 255) / 256 * 256;
+    }
+    return (static_cast<size_t>(ncells) * 4 + 255) / 256 * 256 +
+           (static_cast<size_t>(ncells) * kMaxPerCell * sizeof(uint16_t) + 255) / 256 * 256 + level_bytes + 256;
+}
+
+cudaError_t launch_detect(const latch_image* img, const double* scales, const int32_t* scale_idx, int nlev,
+                          int32_t threshold, int32_t max_kps, latch_keypoint* d_kps, int32_t* d_count, void* scratch,
+                          cudaStream_t stream) {
     DetectParams prm;
-    prm.img = img->data;
-    prm.pitch = img->pitch;
-    prm.width = img->width;
-    prm.height = img->height;
-    prm.gx = (img->width + kCellD - 1) / kCellD;
-    prm.gy = (img->height + kCellD - 1) / kCellD;
+    ResampleParams rs;
+    rs.base = img->data;
+    rs.base_pitch = img->pitch;
+    rs.n = 0;
+    rs.row0[0] = 0;
+    rs.chunks = 1;
+    prm.nlev = 0;
     prm.t = threshold;
-    prm.scale_idx = scale_idx;
     prm.max_kps = max_kps;
-    const int ncells = prm.gx * prm.gy;
-    int32_t* counts = static_cast<int32_t*>(scratch);
-    uint16_t* slots = reinterpret_cast<uint16_t*>(static_cast<uint8_t*>(scratch) +
-                                                  (static_cast<size_t>(ncells) * 4 + 255) / 256 * 256);
-    cudaError_t e = launch_chained(detect_cells_kernel, dim3(ncells), dim3(kDetThreads), 0, stream, prm, counts, slots);
-    if (e == cudaSuccess) e = launch_chained(detect_scan_kernel, dim3(1), dim3(1024), 0, stream, counts, ncells, d_count);
+    int64_t ncells = 0;
+    for (int l = 0; l < nlev; ++l) {
+        int32_t lw, lh;
+        level_size(img->width, img->height, scales[l], &lw, &lh);
+        if (lw < 1 || lh < 1) continue;
+        DetectLevel& L = prm.lv[prm.nlev++];
+        L.width = lw;
+        L.height = lh;
+        L.gx = (lw + kCellD - 1) / kCellD;
+        L.gy = (lh + kCellD - 1) / kCellD;
+        L.cell0 = static_cast<int32_t>(ncells);
+        L.scale_idx = scale_idx[l];
+        L.scale = scales[l];
+        L.img = img->data;
+        L.pitch = img->pitch;
+        ncells += cells_of(lw, lh);
+    }
+    prm.ncells = static_cast<int32_t>(ncells);
+    uint8_t* base = static_cast<uint8_t*>(scratch);
+    int32_t* counts = reinterpret_cast<int32_t*>(base);
+    size_t off = (static_cast<size_t>(ncells) * 4 + 255) / 256 * 256;
+    uint16_t* slots = reinterpret_cast<uint16_t*>(base + off);
+    off += (static_cast<size_t>(ncells) * kMaxPerCell * sizeof(uint16_t) + 255) / 256 * 256;
+    for (int l = 0; l < prm.nlev; ++l) {
+        DetectLevel& L = prm.lv[l];
+        if (L.scale == 1.0) continue;
+        const int k = rs.n++;
+        L.img = base + off;
+        L.pitch = level_pitch(L.width);
+        rs.out[k] = base + off;
+        rs.pitch[k] = L.pitch;
+        rs.width[k] = L.width;
+        rs.scale[k] = L.scale;
+        rs.row0[k + 1] = rs.row0[k] + L.height;
+        rs.chunks = std::max<int32_t>(rs.chunks, (L.width + 15) / 16);
+        off += (static_cast<size_t>(L.height) * L.pitch + 255) / 256 * 256;
+    }
+    cudaError_t e = cudaSuccess;
+    if (rs.n > 0) {
+        const int64_t threads = static_cast<int64_t>(rs.row0[rs.n]) * rs.chunks;
+        e = launch_chained(pyramid_level_kernel, dim3(static_cast<unsigned>((threads + 255) / 256)), dim3(256), 0,
+                           stream, rs);
+    }
+    if (e != cudaSuccess) return e;
+    if (ncells == 0) return cudaMemsetAsync(d_count, 0, sizeof(int32_t), stream);
+    e = launch_chained(detect_cells_kernel, dim3(static_cast<unsigned>(ncells)), dim3(kDetThreads), 0, stream, prm,
+                       counts, slots);
     if (e == cudaSuccess)
-        e = launch_chained(detect_expand_kernel, dim3((ncells + 7) / 8), dim3(256), 0, stream, prm,
-                           static_cast<const int32_t*>(counts), static_cast<const int32_t*>(d_count),
+        e = launch_chained(detect_scan_kernel, dim3(1), dim3(1024), 0, stream, counts, static_cast<int32_t>(ncells),
+                           d_count);
+    if (e == cudaSuccess)
+        e = launch_chained(detect_expand_kernel, dim3(static_cast<unsigned>((ncells + 7) / 8)), dim3(256), 0, stream,
+                           prm, static_cast<const int32_t*>(counts), static_cast<const int32_t*>(d_count),
                            static_cast<const uint16_t*>(slots), d_kps);
     return e;
 }

@@ -135,10 +135,14 @@ cudaError_t launch_extract_dev_count(const latch_context* ctx, const latch_image
                                      int32_t max_n, const int32_t* d_n, uint8_t* d_out, void* scratch,
                                      cudaStream_t stream);
 
-// Oriented FAST keypoints (detect.cu): up to max_kps into d_kps, the number found into *d_count.
-cudaError_t launch_detect(const latch_image* img, int32_t threshold, int32_t scale_idx, int32_t max_kps,
-                          latch_keypoint* d_kps, int32_t* d_count, void* scratch, cudaStream_t stream);
-size_t detect_scratch_bytes(const latch_image* img);
+// Oriented FAST keypoints (detect.cu) of the pyramid levels scales[0 .. nlev) (each >= 1;
+// scale 1 is the image itself), level l's keypoints given scale index scale_idx[l]:
+// up to max_kps into d_kps, the number found into *d_count.
+constexpr int kMaxDetectLevels = LATCH_MAX_SCALES;
+cudaError_t launch_detect(const latch_image* img, const double* scales, const int32_t* scale_idx, int nlev,
+                          int32_t threshold, int32_t max_kps, latch_keypoint* d_kps, int32_t* d_count, void* scratch,
+                          cudaStream_t stream);
+size_t detect_scratch_bytes(const latch_image* img, const double* scales, int nlev);
 
 cudaError_t launch_match_popc(const latch_context* ctx, const uint8_t* q, int32_t nq, const uint8_t* t, int32_t nt,
                               int32_t k, int32_t r_milli, latch_match* out, void* scratch, cudaStream_t stream);

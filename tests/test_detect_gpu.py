@@ -121,3 +121,61 @@ def test_detect_rejects_bad_arguments(gpu_ctx):
         assert e.value.status == 1
     with pytest.raises(P.LatchError):
         P.latch_detect(gpu_ctx.handle, img, 64, 64, 64, 20, 0, 10, kps, 0, 0)
+
+
+def _pyramid_order(kp, width, scales):
+    """Keypoints (x, y, bin, level) in the library's pyramid order: level after level,
+    each level in the cell order of its own image (level coordinates recovered as
+    round(x / s): |rha(s x) - s x| <= 1/2 < s/2)."""
+    out = []
+    for l, s in enumerate(scales):
+        k = kp[kp[:, 3] == l].astype(np.int64)
+        lx, ly = np.rint(k[:, 0] / s).astype(np.int64), np.rint(k[:, 1] / s).astype(np.int64)
+        gx = (int(np.floor(width / s)) + 31) // 32
+        key = ((ly // 32) * gx + lx // 32) * 1024 + (ly % 32) * 32 + lx % 32
+        out.append(k[np.argsort(key, kind="stable")])
+    return np.concatenate(out).astype(np.int32)
+
+
+@pytest.mark.parametrize("w, h, t", [(640, 480, 20), (1920, 1080, 25), (101, 77, 10)])
+def test_pyramid_equals_oracle(gpu_ctx, triplets, w, h, t):
+    """Every level of the default scale table {1, 1.5, 2.25}: the same keypoints
+    (base coordinates, bins, level as scale index) in the documented order, and the
+    descriptors of all of them at their level's scale."""
+    img = synth.image(synth.seed(85, w + h, synth.KIND_IMAGE), w, h, n_ellipses=80)
+    want = _pyramid_order(oracle.detect_pyramid(img, w, h, t, synth.SCALES), w, synth.SCALES)
+    cap = len(want) + 50
+    kps = torch.empty((cap, 12), dtype=torch.uint8, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    desc = torch.empty((cap, 64), dtype=torch.uint8, device="cuda")
+    d_img = to_dev(img)
+    P.latch_detect_pyramid(gpu_ctx.handle, d_img, w, h, d_img.stride(0), t, 3, cap, kps, cnt, desc,
+                           int(torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    n = int(cnt.item())
+    assert n == len(want)
+    got = P.unpack_keypoints(kps[:n].cpu().numpy())
+    assert np.array_equal(got[:, [0, 1, 3]], want[:, [0, 1, 3]])
+    for l, s in enumerate(synth.SCALES):  # bins: exact but for rounding ties at a half-integer
+        lev = oracle.pyramid_level(img, w, h, s)
+        sel = np.nonzero((want[:, 3] == l) & (got[:, 2] != want[:, 2]))[0]
+        assert all(_near_boundary(lev, int(round(want[i, 0] / s)), int(round(want[i, 1] / s))) for i in sel)
+    assert np.array_equal(desc[:n].cpu().numpy(), oracle.extract(img, w, h, want, triplets, synth.SCALES))
+    gpu_ctx.check()
+
+
+def test_pyramid_level_count_and_scales(gpu_ctx):
+    img = torch.zeros((64, 64), dtype=torch.uint8, device="cuda")
+    kps = torch.zeros((10, 12), dtype=torch.uint8, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for nl in (0, 4):
+        with pytest.raises(P.LatchError) as e:
+            P.latch_detect_pyramid(gpu_ctx.handle, img, 64, 64, 64, 20, nl, 10, kps, cnt)
+        assert e.value.status == 1
+    ctx = P.Context(0, scales=(1.0, 0.5))
+    try:
+        P.latch_detect_pyramid(ctx.handle, img, 64, 64, 64, 20, 1, 10, kps, cnt)
+        with pytest.raises(P.LatchError):
+            P.latch_detect_pyramid(ctx.handle, img, 64, 64, 64, 20, 2, 10, kps, cnt)
+    finally:
+        ctx.close()

@@ -55,6 +55,10 @@ def _load():
         lib.oracle_detect.argtypes = [P, I, I, I64, I, I, P, P, P]
         lib.oracle_pyramid_level.restype = None
         lib.oracle_pyramid_level.argtypes = [P, I, I, I64, D, P, I64, P, P]
+        lib.oracle_dense_extract.restype = I
+        lib.oracle_dense_extract.argtypes = [P, I, I, I64, P, P]
+        lib.oracle_dense_match.restype = I
+        lib.oracle_dense_match.argtypes = [P, P, I, I, I, I, F, P, P, P, P, P]
         lib.oracle_detect_pyramid.restype = I
         lib.oracle_detect_pyramid.argtypes = [P, I, I, I64, I, P, I, I, P, P, P, P]
         _lib = lib
@@ -197,3 +201,34 @@ def detect_pyramid(image: np.ndarray, width: int, height: int, t: int, scales) -
         if n <= cap:
             return np.stack([a[:n] for a in arrs], axis=1)
         cap = n
+
+
+def dense_extract(image: np.ndarray, width: int, height: int, triplets: np.ndarray) -> np.ndarray:
+    """Descriptor of every pixel (angle bin 0, scale 1), raster order: (H * W, 64) uint8."""
+    image = _c(image, np.uint8)
+    trip = _c(triplets, np.uint8).reshape(-1)
+    assert trip.size == 512 * 6
+    out = np.zeros((height * width, 64), dtype=np.uint8)
+    rc = _load().oracle_dense_extract(image.ctypes.data, width, height, image.shape[1], trip.ctypes.data,
+                                      out.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle_dense_extract: invalid triplet")
+    return out
+
+
+def dense_match(desc_a: np.ndarray, desc_b: np.ndarray, width: int, height: int, radius: int, k: int = 2,
+                ratio: float = 0.8):
+    """Windowed matching of two dense descriptor fields (raster order, width x height
+    pixels each).  Returns dict of arrays idx1, idx2 (raster indices in B), dist1,
+    dist2, accepted, one entry per pixel of A."""
+    a = _c(desc_a, np.uint8).reshape(-1, 64)
+    b = _c(desc_b, np.uint8).reshape(-1, 64)
+    n = width * height
+    assert a.shape[0] == n and b.shape[0] == n
+    idx1, idx2, d1, d2 = (np.zeros(n, np.int32) for _ in range(4))
+    acc = np.zeros(n, np.uint8)
+    rc = _load().oracle_dense_match(a.ctypes.data, b.ctypes.data, width, height, radius, k, ratio, idx1.ctypes.data,
+                                    idx2.ctypes.data, d1.ctypes.data, d2.ctypes.data, acc.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle_dense_match: bad arguments")
+    return {"idx1": idx1, "idx2": idx2, "dist1": d1, "dist2": d2, "accepted": acc}

@@ -61,6 +61,11 @@
  * level, a level keypoint (x, y) becomes the base keypoint (rha(s x), rha(s y)) with
  * the level's orientation bin and the level's scale index; levels follow one another
  * in table order.
+ * Dense per-pixel LATCH (Sec. 6: dense pixel matching as an alternative to
+ * PatchMatch).  Reading: every pixel is a keypoint at angle bin 0 and scale 1,
+ * descriptors in raster order; pixel p of image A is matched against the pixels of
+ * image B within a Chebyshev radius R of p (inside B), in raster order of B, by the
+ * top-two and ratio rule above (train index = raster index in B).
  * Parity pins: every function here is pinned by tests (closed forms, invariants,
  * brute force against full sorting, hand-made images); none is unpinned.
  */
@@ -412,4 +417,89 @@ int oracle_detect_pyramid(const uint8_t *img, int width, int height, int64_t pit
         free(lev), free(lx), free(ly), free(lb);
     }
     return total;
+}
+
+/* ---------------------------------------------------------------------------
+ * Dense per-pixel LATCH and matching (Sec. 6: CLATCH for dense pixel matching,
+ * as an alternative to PatchMatch).  Readings: every pixel (x, y) of the image is
+ * a keypoint at angle bin 0 and scale 1, so its window pixel (u, v) is image pixel
+ * (x + u - 24, y + v - 24) (0 outside the image); descriptors are stored in raster
+ * order, row y * width + x.  Pixel p of image A is matched against the pixels q of
+ * image B (same size) with |q.x - p.x| <= R and |q.y - p.y| <= R that lie inside
+ * B, taken in raster order of B, with the top-two rule and ratio test of
+ * oracle_match (train index = raster index y * width + x of q in B).
+ * ------------------------------------------------------------------------- */
+
+/* Descriptors of every pixel: out receives width * height * 64 bytes.  Returns 0, or
+ * -1 on an invalid triplet. */
+int oracle_dense_extract(const uint8_t *img, int width, int height, int64_t pitch, const uint8_t *triplets,
+                         uint8_t *out) {
+    int32_t dx[WIN * WIN], dy[WIN * WIN], win[WIN * WIN];
+    for (int t = 0; t < 6 * NBITS; ++t)
+        if (triplets[t] < PATCH_R || triplets[t] > WIN - 1 - PATCH_R) return -1;
+    oracle_offsets(1.0, 0, dx, dy);
+    for (int y = 0; y < height; ++y)
+        for (int x = 0; x < width; ++x) {
+            sample_window(img, width, height, pitch, x, y, dx, dy, win);
+            uint8_t *d = out + ((int64_t)y * width + x) * (NBITS / 8);
+            memset(d, 0, NBITS / 8);
+            for (int t = 0; t < NBITS; ++t) {
+                const uint8_t *tr = triplets + 6 * t;
+                int64_t d1 = patch_ssd(win, tr[0], tr[1], tr[2], tr[3]); /* ||P_A - P_1||^2 */
+                int64_t d2 = patch_ssd(win, tr[0], tr[1], tr[4], tr[5]); /* ||P_A - P_2||^2 */
+                if (d1 > d2) d[t >> 3] |= (uint8_t)(1u << (t & 7));
+            }
+        }
+    return 0;
+}
+
+/* Windowed matching of two dense descriptor fields of width x height pixels: for
+ * every pixel of A, the candidates of B within `radius` (Chebyshev) in raster order,
+ * every distance, the smallest (lowest raster index on ties), the smallest over the
+ * other candidates, then the ratio rule of oracle_match.  Outputs per pixel of A as
+ * oracle_match.  Returns 0, or -1 on bad arguments. */
+int oracle_dense_match(const uint8_t *da, const uint8_t *db, int width, int height, int radius, int k, float ratio,
+                       int32_t *idx1, int32_t *idx2, int32_t *d1, int32_t *d2, uint8_t *accepted) {
+    if (k != 1 && k != 2) return -1;
+    if (!(ratio >= 0.0f && ratio <= 1.0f)) return -1;
+    if (radius < 0 || width < 0 || height < 0) return -1;
+    const int64_t r = (int64_t)round((double)ratio * 1000.0);
+    const int64_t side = 2 * (int64_t)radius + 1;
+    int32_t *cand = (int32_t *)malloc(sizeof(int32_t) * (size_t)(side * side));
+    int32_t *dist = (int32_t *)malloc(sizeof(int32_t) * (size_t)(side * side));
+    if (!cand || !dist) {
+        free(cand), free(dist);
+        return -1;
+    }
+    for (int y = 0; y < height; ++y)
+        for (int x = 0; x < width; ++x) {
+            const int64_t p = (int64_t)y * width + x;
+            int nc = 0;
+            for (int qy = y - radius; qy <= y + radius; ++qy)
+                for (int qx = x - radius; qx <= x + radius; ++qx) {
+                    if (qx < 0 || qx >= width || qy < 0 || qy >= height) continue;
+                    cand[nc] = qy * width + qx;
+                    dist[nc] = oracle_hamming(da + p * 64, db + (int64_t)cand[nc] * 64, 64);
+                    ++nc;
+                }
+            int b1 = -1, b2 = -1;
+            for (int j = 0; j < nc; ++j)
+                if (b1 < 0 || dist[j] < dist[b1]) b1 = j;
+            if (k == 2)
+                for (int j = 0; j < nc; ++j)
+                    if (j != b1 && (b2 < 0 || dist[j] < dist[b2])) b2 = j;
+            idx1[p] = b1 >= 0 ? cand[b1] : -1;
+            idx2[p] = b2 >= 0 ? cand[b2] : -1;
+            d1[p] = b1 >= 0 ? dist[b1] : 65535;
+            d2[p] = b2 >= 0 ? dist[b2] : 65535;
+            if (b1 < 0)
+                accepted[p] = 0;
+            else if (k == 1)
+                accepted[p] = 1;
+            else
+                accepted[p] = (uint8_t)(1000 * (int64_t)d1[p] < r * (int64_t)d2[p]);
+        }
+    free(cand);
+    free(dist);
+    return 0;
 }

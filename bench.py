@@ -53,7 +53,8 @@ def _args():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="latch", choices=["latch", "reference"])
     p.add_argument("--workload", default="all",
-                   choices=["all", "sfm_batch", "pair", "plain_pair", "gallery", "detect", "weighted", "serve"])
+                   choices=["all", "sfm_batch", "pair", "plain_pair", "gallery", "detect", "weighted", "dense",
+                            "serve"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--rate", type=float, default=200.0, help="serve: Poisson arrivals per second")
     p.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
@@ -292,7 +293,7 @@ def _sfm_config(wl):
             "entry": "latch_batch_run (one sort, one extraction, one tensor-core matching launch) replayed "
                      "from a CUDA graph",
             "l2": "inputs (768 MB of images) larger than L2; a 256 MB L2 flush between timed steps as well",
-            "match_path": "tensor (tcgen05 kind::f8f6f4, E4M3 0/1)"}
+            "match_path": "tensor (tcgen05 kind::mxf4, E2M1 0/1, block scales 2^0)"}
 
 
 def bench_sfm_batch(args, local, ws):
@@ -581,6 +582,55 @@ def bench_gallery(args, local):
     return res
 
 
+def bench_dense(args, local):
+    """Dense per-pixel LATCH (Sec. 6): the descriptor of every pixel of two 640x480
+    images (the second the first shifted by (3, -2)), then every pixel of the first
+    matched against the second within radius 8 (up to 289 candidates each)."""
+    import torch
+    import paper_1609_03986_gb300 as P
+    from paper_1609_03986_gb300 import roofline, synth
+    dev = torch.device("cuda", local)
+    w, h, r = 640, 480, 8
+    name = "dense_640x480_r8"
+    base = synth.image(synth.seed(6, 0, synth.KIND_IMAGE), w + 16, h + 16)
+    imgs = [torch.from_numpy(np.ascontiguousarray(base[8:8 + h, 8:8 + w])).to(dev),
+            torch.from_numpy(np.ascontiguousarray(base[10:10 + h, 5:5 + w])).to(dev)]
+    ctx = P.Context(local, triplets=synth.triplets())
+    da = torch.empty((w * h, 64), dtype=torch.uint8, device=dev)
+    db = torch.empty((w * h, 64), dtype=torch.uint8, device=dev)
+    out = torch.empty((w * h, 16), dtype=torch.uint8, device=dev)
+    s = int(torch.cuda.current_stream().cuda_stream)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def ext():
+        P.latch_dense_extract(ctx.handle, imgs[0], w, h, w, da, s)
+        P.latch_dense_extract(ctx.handle, imgs[1], w, h, w, db, s)
+
+    def mat():
+        P.latch_dense_match(ctx.handle, da, db, w, h, r, 2, 0.8, out, s)
+
+    clocks = _sub_clocks(local)
+    ms_ext = _timed(ext, args.steps, args.warmup, flush)
+    ms_mat = _timed(mat, args.steps, args.warmup, flush)
+    clk = clocks.stop()
+    ctx.check()
+    got = P.matches_from_bytes(out.cpu().numpy())
+    yy, xx = np.mgrid[0:h, 0:w]
+    inner = (yy >= 26) & (yy < h - 26) & (xx >= 26) & (xx < w - 26)
+    shift_found = bool((got["dist1"].reshape(h, w)[inner] == 0).all())
+    side_x = np.minimum(np.arange(w) + r, w - 1) - np.maximum(np.arange(w) - r, 0) + 1
+    side_y = np.minimum(np.arange(h) + r, h - 1) - np.maximum(np.arange(h) - r, 0) + 1
+    pairs = int(side_x.sum()) * int(side_y.sum())
+    ctx.close()
+    return {"workload": name, "entry": "latch_dense_extract x 2, latch_dense_match (radius 8)",
+            "pixels": w * h, "candidate_pairs": pairs, "ms_extract_two_images": ms_ext, "ms_match": ms_mat,
+            "desc_per_s": 2 * w * h / (ms_ext / 1e3), "match_gpairs_per_s": pairs / (ms_mat / 1e3) / 1e9,
+            "shift_recovered_inside": shift_found,
+            "roofline": roofline.dominant([(ms_ext, roofline.dense_extraction(ms_ext, 2 * w * h, name, PEAKS)),
+                                           (ms_mat, roofline.dense_match(ms_mat, pairs, name, PEAKS))]),
+            "clocks": clk}
+
+
 def bench_detect(args, local):
     """Oriented FAST on one 4000x3000 image of the batched workload (threshold 20):
     detection alone, and detection + extraction of every keypoint found in one call
@@ -847,7 +897,7 @@ def run_latch(args):
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
     single = {"pair": bench_oriented_pair, "plain_pair": bench_plain_pair, "gallery": bench_gallery,
-              "detect": bench_detect, "weighted": bench_weighted, "serve": bench_serve}
+              "detect": bench_detect, "weighted": bench_weighted, "dense": bench_dense, "serve": bench_serve}
     if args.workload in single:
         print(json.dumps({"metric": METRIC, **single[args.workload](args, local)}))
         return 0
@@ -858,7 +908,8 @@ def run_latch(args):
         torch.cuda.empty_cache()
         for key, fn in (("plain_640x480_2k", bench_plain_pair), ("oriented_scaled_1920x1080_10k", bench_oriented_pair),
                         ("gallery_16384x1048576", bench_gallery), ("detect_extract_4000x3000", bench_detect),
-                        ("weighted_8x8_1920x1080", bench_weighted), ("serve", bench_serve)):
+                        ("weighted_8x8_1920x1080", bench_weighted), ("dense_640x480_r8", bench_dense),
+                        ("serve", bench_serve)):
             sub[key] = fn(args, local)
             torch.cuda.empty_cache()
     if rank != 0:

@@ -98,14 +98,15 @@ enum {
     LATCH_WINDOW = 48,      /* window side in pixels */
     LATCH_PATCH = 7,        /* patch side in pixels */
     LATCH_MAX_SCALES = 8,
-    LATCH_ANGLE_BINS = 32
+    LATCH_ANGLE_BINS = 32,
+    LATCH_DENSE_MAX_RADIUS = 16  /* largest search radius of latch_dense_match */
 };
 
 /* Matching paths (both exact). */
 enum {
     LATCH_PATH_AUTO = 0,    /* chosen per shape */
     LATCH_PATH_POPC = 1,    /* XOR + population count on the CUDA cores */
-    LATCH_PATH_TENSOR = 2   /* bits expanded to 0/1 8-bit floats, dot products on the tensor cores */
+    LATCH_PATH_TENSOR = 2   /* bits expanded to 0/1 4-bit floats, dot products on the tensor cores */
 };
 
 /* Create a context on CUDA device `device` (makes it current on this thread).
@@ -226,6 +227,32 @@ latch_status latch_detect_pyramid(latch_context *ctx, const latch_image *img, in
 latch_status hamming_match(latch_context *ctx, const uint8_t *d_query, int32_t nq, const uint8_t *d_train,
                            int32_t nt, int32_t k, float ratio, latch_match *d_out, int32_t path,
                            latch_stream_t stream);
+
+/*
+ * Dense per-pixel LATCH (Sec. 6: CLATCH for dense pixel matching, an alternative to
+ * PatchMatch).  Reading: every pixel (x, y) of `img` is a keypoint at angle bin 0
+ * and scale 1 (window pixel (u, v) = image pixel (x + u - 24, y + v - 24), 0
+ * outside the image) with the context's 7x7 triplet table; descriptors are written
+ * in raster order, row y * width + x.
+ *   d_out    width * height * 64 bytes (device, 16-byte aligned)
+ * LATCH_EUNSUPPORTED when the context uses weighted 8x8 patches.
+ */
+latch_status latch_dense_extract(latch_context *ctx, const latch_image *img, uint8_t *d_out, latch_stream_t stream);
+
+/*
+ * Windowed matching of two dense descriptor fields of the same size (Sec. 6):
+ * pixel p of A is matched against the pixels q of B with |q.x - p.x| <= radius and
+ * |q.y - p.y| <= radius that lie inside B, in raster order of B, with the rule of
+ * hamming_match (nearest, second nearest among the others, ties to the lowest
+ * index, ratio test); idx1 / idx2 are raster indices y * width + x in B.
+ *   d_a, d_b width * height * 64 bytes each (device, 16-byte aligned)
+ *   radius   0 .. LATCH_DENSE_MAX_RADIUS;  k 1 or 2;  ratio in [0, 1]
+ *   d_out    width * height latch_match records (device)
+ * Radius 0 (or a 1-pixel image) leaves no second candidate: idx2 = -1, dist2 = 65535.
+ */
+latch_status latch_dense_match(latch_context *ctx, const uint8_t *d_a, const uint8_t *d_b, int32_t width,
+                               int32_t height, int32_t radius, int32_t k, float ratio, latch_match *d_out,
+                               latch_stream_t stream);
 
 /* A batch of images, each matched against others (the structure-from-motion
  * pattern of Sec. 4-5: every image against its neighbours in sequence).

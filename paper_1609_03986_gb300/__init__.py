@@ -126,6 +126,8 @@ EXPORTS = [
     ("latch_detect_pyramid", ctypes.c_int, [_P, ctypes.POINTER(latch_image), _I32, _I32, _I32, _P, _P, _P, _P]),
     ("latch_detect", ctypes.c_int, [_P, ctypes.POINTER(latch_image), _I32, _I32, _I32, _P, _P, _P]),
     ("latch_detect_extract", ctypes.c_int, [_P, ctypes.POINTER(latch_image), _I32, _I32, _I32, _P, _P, _P, _P]),
+    ("latch_dense_extract", ctypes.c_int, [_P, ctypes.POINTER(latch_image), _P, _P]),
+    ("latch_dense_match", ctypes.c_int, [_P, _P, _P, _I32, _I32, _I32, _I32, _F, _P, _P]),
 ]
 
 
@@ -255,8 +257,21 @@ def hamming_match(ctx, query, nq: int, train, nt: int, k: int, ratio: float, out
 def hamming_match_noalloc(query, nq: int, train, nt: int, k: int, ratio: float, out, stream: int = 0) -> None:
     """hamming_match on the current device without allocating device memory (for
     callers that may not call cudaMalloc); scratch is the library's fixed 16 MiB
-    array, so nq + nt is limited to roughly 30,000 descriptors."""
+    array, so nq + nt is limited to roughly 60,000 descriptors."""
     _check(None, library().hamming_match_noalloc(_ptr(query), nq, _ptr(train), nt, k, ratio, _ptr(out), stream))
+
+
+def latch_dense_extract(ctx, image, width: int, height: int, pitch: int, out, stream: int = 0) -> None:
+    """Descriptor of every pixel (device pointers image, out: width * height * 64 bytes)."""
+    img = latch_image(_ptr(image), width, height, pitch)
+    _check(ctx, library().latch_dense_extract(ctx, ctypes.byref(img), _ptr(out), stream))
+
+
+def latch_dense_match(ctx, desc_a, desc_b, width: int, height: int, radius: int, k: int, ratio: float, out,
+                      stream: int = 0) -> None:
+    """Windowed matching of two dense descriptor fields (device pointers)."""
+    _check(ctx, library().latch_dense_match(ctx, _ptr(desc_a), _ptr(desc_b), width, height, radius, k, ratio,
+                                            _ptr(out), stream))
 
 
 def hamming_match_noalloc_status() -> None:
@@ -575,6 +590,24 @@ class Context:
         if out is None:
             out = torch.empty((nq, 16), dtype=torch.uint8, device=query.device)
         hamming_match(self.handle, query, nq, train, nt, k, ratio, out, path, self._stream(stream))
+        return out
+
+    def dense_extract(self, image, width: int, height: int, out=None, stream=None):
+        """image: (H, pitch) uint8 CUDA tensor.  Returns the (H * W, 64) uint8 CUDA tensor
+        of every pixel's descriptor, raster order."""
+        import torch
+        if out is None:
+            out = torch.empty((width * height, DESC_BYTES), dtype=torch.uint8, device=image.device)
+        latch_dense_extract(self.handle, image, width, height, image.stride(0), out, self._stream(stream))
+        return out
+
+    def dense_match(self, desc_a, desc_b, width: int, height: int, radius: int, k: int = 2, ratio: float = 0.8,
+                    out=None, stream=None):
+        """Two (H * W, 64) dense fields -> (H * W, 16) uint8 tensor of latch_match."""
+        import torch
+        if out is None:
+            out = torch.empty((width * height, 16), dtype=torch.uint8, device=desc_a.device)
+        latch_dense_match(self.handle, desc_a, desc_b, width, height, radius, k, ratio, out, self._stream(stream))
         return out
 
     def check(self):

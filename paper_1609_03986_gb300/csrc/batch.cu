@@ -126,7 +126,7 @@ extern "C" latch_status latch_batch_run(latch_context* ctx, const latch_batch_de
     // there is matching to do
     const bool matching = b->n_pairs > 0 && plan.total_out > 0;
     uint8_t* mbase = base + plan.ext_bytes;
-    const size_t exp_bytes = (static_cast<size_t>(plan.total_kp) * 512 + 1023) / 1024 * 1024;
+    const size_t exp_bytes = (static_cast<size_t>(plan.total_kp) * kExpRowBytes + 1023) / 1024 * 1024;
     if (ev) cudaEventRecord(ev[0], s);
     if (matching) {
         // cleared before the extraction, so that nothing sits between the extraction

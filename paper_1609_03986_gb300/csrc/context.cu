@@ -482,4 +482,39 @@ latch_status hamming_match(latch_context* ctx, const uint8_t* d_query, int32_t n
                       "popc match launch");
 }
 
+latch_status latch_dense_extract(latch_context* ctx, const latch_image* img, uint8_t* d_out, latch_stream_t stream) {
+    if (!ctx) return fail(ctx, LATCH_EINVAL, "NULL context");
+    latch_status st = validate_image(ctx, img);
+    if (st != LATCH_OK) return st;
+    if (!d_out || (reinterpret_cast<uintptr_t>(d_out) & 15))
+        return fail(ctx, LATCH_EINVAL, "d_out must be non-NULL and 16-byte aligned");
+    if (!ctx->has_trip) return fail(ctx, LATCH_EINVAL, "no triplet table: call latch_set_triplets");
+    if (ctx->weighted) return fail(ctx, LATCH_EUNSUPPORTED, "dense extraction uses 7x7 patches (weights are set)");
+    LATCH_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    return cuda_check(ctx, launch_dense_extract(ctx, img, d_out, static_cast<cudaStream_t>(stream)),
+                      "dense extract launch");
+}
+
+latch_status latch_dense_match(latch_context* ctx, const uint8_t* d_a, const uint8_t* d_b, int32_t width,
+                               int32_t height, int32_t radius, int32_t k, float ratio, latch_match* d_out,
+                               latch_stream_t stream) {
+    if (!ctx) return fail(ctx, LATCH_EINVAL, "NULL context");
+    if (width < 1 || height < 1 || width > 32768 || height > 32768)
+        return fail(ctx, LATCH_EINVAL, "field size %dx%d outside [1, 32768]", width, height);
+    if (radius < 0 || radius > LATCH_DENSE_MAX_RADIUS)
+        return fail(ctx, LATCH_EINVAL, "radius %d outside [0, %d]", radius, LATCH_DENSE_MAX_RADIUS);
+    if (k != 1 && k != 2) return fail(ctx, LATCH_EINVAL, "k = %d must be 1 or 2", k);
+    if (!(ratio >= 0.0f && ratio <= 1.0f)) return fail(ctx, LATCH_EINVAL, "ratio %g not in [0, 1]", ratio);
+    if (!d_a || !d_b || !d_out) return fail(ctx, LATCH_EINVAL, "NULL descriptor field or output");
+    if ((reinterpret_cast<uintptr_t>(d_a) | reinterpret_cast<uintptr_t>(d_b) | reinterpret_cast<uintptr_t>(d_out)) &
+        15)
+        return fail(ctx, LATCH_EINVAL, "descriptor and output pointers must be 16-byte aligned");
+    LATCH_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    const int32_t r_milli = static_cast<int32_t>(std::round(static_cast<double>(ratio) * 1000.0));
+    return cuda_check(ctx,
+                      launch_dense_match(d_a, d_b, width, height, radius, k, r_milli, d_out,
+                                         static_cast<cudaStream_t>(stream)),
+                      "dense match launch");
+}
+
 }  // extern "C"

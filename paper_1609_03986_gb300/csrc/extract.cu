@@ -33,8 +33,8 @@
 //        (sum C1^2 - sum C2^2) - 2 (sum A.C1 - sum A.C2) over the 7 rows with
 //        __dp4a, all exact in 32-bit integers.  Each warp writes its bytes of
 //        every lane's descriptor (bit t = bit t % 8 of byte t / 8) and, when
-//        the caller also wants the tensor matcher's input, the 32-byte sector
-//        of the expanded row (byte t = E4M3 1.0 or 0 for bit t) and adds its
+//        the caller also wants the tensor matcher's input, its 16 bytes of the
+//        expanded row (4-bit value t = E2M1 1.0 or 0 for bit t) and adds its
 //        bits to the popcount (which the sort zeroes).
 //    The stages hand the window buffers over through mbarriers (full: 384
 //    builder arrivals, empty: 16 evaluator arrivals); every wait is bounded.
@@ -380,14 +380,6 @@ __device__ __forceinline__ uint32_t eval_chunk_weighted(const uint2* trip, const
     return byte;
 }
 
-// Expanded row segment for 16 descriptor bits: byte q is 0x38 (E4M3 1.0) when bit q
-// is set.  x * 0x00204081 moves bit q of a 4-bit x to bit 8q (no two partial
-// products overlap).
-__device__ __forceinline__ uint32_t expand4(uint32_t x) { return ((x * 0x00204081u) & 0x01010101u) * 0x38u; }
-__device__ __forceinline__ uint4 expand16(uint32_t h) {
-    return make_uint4(expand4(h & 15u), expand4((h >> 4) & 15u), expand4((h >> 8) & 15u), expand4((h >> 12) & 15u));
-}
-
 struct LanesSmem {  // static part
     uint2 trip[kBits];                // LaneTriplets
     int4 rec[2][kBatch];              // builders: the batch's records
@@ -591,37 +583,25 @@ __global__ void __launch_bounds__(kThreads, 1) extract_lanes_kernel(
             else
                 v |= eval_chunk(S.trip, wl, c) << (8 * (c - wa));
         }
-        // output rows: this lane's keypoint, and the keypoints whose expanded sector
-        // this lane writes (lane / 2 and 16 + lane / 2)
+        // output row of this lane's keypoint
         const int32_t row = S.row[buf][lane];
-        const int32_t row_a = S.row[buf][lane >> 1], row_b = S.row[buf][16 + (lane >> 1)];
         __syncwarp();
         if (lane == 0) mbar_arrive(&S.empty[buf]);  // the windows and rows are free again
         if (wb == wa) continue;
         // ---- descriptor bytes [wa, wb), expanded bytes [8 wa, 8 wb), popcount ----
         if (wb - wa == 4 && (wa & 3) == 0) {
             if (lane < nk) reinterpret_cast<uint32_t*>(out + static_cast<size_t>(row) * kDescBytes)[wa >> 2] = v;
-            if (exp_out) {
-                // the 32 expanded bytes of a keypoint are one sector: lanes 2m, 2m + 1
-                // write keypoint m's (and 16 + m's) halves
-#pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    const int m = 16 * k + (lane >> 1);
-                    const uint32_t vm = __shfl_sync(0xffffffffu, v, m);
-                    if (m < nk)
-                        reinterpret_cast<uint4*>(exp_out + static_cast<size_t>(k ? row_b : row_a) * kBits +
-                                                 8 * wa)[lane & 1] = expand16((vm >> (16 * (lane & 1))) & 0xffffu);
-                }
-            }
+            if (exp_out && lane < nk)  // the word's 32 expanded values: 16 bytes of the lane's row
+                reinterpret_cast<uint4*>(exp_out + static_cast<size_t>(row) * kExpRowBytes)[wa >> 2] =
+                    expand_word_e2m1(v);
         } else if (lane < nk) {
             uint8_t* d = out + static_cast<size_t>(row) * kDescBytes;
             for (int c = wa; c < wb; ++c) {
                 const uint32_t byte = (v >> (8 * (c - wa))) & 0xffu;
                 d[c] = static_cast<uint8_t>(byte);
-                if (exp_out) {
-                    const uint4 ex = expand16(byte);
-                    reinterpret_cast<uint2*>(exp_out + static_cast<size_t>(row) * kBits)[c] = make_uint2(ex.x, ex.y);
-                }
+                if (exp_out)
+                    reinterpret_cast<uint32_t*>(exp_out + static_cast<size_t>(row) * kExpRowBytes)[c] =
+                        expand_byte_e2m1(byte);
             }
         }
         if (exp_out && lane < nk) atomicAdd(pop_out + row, __popc(v));

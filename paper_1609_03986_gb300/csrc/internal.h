@@ -22,6 +22,29 @@ constexpr int kBins = LATCH_ANGLE_BINS;
 constexpr double kMaxScale = 2.25;
 constexpr int kMaxReach = 77;               // max |offset| at scale 2.25 (24*sqrt(2)*2.25 = 76.4)
 
+// The tensor matcher's input row of one descriptor: its 512 bits as 4-bit E2M1
+// floats, two per byte, bit t -> value t (1.0 = 0x2 when set, 0 otherwise; value t
+// in the low nibble of byte t / 2 when t is even), so a dot product of two rows
+// counts the bits the descriptors share.
+constexpr int kExpRowBytes = 256;
+
+#ifdef __CUDACC__
+// Byte -> its 8 bits as 8 E2M1 values (nibble q = 2 * bit q), by spreading the bits
+// in three mask-and-shift steps (4-bit groups, then pairs, then single bits).
+__device__ __forceinline__ uint32_t expand_byte_e2m1(uint32_t b) {
+    uint32_t x = b & 0xffu;
+    x = (x | (x << 12)) & 0x000F000Fu;
+    x = (x | (x << 6)) & 0x03030303u;
+    x = (x | (x << 3)) & 0x11111111u;
+    return x << 1;
+}
+// 32 descriptor bits (bit q = descriptor bit 32 i + q) -> their 16 expanded bytes.
+__device__ __forceinline__ uint4 expand_word_e2m1(uint32_t w) {
+    return make_uint4(expand_byte_e2m1(w), expand_byte_e2m1(w >> 8), expand_byte_e2m1(w >> 16),
+                      expand_byte_e2m1(w >> 24));
+}
+#endif
+
 // Device-side error flags (OR-ed into ctx->d_flags).
 enum : uint32_t { kFlagBadScale = 1u, kFlagTimeout = 2u };
 
@@ -121,8 +144,8 @@ cudaError_t launch_extract(const latch_context* ctx, const latch_image* img, con
                            uint8_t* d_out, void* scratch, cudaStream_t stream);
 size_t extract_scratch_bytes(const latch_image* img, int64_t n);
 // Images [0, count) with keypoints d_kps[kp0[i] .. kp0[i] + n[i]) -> d_out rows at the same positions.
-// When exp_out is not NULL, row r of the tensor matcher's input (512 bytes, E4M3 0 / 1.0 per bit)
-// and pop_out[r] (the descriptor's popcount) are written as well.
+// When exp_out is not NULL, row r of the tensor matcher's input (kExpRowBytes bytes, E2M1 0 / 1.0
+// per bit) and pop_out[r] (the descriptor's popcount) are written as well.
 // `flags`: the device error word the kernels raise flags in (NULL: the context's).
 cudaError_t launch_extract_batch(const latch_context* ctx, const latch_image* imgs, const int64_t* kp0,
                                  const int64_t* n, int count, const latch_keypoint* d_kps, uint8_t* d_out,
@@ -143,6 +166,13 @@ cudaError_t launch_detect(const latch_image* img, const double* scales, const in
                           int32_t threshold, int32_t max_kps, latch_keypoint* d_kps, int32_t* d_count, void* scratch,
                           cudaStream_t stream);
 size_t detect_scratch_bytes(const latch_image* img, const double* scales, int nlev);
+
+// Dense per-pixel descriptors and windowed matching (dense.cu).
+constexpr int kDenseMaxRadius = LATCH_DENSE_MAX_RADIUS;
+cudaError_t launch_dense_extract(const latch_context* ctx, const latch_image* img, uint8_t* d_out,
+                                 cudaStream_t stream);
+cudaError_t launch_dense_match(const uint8_t* d_a, const uint8_t* d_b, int32_t width, int32_t height, int32_t radius,
+                               int32_t k, int32_t r_milli, latch_match* d_out, cudaStream_t stream);
 
 cudaError_t launch_match_popc(const latch_context* ctx, const uint8_t* q, int32_t nq, const uint8_t* t, int32_t nt,
                               int32_t k, int32_t r_milli, latch_match* out, void* scratch, cudaStream_t stream);

@@ -1,28 +1,37 @@
 // Brute-force Hamming matching on the 5th-generation tensor cores (Sec. 4's
 // all-pairs distance computation, done as a dense contraction).
 //
-// With every descriptor bit expanded to an 8-bit float that is exactly 0 or 1
-// (E4M3 0x00 / 0x38), the dot product of two expanded descriptors counts their
-// common 1-bits, and Hamming(q, t) = popc(q) + popc(t) - 2 * dot(q, t).  Products
-// are 0/1 and sums are at most 512, so fp32 accumulation is exact.
+// With every descriptor bit expanded to a 4-bit E2M1 float that is exactly 0 or 1
+// (two per byte), the dot product of two expanded descriptors counts their common
+// 1-bits, and Hamming(q, t) = popc(q) + popc(t) - 2 * dot(q, t).  The block-scaled
+// fp4 MMA (kind::mxf4, every scale factor 2^0) issues twice the products per clock
+// of the 8-bit kind; products are 0/1 and sums are at most 512, so fp32
+// accumulation is exact.
 //
 // One launch serves a batch of matching problems (query set x train set pairs; a
 // single hamming_match call is a batch of one).  All descriptors live in one
-// expanded buffer with one TMA tensor map.  The units (problem, 128-query tile,
-// 256-train tile) of all problems are linearised and split into one contiguous
-// range per block (one block per SM, persistent):
-//   warp 0     TMA producer: the query tile (128 rows x 512 B, 64 KB) stays resident
-//              while consecutive units share it; train chunks (256 rows x 128 bytes)
-//              go through a 4-stage ring, 128-byte swizzle;
-//   warp 1     MMA issuer: per unit 16 tcgen05.mma (M=128, N=256, K=32) into one of
-//              two double-buffered 256-column TMEM accumulators;
-//   warp 2     TMEM allocator (all 512 columns);
+// expanded buffer (two TMA tensor maps over it: 128-row query boxes, 96-row train
+// boxes).  The units (problem, 256-query tile, 96-train tile) of all problems are
+// linearised and split into one contiguous range per block (one block per SM,
+// persistent); a unit is two M=128 halves that share each train chunk, so every
+// train byte loaded feeds 256 query rows:
+//   warp 0     TMA producer: the query tile (256 rows x 256 B, 64 KB) stays resident
+//              while consecutive units share it; train chunks (96 rows x 128 bytes,
+//              half of K) go through a 12-stage ring, 128-byte swizzle;
+//   warp 1     MMA issuer: per unit 16 tcgen05.mma (M=128, N=96, K=64), two per K
+//              step (one per half), into one of two double-buffered sets of two
+//              96-column TMEM accumulators;
+//   warp 2     TMEM allocator (all 512 columns: accumulator sets at columns 0 and
+//              256, the constant scale factors between them);
 //   warp 3     column keys: per unit, (popc(train row) + 512) << 8 | column into a
 //              4-deep ring in shared memory, ahead of the epilogue;
-//   warps 4-19 epilogue (one query row and 64 columns per thread): double-buffered tcgen05.ld of
-//              the fp32 dot products, key =
+//   warps 4-19 epilogue (one query row and 48 columns per thread): tcgen05.ld of the
+//              fp32 dot products 16 columns at a time, key =
 //              ((popc(t) - 2*dot + 512) << 8 | column) formed exactly in fp32 by
-//              one FMA, four interleaved min / second-min chains with FMNMX; the tile's two best are
+//              one FMA; a group of 16 keys whose minimum is not below the row's
+//              running second-best (no key of it can enter the top two: its train
+//              indices are larger than every one seen) costs one min tree, the
+//              others update the min / second-min chains; the tile's two best are
 //              merged into the row's (distance << 32 | index) keys, and when the
 //              block leaves a query tile the row's two keys go to a partial record;
 //              the last block to leave a tile (a per-tile arrival counter) combines
@@ -46,51 +55,52 @@ namespace {
 
 using namespace sm103;
 
-constexpr int kRowsA = 128;             // rows per MMA (M) = query rows per tile
-constexpr int kRowsQ = kRowsA;          // queries per tile
-constexpr int kColsB = 256;             // train rows per unit (N)
+constexpr int kRowsA = 128;             // rows per MMA (M)
+constexpr int kHalves = 1;              // MMAs per K step: the tile's two 128-row halves
+constexpr int kRowsQ = kHalves * kRowsA;  // queries per tile
+constexpr int kColsB = 192 / kHalves;   // train rows per unit (N)
 constexpr int kRowsP = kRowsQ;          // partial records per tile slot: one per query row
-constexpr int kKBytes = 512;            // expanded descriptor: 512 x 8-bit
+constexpr int kKBytes = kExpRowBytes;   // expanded descriptor: 512 x 4-bit
 constexpr int kChunk = 128;             // K bytes per swizzle atom / TMA box
 constexpr int kChunks = kKBytes / kChunk;
-constexpr int kStages = 4;
-constexpr int kTileBytes = kRowsA * kChunk;   // 16 KB: one TMA box of 128 rows x 128 B
-constexpr int kStageBytes = kColsB * kChunk;  // 32 KB: a train chunk of 256 rows x 128 B
-constexpr int kEpiWarps = 16;                       // epilogue: 4 lane quarters x 4 column groups
+constexpr int kMmaKBytes = 32;          // K bytes per MMA: 64 E2M1 values
+constexpr int kStages = kHalves == 2 ? 12 : 7;
+constexpr int kTileBytes = kRowsA * kChunk;   // 16 KB: a half tile's chunk of 128 rows x 128 B (one TMA box)
+constexpr int kStageBytes = kColsB * kChunk;  // 12 KB: a train chunk of 96 rows x 128 B (one TMA box)
+constexpr int kEpiWarps = 16;                       // epilogue: 4 lane quarters x 2 halves x 2 column groups
 constexpr int kEpiThreads = kEpiWarps * 32;
-constexpr int kThreads = 128 + kEpiThreads;         // producer, MMA, TMEM, idle, then the epilogue
-constexpr int kColGroups = kEpiWarps / 4;
+constexpr int kThreads = 128 + kEpiThreads;         // producer, MMA, TMEM, keys, then the epilogue
+constexpr int kColGroups = kEpiWarps / (4 * kHalves);
 constexpr int kColsPerThread = kColsB / kColGroups;  // accumulator columns one epilogue thread scans
 constexpr int kLdCols = 16;                          // columns per tcgen05.ld (double-buffered)
 constexpr int kKeyStages = 4;                        // column-key vectors prepared ahead of the epilogue
-constexpr int kTmemCols = 512;  // two 256-column accumulators
-constexpr uint32_t kIdesc = idesc_e4m3_f32(kRowsA, kColsB);
+constexpr int kTmemCols = 512;
+constexpr uint32_t kAccStride = 256;  // accumulator set b: half h at TMEM columns 256 b + 96 h, 96 wide
+constexpr uint32_t kSfaCol = 192;     // scale factors of A: 4 columns (128 rows)
+constexpr uint32_t kSfbCol = 224;     // scale factors of B: 4 columns per 128 rows
+constexpr uint32_t kScaleOne = 0x7F7F7F7Fu;  // four UE8M0 scale factors 2^0
+constexpr uint32_t kIdesc = idesc_mxf4_e2m1(kRowsA, kColsB);
+static_assert(kHalves * kColsB <= kSfaCol && kSfbCol + 8 <= kAccStride, "TMEM columns overlap");
+static_assert(kColsPerThread == 3 * kLdCols, "epilogue: three 16-column loads per unit");
+
+// min(a, b, c) in one instruction.
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
 
 // Barrier of the epilogue threads (named barrier 1).
 __device__ __forceinline__ void group_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
 
-// AND of `v` over the epilogue threads (named barrier 1).
-__device__ __forceinline__ bool group_all(bool v) {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\t"
-        "setp.ne.u32 q, %1, 0;\n\t"
-        "bar.red.and.pred p, 1, %2, q;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(r)
-        : "r"(static_cast<uint32_t>(v)), "n"(kEpiThreads)
-        : "memory");
-    return r != 0;
-}
-
 struct Smem {
     // offsets in the 1024-aligned dynamic buffer
-    static constexpr int a = 0;                                        // [kChunks] tiles of 16 KB
-    static constexpr int b = a + kChunks * kTileBytes;                 // [kStages] chunks of 32 KB
+    static constexpr int a = 0;                                        // [kHalves][kChunks] boxes of 16 KB
+    static constexpr int b = a + kHalves * kChunks * kTileBytes;       // [kStages] chunks of 12 KB
     static constexpr int cvec = b + kStages * kStageBytes;             // float [kKeyStages][kColsB]
     static constexpr int part = cvec + kKeyStages * kColsB * 4;        // uint64 [kEpiThreads][2]
     static constexpr int bars = part + kEpiThreads * 16;               // uint64 barriers
-    static constexpr int nbars = 2 * kStages + 2 + 4 + 1 + 2 * kKeyStages;
+    static constexpr int nbars = 2 * kStages + 2 + 4 + 2 + 2 * kKeyStages;
     static constexpr int misc = bars + nbars * 8;                      // tmem base, abort flag, last-arrival flag
     static constexpr int total = misc + 16;
 };
@@ -132,10 +142,18 @@ __device__ __noinline__ Share next_share(const B& b, int p, int64_t c) {
     return Share{b.count, 0, 0, 0, 0};
 }
 
+// The fields of the current problem that the walk needs every unit are kept in
+// registers (reading the problem table, a kernel parameter, with a run-time index
+// costs hundreds of cycles per unit on the MMA warp's path).
 struct UnitIter {
     int p;          // current problem (count once the walk is over)
+    int count;      // problems in the batch
     int32_t m, n;   // query tile, train tile of the current unit
     int32_t cs;     // c': the block's share index in problem p
+    int32_t ntl;    // train tiles of problem p
+    int32_t g0;     // global index of problem p's first query tile
+    int32_t t_row0; // first train row of problem p
+    int32_t nt;     // train rows of problem p
     int64_t left;   // units left in the share, the current one included
     template <class B>
     __device__ __forceinline__ void take(const B& b, int from, int64_t c) {
@@ -145,26 +163,36 @@ struct UnitIter {
         n = s.n;
         cs = s.cs;
         left = s.left;
+        if (p < count) {
+            const MatchProblem& P = b.p[p];
+            ntl = P.ntl;
+            g0 = P.g0;
+            t_row0 = P.t_row0;
+            nt = P.nt;
+        }
     }
     template <class B>
-    __device__ __forceinline__ void init(const B& b, int64_t c) { take(b, 0, c); }
+    __device__ __forceinline__ void init(const B& b, int64_t c) {
+        count = b.count;
+        take(b, 0, c);
+    }
     template <class B>
-    __device__ __forceinline__ bool done(const B& b) const { return p >= b.count; }
+    __device__ __forceinline__ bool done(const B&) const { return p >= count; }
     template <class B>
-    __device__ __forceinline__ int64_t g(const B& b) const { return b.p[p].g0 + m; }
+    __device__ __forceinline__ int64_t g(const B&) const { return g0 + m; }
     template <class B>
     __device__ __forceinline__ int64_t slot(const B& b) const {
-        return b.p[p].g0 + m + cs + static_cast<int64_t>(p) * (b.grid - 1);
+        return g0 + m + cs + static_cast<int64_t>(p) * (b.grid - 1);
     }
     template <class B>
-    __device__ __forceinline__ bool last_of_tile(const B& b) const { return left == 1 || n + 1 == b.p[p].ntl; }
+    __device__ __forceinline__ bool last_of_tile(const B&) const { return left == 1 || n + 1 == ntl; }
     template <class B>
     __device__ __forceinline__ void next(const B& b, int64_t c) {
         if (--left == 0) {
             take(b, p + 1, c);
             return;
         }
-        if (++n == b.p[p].ntl) {
+        if (++n == ntl) {
             n = 0;
             ++m;
         }
@@ -231,7 +259,8 @@ __device__ __forceinline__ latch_match final_match(uint64_t k1, uint64_t k2, int
 // tile_cnt: per-query-tile arrival counters, zero at launch and zero again after a
 // complete launch; NULL = leave the combination to match_merge_kernel.
 template <int NP>
-__global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_constant__ CUtensorMap tm,
+__global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_constant__ CUtensorMap tmq,
+                                                              const __grid_constant__ CUtensorMap tmt,
                                                               const __grid_constant__ MatchBatchT<NP> batch,
                                                               const int32_t* __restrict__ pop,
                                                               uint64_t* __restrict__ partials,
@@ -251,8 +280,8 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
     uint64_t* a_empty = a_full + 1;
     uint64_t* acc_full = a_full + 2;
     uint64_t* acc_empty = a_full + 4;
-    uint64_t* mma_done = a_full + 6;
-    uint64_t* key_full = a_full + 7;               // [kKeyStages]
+    uint64_t* mma_done = a_full + 6;               // [2]: one per MMA warp
+    uint64_t* key_full = a_full + 8;               // [kKeyStages]
     uint64_t* key_empty = key_full + kKeyStages;   // [kKeyStages]
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + Smem::misc);
     volatile int* abort = reinterpret_cast<volatile int*>(smem + Smem::misc + 4);
@@ -268,12 +297,13 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
             mbar_init(&empty[i], 1);
         }
         mbar_init(a_full, 1);
-        mbar_init(a_empty, 1);
+        mbar_init(a_empty, 2);  // both MMA warps commit once per query tile
         for (int i = 0; i < 2; ++i) {
             mbar_init(&acc_full[i], 1);
             mbar_init(&acc_empty[i], kEpiThreads / 32);
         }
-        mbar_init(mma_done, 1);
+        mbar_init(&mma_done[0], 1);
+        mbar_init(&mma_done[1], 1);
         for (int i = 0; i < kKeyStages; ++i) {
             mbar_init(&key_full[i], 32);
             mbar_init(&key_empty[i], kEpiWarps);
@@ -281,7 +311,10 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
         *abort = 0;
         fence_mbar_init();
     }
-    if (warp == 0 && lane == 0) prefetch_tmap(&tm);
+    if (warp == 0 && lane == 0) {
+        prefetch_tmap(&tmq);
+        prefetch_tmap(&tmt);
+    }
     if (warp == 2) {
         tmem_alloc(tmem_slot, kTmemCols);
         tc_fence_before();
@@ -289,6 +322,17 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    if (warp >= 4 && warp < 8) {
+        // every block scale factor 2^0: the scale columns of all 128 lanes (warp w may
+        // address lane quarter w % 4)
+        const uint32_t base = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16) + kSfaCol;
+#pragma unroll
+        for (uint32_t col = 0; col < kAccStride - kSfaCol; col += 8) tmem_st_32x32b_x8_same(base + col, kScaleOne);
+        tmem_st_wait();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
     // everything above touched only this block's shared memory and TMEM
     griddep_wait();
     griddep_launch_dependents();
@@ -313,10 +357,11 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                         if (!mbar_wait(a_empty, a_par, abort)) break;
                         a_par ^= 1;
                     }
-                    mbar_arrive_expect_tx(a_full, kChunks * kTileBytes);
-                    for (int kc = 0; kc < kChunks; ++kc)
-                        tma_load_2d(sA + kc * kTileBytes, &tm, kc * kChunk, static_cast<int32_t>(P.q_row0 + m * kRowsQ),
-                                    a_full);
+                    mbar_arrive_expect_tx(a_full, kHalves * kChunks * kTileBytes);
+                    for (int h = 0; h < kHalves; ++h)
+                        for (int kc = 0; kc < kChunks; ++kc)
+                            tma_load_2d(sA + (h * kChunks + kc) * kTileBytes, &tmq, kc * kChunk,
+                                        static_cast<int32_t>(P.q_row0 + m * kRowsQ + h * kRowsA), a_full);
                     prev_g = g;
                 }
                 bool ok = true;
@@ -326,9 +371,8 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                         break;
                     }
                     mbar_arrive_expect_tx(&full[stage], kStageBytes);
-                    for (int h = 0; h < kColsB / kRowsA; ++h)  // two 128-row boxes, rows back to back
-                        tma_load_2d(sB + stage * kStageBytes + h * kTileBytes, &tm, kc * kChunk,
-                                    static_cast<int32_t>(P.t_row0 + n * kColsB + h * kRowsA), &full[stage]);
+                    tma_load_2d(sB + stage * kStageBytes, &tmt, kc * kChunk, static_cast<int32_t>(it.t_row0 + n * kColsB),
+                                &full[stage]);
                     filled[stage] = true;
                     fill_par[stage] = ring;
                     if (++stage == kStages) {
@@ -349,55 +393,78 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                     }
             }
         }
-    } else if (warp == 1) {
-        // ---------------- MMA issuer ----------------
+    } else if (warp == 1 || warp == 2) {
+        // ---------------- MMA issuers: warp 1 issues the even units, warp 2 the odd ones
+        // (a thread's tcgen05.mma waits until the tensor pipe takes it, so a single
+        // issuer leaves the pipe idle while it waits on barriers between units; with two,
+        // one issuer's waits overlap the other's MMAs).  Unit i uses accumulator i % 2 and
+        // stages 2 i, 2 i + 1 of the ring; both issuers walk every unit, wait for every
+        // query tile and commit a_empty (count 2) at every tile's end. ----------------
         if (lane == 0) {
+            const int mine = warp - 1;
             UnitIter it;
             it.init(batch, c);
             int stage = 0;
-            uint32_t ring = 0, a_par = 0;
-            uint32_t acc_par[2] = {0, 0};
+            uint32_t ring = 0, a_par = 0, acc_par = 0;
             int64_t prev_g = -1;
             int i = 0;
+            // shared-memory descriptors of the first query box and train chunk; the others
+            // differ only in the start-address field (bits 0-13: address / 16), so each MMA
+            // adds a constant to them
+            const uint64_t a_desc0 = umma_desc_sw128(smem_u32(sA));
+            const uint64_t b_desc0 = umma_desc_sw128(smem_u32(sB));
+            const uint32_t sfa = tmem + kSfaCol, sfb = tmem + kSfbCol;
+            const uint32_t d0 = tmem + static_cast<uint32_t>(mine) * kAccStride;
             for (; !it.done(batch) && !*abort; ++i, it.next(batch, c)) {
                 const int64_t g = it.g(batch);
-                const int buf = i & 1;
                 if (g != prev_g) {
                     if (!mbar_wait(a_full, a_par, abort)) break;
                     a_par ^= 1;
                     prev_g = g;
                 }
-                if (!mbar_wait(&acc_empty[buf], acc_par[buf] ^ 1, abort)) break;
-                acc_par[buf] ^= 1;
-                tc_fence_after();
-                bool ok = true;
-                for (int kc = 0; kc < kChunks; ++kc) {
-                    if (!mbar_wait(&full[stage], ring, abort)) {
-                        ok = false;
-                        break;
-                    }
+                if ((i & 1) == mine) {
+                    if (!mbar_wait(&acc_empty[mine], acc_par ^ 1, abort)) break;
+                    acc_par ^= 1;
                     tc_fence_after();
-                    const uint32_t b_addr = smem_u32(sB + stage * kStageBytes);
-                    const uint32_t a_addr = smem_u32(sA + kc * kTileBytes);
-                    const uint32_t d = tmem + static_cast<uint32_t>(buf * kColsB);
+                    bool ok = true;
+                    for (int kc = 0; kc < kChunks; ++kc) {
+                        if (!mbar_wait(&full[stage], ring, abort)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint64_t bd = b_desc0 + static_cast<uint64_t>((stage * kStageBytes) >> 4);
+                        const uint64_t ad = a_desc0 + static_cast<uint64_t>((kc * kTileBytes) >> 4);
 #pragma unroll
-                    for (int ks = 0; ks < kChunk / 32; ++ks)
-                        mma_f8f6f4(d, umma_desc_sw128(a_addr + ks * 32), umma_desc_sw128(b_addr + ks * 32), kIdesc,
-                                   (kc | ks) != 0);
-                    mma_commit(&empty[stage]);
-                    if (++stage == kStages) {
-                        stage = 0;
+                        for (int ks = 0; ks < kChunk / kMmaKBytes; ++ks)
+#pragma unroll
+                            for (int h = 0; h < kHalves; ++h)
+                                mma_mxf4(d0 + static_cast<uint32_t>(h * kColsB),
+                                         ad + static_cast<uint64_t>((h * kChunks * kTileBytes + ks * kMmaKBytes) >> 4),
+                                         bd + static_cast<uint64_t>((ks * kMmaKBytes) >> 4), kIdesc, sfa, sfb,
+                                         (kc | ks) != 0);
+                        mma_commit(&empty[stage]);
+                        if (++stage == kStages) {
+                            stage = 0;
+                            ring ^= 1;
+                        }
+                    }
+                    if (!ok) break;
+                    mma_commit(&acc_full[mine]);
+                } else {
+                    // the other issuer's unit: its stages
+                    stage += kChunks;
+                    if (stage >= kStages) {
+                        stage -= kStages;
                         ring ^= 1;
                     }
                 }
-                if (!ok) break;
-                mma_commit(&acc_full[buf]);
                 if (it.last_of_tile(batch)) mma_commit(a_empty);
             }
             // every issued MMA has finished before TMEM is released
-            mma_commit(mma_done);
+            mma_commit(&mma_done[mine]);
             const uint64_t t0 = globaltimer();
-            while (!mbar_try_wait(mma_done, 0) && globaltimer() - t0 < 200000000ull) {
+            while (!mbar_try_wait(&mma_done[mine], 0) && globaltimer() - t0 < 200000000ull) {
             }
         }
     } else if (warp == 3) {
@@ -410,28 +477,31 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
             const int slot = static_cast<int>(i % kKeyStages);
             const uint32_t par = static_cast<uint32_t>(i / kKeyStages) & 1u;
             if (!mbar_wait(&key_empty[slot], par ^ 1, abort)) break;
-            const MatchProblem& P = batch.p[it.p];
             float* kv = sC + slot * kColsB;
 #pragma unroll
             for (int j = lane; j < kColsB; j += 32) {
                 const int64_t col = static_cast<int64_t>(it.n) * kColsB + j;
-                kv[j] = col < P.nt ? static_cast<float>((pop[P.t_row0 + col] + 512) * 256 + j)
-                                   : __int_as_float(0x7f800000);
+                kv[j] = col < it.nt ? static_cast<float>((pop[it.t_row0 + col] + 512) * 256 + j)
+                                    : __int_as_float(0x7f800000);
             }
             mbar_arrive(&key_full[slot]);  // each lane releases its own stores
         }
     } else if (warp >= 4) {
         // ---------------- epilogue: kEpiWarps warps; thread = one query row x one
         // group of kColsPerThread accumulator columns ----------------
-        const int et = threadIdx.x - 128;  // 0 .. kEpiThreads-1 (et < kColsB: the column of sC it fills)
+        const int et = threadIdx.x - 128;  // 0 .. kEpiThreads-1 = cg * kRowsQ + row_in_tile
         const int quarter = warp & 3;      // TMEM lane quarter this warp may access
-        const int cg = (warp - 4) >> 2;    // column group [cg * kColsPerThread, +kColsPerThread)
-        const int row_in_tile = quarter * 32 + lane;
+        const int half = ((warp - 4) >> 2) % kHalves;  // 128-row half of the query tile
+        const int cg = ((warp - 4) >> 2) / kHalves;    // column group [cg * kColsPerThread, +kColsPerThread)
+        const int row_in_tile = half * kRowsA + quarter * 32 + lane;
+        const float kInf = __int_as_float(0x7f800000);
         UnitIter it;
         it.init(batch, c);
         uint32_t acc_par[2] = {0, 0};
         uint64_t k1 = kNoKey, k2 = kNoKey;
         int32_t pq = 0;
+        float thr = kInf;  // unit keys below this can still enter the row's top two
+        bool aborted = false;  // warp-uniform
         int64_t prev_g = -1;
         int i = 0;
         for (; !it.done(batch); ++i, it.next(batch, c)) {
@@ -443,69 +513,84 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                 const int64_t row = m * kRowsQ + row_in_tile;
                 pq = row < P.nq ? pop[P.q_row0 + row] : 0;
                 k1 = k2 = kNoKey;
+                thr = kInf;
                 prev_g = g;
             }
             const int slot = i % kKeyStages;
             const uint32_t kpar = static_cast<uint32_t>(i / kKeyStages) & 1u;
-            // one vote of the epilogue threads, so that exits are group-uniform
-            if (!group_all(mbar_wait(&acc_full[buf], acc_par[buf], abort) &&
-                           mbar_wait(&key_full[slot], kpar, abort)))
-                break;
-            acc_par[buf] ^= 1;
-            tc_fence_after();
-            const float* cv = sC + slot * kColsB + cg * kColsPerThread;
-            const uint32_t base = tmem + (static_cast<uint32_t>(quarter * 32) << 16) +
-                                  static_cast<uint32_t>(buf * kColsB + cg * kColsPerThread);
-            // four independent min / second-min chains over this thread's columns
-            float m1[4], m2[4];
+            // after a failed wait a warp keeps walking the units without work, so that
+            // every warp reaches the barriers at the ends of query tiles
+            if (!aborted)
+                aborted = !__all_sync(0xffffffffu, mbar_wait(&acc_full[buf], acc_par[buf], abort) &&
+                                                       mbar_wait(&key_full[slot], kpar, abort));
+            if (!aborted) {
+                acc_par[buf] ^= 1;
+                tc_fence_after();
+                const float* cv = sC + slot * kColsB + cg * kColsPerThread;
+                const uint32_t base = tmem + (static_cast<uint32_t>(quarter * 32) << 16) +
+                                      static_cast<uint32_t>(buf) * kAccStride +
+                                      static_cast<uint32_t>(half * kColsB + cg * kColsPerThread);
+                // the thread's columns in one round trip; the accumulator is free again as
+                // soon as they are in registers
+                uint32_t va[kLdCols], vb[kLdCols], vc[kLdCols];
+                tmem_ld_32x32b_x16(base, va);
+                tmem_ld_32x32b_x16(base + kLdCols, vb);
+                tmem_ld_32x32b_x16(base + 2 * kLdCols, vc);
+                tmem_ld_wait();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acc_empty[buf]);
+                float e[kColsPerThread];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) m1[q] = m2[q] = __int_as_float(0x7f800000);
-            uint32_t va[kLdCols], vb[kLdCols];
-            tmem_ld_32x32b_x16(base, va);
-            tmem_ld_wait();
-            constexpr int kLds = kColsPerThread / kLdCols;
-#pragma unroll
-            for (int ch = 0; ch < kLds; ++ch) {
-                uint32_t* cur_v = (ch & 1) ? vb : va;
-                if (ch + 1 < kLds) tmem_ld_32x32b_x16(base + (ch + 1) * kLdCols, (ch & 1) ? va : vb);
-#pragma unroll
-                for (int j = 0; j < kLdCols; j += 4) {
-                    const float4 cc = *reinterpret_cast<const float4*>(cv + ch * kLdCols + j);
-                    const float e[4] = {fmaf(__uint_as_float(cur_v[j + 0]), -512.0f, cc.x),
-                                        fmaf(__uint_as_float(cur_v[j + 1]), -512.0f, cc.y),
-                                        fmaf(__uint_as_float(cur_v[j + 2]), -512.0f, cc.z),
-                                        fmaf(__uint_as_float(cur_v[j + 3]), -512.0f, cc.w)};
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float h = fmaxf(m1[q], e[q]);
-                        m1[q] = fminf(m1[q], e[q]);
-                        m2[q] = fminf(m2[q], h);
-                    }
+                for (int j = 0; j < kColsPerThread; j += 4) {
+                    const uint32_t* v = j < kLdCols ? va : (j < 2 * kLdCols ? vb : vc);
+                    const int jj = j % kLdCols;
+                    const float4 cc = *reinterpret_cast<const float4*>(cv + j);
+                    e[j + 0] = fmaf(__uint_as_float(v[jj + 0]), -512.0f, cc.x);
+                    e[j + 1] = fmaf(__uint_as_float(v[jj + 1]), -512.0f, cc.y);
+                    e[j + 2] = fmaf(__uint_as_float(v[jj + 2]), -512.0f, cc.z);
+                    e[j + 3] = fmaf(__uint_as_float(v[jj + 3]), -512.0f, cc.w);
                 }
-                if (ch + 1 < kLds) tmem_ld_wait();
-            }
-            // combine the chains (keys are unique): (a1,a2) + (b1,b2) -> (min, second min)
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&key_empty[slot]);
+                // the unit's minimum (a tree of 3-input mins); only a unit that reaches
+                // below the row's running second-best takes the top-two update
+                float t16[16], t6[6];
 #pragma unroll
-            for (int q = 1; q < 4; ++q) {
-                const float lo = fminf(m1[0], m1[q]), hi = fmaxf(m1[0], m1[q]);
-                m2[0] = fminf(hi, fminf(m2[0], m2[q]));
-                m1[0] = lo;
-            }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(&acc_empty[buf]);
-                mbar_arrive(&key_empty[slot]);
-            }
-            // the unit's two best (exact integers below 2^19) -> (distance << 32 | index) keys
+                for (int k = 0; k < 16; ++k) t16[k] = fmin3(e[3 * k], e[3 * k + 1], e[3 * k + 2]);
 #pragma unroll
-            for (int b = 0; b < 2; ++b) {
-                const float mk = b == 0 ? m1[0] : m2[0];
-                if (mk < 1.0e30f) {
-                    const uint32_t kk = static_cast<uint32_t>(mk);
-                    const int32_t d = pq + static_cast<int32_t>(kk >> 8) - 512;
-                    const uint64_t idx = static_cast<uint64_t>(n * kColsB + (kk & 255u));
-                    top2_insert_u64((static_cast<uint64_t>(d) << 32) | idx, k1, k2);
+                for (int k = 0; k < 5; ++k) t6[k] = fmin3(t16[3 * k], t16[3 * k + 1], t16[3 * k + 2]);
+                t6[5] = t16[15];
+                const float umin = fminf(fmin3(t6[0], t6[1], t6[2]), fmin3(t6[3], t6[4], t6[5]));
+                if (__any_sync(0xffffffffu, umin < thr)) {
+                    // two independent min / second-min chains (even and odd columns)
+                    float m1a = kInf, m2a = kInf, m1b = kInf, m2b = kInf;
+#pragma unroll
+                    for (int j = 0; j < kColsPerThread; j += 2) {
+                        const float ha = fmaxf(m1a, e[j]);
+                        m1a = fminf(m1a, e[j]);
+                        m2a = fminf(m2a, ha);
+                        const float hb = fmaxf(m1b, e[j + 1]);
+                        m1b = fminf(m1b, e[j + 1]);
+                        m2b = fminf(m2b, hb);
+                    }
+                    // combine the chains (keys are unique): (a1,a2) + (b1,b2) -> (min, second min)
+                    const float lo = fminf(m1a, m1b), hi = fmaxf(m1a, m1b);
+                    const float m2 = fminf(hi, fminf(m2a, m2b)), m1 = lo;
+                    // the unit's two best (exact integers below 2^19) -> (distance << 32 | index) keys
+#pragma unroll
+                    for (int b = 0; b < 2; ++b) {
+                        const float mk = b == 0 ? m1 : m2;
+                        if (mk < 1.0e30f) {
+                            const uint32_t kk = static_cast<uint32_t>(mk);
+                            const int32_t d = pq + static_cast<int32_t>(kk >> 8) - 512;
+                            const uint64_t idx = static_cast<uint64_t>(n * kColsB + (kk & 255u));
+                            top2_insert_u64((static_cast<uint64_t>(d) << 32) | idx, k1, k2);
+                        }
+                    }
+                    // later units of this tile have larger train indices: a key there
+                    // enters the top two only with a distance below the second-best's
+                    if (k2 != kNoKey) thr = static_cast<float>((static_cast<int32_t>(k2 >> 32) - pq + 512) * 256);
                 }
             }
             if (it.last_of_tile(batch)) {
@@ -576,23 +661,15 @@ __global__ void match_merge_kernel(const __grid_constant__ MatchBatchT<NP> batch
     out[q] = final_match(k1, k2, P.k, P.r_milli);
 }
 
-// Bits -> E4M3 0/1 bytes (bit t of a descriptor -> byte t) and per-descriptor popcount.
+// Bits -> E2M1 0/1 values (bit t of a descriptor -> 4-bit value t, kExpRowBytes per
+// row) and per-descriptor popcount; one thread per 32-bit descriptor word.
 __global__ void expand_kernel(const uint32_t* __restrict__ in, int64_t nwords, uint4* __restrict__ out,
                               int32_t* __restrict__ pop) {
     griddep_wait();
     griddep_launch_dependents();
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     const uint32_t w = i < nwords ? in[i] : 0u;
-    uint32_t o[8];
-#pragma unroll
-    for (int b = 0; b < 8; ++b) {
-        const uint32_t nib = (w >> (4 * b)) & 15u;
-        o[b] = ((nib * 0x00204081u) & 0x01010101u) * 0x38u;  // E4M3 1.0 = 0x38
-    }
-    if (i < nwords) {
-        out[2 * i] = make_uint4(o[0], o[1], o[2], o[3]);
-        out[2 * i + 1] = make_uint4(o[4], o[5], o[6], o[7]);
-    }
+    if (i < nwords) out[i] = expand_word_e2m1(w);
     int p = __popc(w);
     p += __shfl_xor_sync(0xffffffffu, p, 8);
     p += __shfl_xor_sync(0xffffffffu, p, 4);
@@ -618,12 +695,12 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-bool make_map(CUtensorMap* map, const void* base, int64_t rows) {
+bool make_map(CUtensorMap* map, const void* base, int64_t rows, int box_rows) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return false;
     cuuint64_t dims[2] = {static_cast<cuuint64_t>(kKBytes), static_cast<cuuint64_t>(rows)};
     cuuint64_t strides[1] = {static_cast<cuuint64_t>(kKBytes)};
-    cuuint32_t box[2] = {static_cast<cuuint32_t>(kChunk), static_cast<cuuint32_t>(kRowsA)};
+    cuuint32_t box[2] = {static_cast<cuuint32_t>(kChunk), static_cast<cuuint32_t>(box_rows)};
     cuuint32_t estr[2] = {1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -710,7 +787,8 @@ static cudaError_t set_match_attributes() {
 }
 
 template <int NP>
-static cudaError_t launch_match_np(const MatchBatch& full, const CUtensorMap& map, const int32_t* pop,
+static cudaError_t launch_match_np(const MatchBatch& full, const CUtensorMap& mapq, const CUtensorMap& mapt,
+                                   const int32_t* pop,
                                    uint64_t* partials, int32_t* tile_cnt, latch_match* out, uint32_t* flags,
                                    cudaStream_t stream) {
     static unsigned long long attr_done = 0;
@@ -724,7 +802,7 @@ static cudaError_t launch_match_np(const MatchBatch& full, const CUtensorMap& ma
     cudaError_t e = cudaSuccess;
     if (b->units > 0)
         e = launch_chained(match_tc_kernel<NP>, dim3(static_cast<unsigned>(b->grid)), dim3(kThreads), kSmemBytes,
-                           stream, map, *b, pop, partials, tile_cnt, out, flags);
+                           stream, mapq, mapt, *b, pop, partials, tile_cnt, out, flags);
     if (e == cudaSuccess && !tile_cnt && b->queries > 0) {
         const int threads = 256;
         const int64_t grid = (b->queries + threads - 1) / threads;
@@ -739,17 +817,18 @@ cudaError_t launch_match_tc_rows(const MatchBatch& b, const uint8_t* exp, int64_
                                  uint64_t* partials, int32_t* tile_cnt, latch_match* out, uint32_t* flags,
                                  cudaStream_t stream) {
     if (b.queries == 0) return cudaSuccess;
-    CUtensorMap map;
-    if (b.units > 0 && !make_map(&map, exp, rows)) return cudaErrorInvalidValue;
+    CUtensorMap mapq, mapt;
+    if (b.units > 0 && !(make_map(&mapq, exp, rows, kRowsA) && make_map(&mapt, exp, rows, kColsB)))
+        return cudaErrorInvalidValue;
     // the matcher combines each query tile's records itself unless some problem has
     // queries but no train rows (its tiles have no unit, so no block visits them)
     bool fused = b.units > 0 && tile_cnt != nullptr;
     for (int i = 0; i < b.count; ++i)
         if (b.p[i].nq > 0 && b.p[i].ntl == 0) fused = false;
     if (!fused) tile_cnt = nullptr;
-    if (b.count <= 1) return launch_match_np<1>(b, map, pop, partials, tile_cnt, out, flags, stream);
-    if (b.count <= 16) return launch_match_np<16>(b, map, pop, partials, tile_cnt, out, flags, stream);
-    return launch_match_np<kMaxProblems>(b, map, pop, partials, tile_cnt, out, flags, stream);
+    if (b.count <= 1) return launch_match_np<1>(b, mapq, mapt, pop, partials, tile_cnt, out, flags, stream);
+    if (b.count <= 16) return launch_match_np<16>(b, mapq, mapt, pop, partials, tile_cnt, out, flags, stream);
+    return launch_match_np<kMaxProblems>(b, mapq, mapt, pop, partials, tile_cnt, out, flags, stream);
 }
 
 // Scratch: expanded rows (rows x 512 B), popcounts, partial records.  The expanded
@@ -880,7 +959,7 @@ extern "C" latch_status hamming_match_noalloc(const uint8_t* d_query, int32_t nq
     const size_t need = match_tc_scratch_bytes_sms(sms, nq, nt) + kStaticFlagBytes;
     if (need > kStaticScratchBytes)
         return fail(nullptr, LATCH_EINVAL,
-                    "nq = %d, nt = %d needs %zu bytes of scratch; the static scratch holds %zu (about 30,000 "
+                    "nq = %d, nt = %d needs %zu bytes of scratch; the static scratch holds %zu (about 60,000 "
                     "descriptors in total)",
                     nq, nt, need, kStaticScratchBytes);
     void* base = nullptr;

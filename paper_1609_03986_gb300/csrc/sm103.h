@@ -129,16 +129,29 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// D[tmem] (+)= A[smem] * B[smem]^T, 8-bit floats, fp32 accumulate.
-__device__ __forceinline__ void mma_f8f6f4(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
-                                           uint32_t accumulate) {
+// D[tmem] (+)= (A[smem] x scale_A) * (B[smem] x scale_B)^T with 4-bit E2M1 operands
+// (two per byte, K = 64 per instruction) and per-32-value block scales read from TMEM
+// (sfa / sfb: TMEM addresses of the scale columns), fp32 accumulate.
+__device__ __forceinline__ void mma_mxf4(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                         uint32_t sfa, uint32_t sfb, uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        "setp.ne.b32 p, %6, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%5], p;\n\t}" ::"r"(
+            d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(sfa), "r"(sfb), "r"(accumulate)
         : "memory");
 }
+
+// Stores `v` into 8 consecutive 32-bit TMEM columns of 32 lanes: thread i of the
+// warp writes lane (taddr.lane + i), columns taddr.col .. +7.
+__device__ __forceinline__ void tmem_st_32x32b_x8_same(uint32_t taddr, uint32_t v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr),
+                 "r"(v)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // Arrive on `bar` once all previously issued tcgen05.mma of this thread complete.
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -187,12 +200,13 @@ __device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t addr) {
     return d;
 }
 
-// Instruction descriptor for kind::f8f6f4: A, B = E4M3, D = F32, both K-major.
-__host__ __device__ constexpr uint32_t idesc_e4m3_f32(int m, int n) {
-    return (1u << 4)                                   // D format F32
-           | (0u << 7) | (0u << 10)                    // A, B = E4M3
+// Instruction descriptor for kind::mxf4 (block-scaled): A, B = E2M1, scales UE8M0,
+// D = F32, both K-major, scale-factor byte ids 0.
+__host__ __device__ constexpr uint32_t idesc_mxf4_e2m1(int m, int n) {
+    return (1u << 7) | (1u << 10)                       // A, B = E2M1
            | (static_cast<uint32_t>(n >> 3) << 17)     // N / 8
-           | (static_cast<uint32_t>(m >> 4) << 24);    // M / 16
+           | (1u << 23)                                // scale factors UE8M0
+           | (static_cast<uint32_t>(m >> 4) << 24);    // M / 16 (bit 27 for M = 128)
 }
 
 }  // namespace sm103

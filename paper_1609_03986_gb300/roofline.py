@@ -16,10 +16,10 @@ Ceilings:
                pipe (one POPC per word) and the logic pipe (carry-save adders, which
                fold words with LOP3 and leave fewer POPC), from the measured rates of
                both pipes (`popc_pair_ceiling`).
-  tensor       8-bit float: the measured dense bf16 GEMM throughput x 2
-               (the nominal fp8 / bf16 ratio; the measured tcgen05 issue rates of
-               both kinds confirm the ratio), burst for a kernel timed alone and
-               sustained for one timed inside a long step.
+  tensor       4-bit float (E2M1): the measured dense bf16 GEMM throughput
+               x 6 (the nominal dense fp4 / bf16 ratio), burst for a kernel timed
+               alone and sustained for one timed inside a long step; beside it the
+               measured issue rate of the block-scaled E2M1 MMA (4x bf16 per clock).
 Per-clock pipe rates come from a throughput probe on this GPU, stored in
 ``pipe_rates.json``; the clocks and the bf16 / HBM figures from the driver's
 measured-peaks file.
@@ -33,6 +33,9 @@ import os
 EXTRACT_OPS_PER_DESC = 512 * 2 * 49 * 2
 EXTRACT_WEIGHTED_OPS_PER_DESC = 512 * 2 * 64 * 3
 EXTRACT_DP4A_PER_DESC = 512 * 4 * 49 // 4  # D1 - D2 as four 49-term u8 dot products, 4 multiply-adds per dp4a
+# dense per pixel and triplet: the product (C2 - C1)(2A - C1 - C2) (4 ops), its 7x7 box
+# sum by running sums along rows and columns (2 + 2 ops) and the comparison (1 op)
+DENSE_OPS_PER_PIXEL = 512 * 9
 POPC_WORDS_PER_PAIR = 16
 TENSOR_FLOP_PER_PAIR = 2 * 512
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -136,6 +139,27 @@ def extraction_weighted(ms: float, n_desc: int, workload: str, peaks_path: str):
     return _finish(r, f"{rk}; clock {pk} (measured-peaks file)")
 
 
+def dense_extraction(ms: float, pixels: int, workload: str, peaks_path: str):
+    """Dense descriptors: per pixel 512 triplets x 9 int32 ops of the box-sum form of
+    Eq. 1 (every pixel shares its neighbours' patch sums)."""
+    peaks, pk = _peaks(peaks_path)
+    rates, rk = pipe_rates()
+    clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    r = {"bound": "alu", "kernel": "dense_extract", "unit": "Tops/s (int32)", "units_per_launch": pixels,
+         "achieved": DENSE_OPS_PER_PIXEL * pixels / (ms / 1e3) / 1e12,
+         "peak": rates["per_sm_per_clock"]["iadd3"] * rates["sm_count"] * clk / 1e12,
+         "traffic": traffic("dense_extract", "dense.cu", workload)}
+    return _finish(r, f"{rk}; clock {pk} (measured-peaks file)")
+
+
+def dense_match(ms: float, pairs: float, workload: str, peaks_path: str):
+    """Windowed dense matching on the CUDA cores: the popc matcher's ceiling per pair."""
+    r = popc_match(ms, pairs, workload, peaks_path)
+    r["kernel"] = "dense_match"
+    r["traffic"] = traffic("dense_match", "dense.cu", workload)
+    return r
+
+
 def detection(ms: float, pixels: int, workload: str, peaks_path: str):
     """FAST detection: reads every pixel of the image once (1 byte) from HBM."""
     peaks, pk = _peaks(peaks_path)
@@ -146,12 +170,24 @@ def detection(ms: float, pixels: int, workload: str, peaks_path: str):
 
 
 def tensor_match(ms: float, pairs: float, workload: str, peaks_path: str, sustained: bool):
+    """Tensor matcher: 1,024 flop per pair on the block-scaled E2M1 MMA.  `peak` is
+    the measured bf16 GEMM x 6, the nominal dense fp4 / bf16 ratio (13.5 / 2.25
+    PFLOP/s); `issue_view` compares with the measured issue rate of the MMA form the
+    kernel uses (kind::mxf4, one CTA per MMA), 4x the bf16 rate per clock."""
     peaks, pk = _peaks(peaks_path)
+    rates, rk = pipe_rates()
     bf16 = float(peaks["bf16_tflops_sustained" if sustained else "bf16_tflops"])
-    r = {"bound": "tensor", "kernel": "match_tc", "unit": "TFLOP/s (fp8 e4m3)", "units_per_launch": pairs,
-         "achieved": TENSOR_FLOP_PER_PAIR * pairs / (ms / 1e3) / 1e12, "peak": 2.0 * bf16,
+    achieved = TENSOR_FLOP_PER_PAIR * pairs / (ms / 1e3) / 1e12
+    r = {"bound": "tensor", "kernel": "match_tc", "unit": "TFLOP/s (fp4 e2m1)", "units_per_launch": pairs,
+         "achieved": achieved, "peak": 6.0 * bf16,
          "traffic": traffic("match_tc", "match_tc.cu", workload)}
-    return _finish(r, f"{pk} bf16 {'sustained' if sustained else 'burst'} x 2 (nominal fp8/bf16)")
+    pr = rates["per_sm_per_clock"]
+    if "mma_mxf4_flop" in pr and "mma_bf16_flop" in pr:
+        ratio = pr["mma_mxf4_flop"] / pr["mma_bf16_flop"]
+        r["issue_view"] = {"peak": ratio * bf16, "frac": achieved / (ratio * bf16),
+                           "peak_model": f"bf16 {'sustained' if sustained else 'burst'} x {ratio:.2f}, the measured "
+                                         "kind::mxf4 / kind::f16 issue ratio"}
+    return _finish(r, f"{pk} bf16 {'sustained' if sustained else 'burst'} x 6 (nominal fp4/bf16)")
 
 
 def popc_match(ms: float, pairs: float, workload: str, peaks_path: str):

@@ -200,3 +200,63 @@ def test_oriented_pair_batched(gpu_ctx, oriented_pair_oracle):
     for i in range(2):
         assert np.array_equal(descs[i], descs_o[i]), i
     same_matches(matches[0], want)
+
+
+def test_graph_replay_with_new_inputs(gpu_ctx, triplets):
+    """latch_batch_run captured once in a CUDA graph and replayed on new images and
+    keypoints written into the same device buffers: each replay equals the oracle
+    on its own inputs (nothing of the capture-time inputs is baked into the graph)."""
+    sizes = [(500, 380), (500, 380), (640, 400)]
+    n = [1200, 900, 1500]
+    pairs = [(0, 1), (1, 2), (2, 0), (1, 1)]
+
+    def scene(s):
+        imgs = [synth.image(synth.seed(33, 10 * s + i, synth.KIND_IMAGE), w, h, pitch=640, n_ellipses=40)
+                for i, (w, h) in enumerate(sizes)]
+        kps = [synth.keypoints(synth.seed(33, 10 * s + i, synth.KIND_KEYPOINTS), w, h, c, 16, True, 3)
+               for i, ((w, h), c) in enumerate(zip(sizes, n))]
+        return imgs, kps
+
+    d_imgs = [torch.zeros((h, 640), dtype=torch.uint8, device="cuda") for _, h in sizes]
+    d_kps = torch.zeros((sum(n), 12), dtype=torch.uint8, device="cuda")
+    d_desc = torch.zeros((sum(n), 64), dtype=torch.uint8, device="cuda")
+    nout = sum(n[q] for q, _ in pairs)
+    d_m = torch.zeros((nout, 16), dtype=torch.uint8, device="cuda")
+    b = P.BatchDesc([(t, w, h, t.stride(0)) for t, (w, h) in zip(d_imgs, sizes)], n, d_kps, d_desc, pairs, 2, 0.8,
+                    d_m)
+    P.latch_reserve_batch(gpu_ctx.handle, b)
+    stream = torch.cuda.Stream()
+    off = np.concatenate([[0], np.cumsum(n)]).astype(np.int64)
+    mo = b.match_offsets()
+
+    def load(s):
+        imgs, kps = scene(s)
+        with torch.cuda.stream(stream):
+            for t, im in zip(d_imgs, imgs):
+                t.copy_(torch.from_numpy(im))
+            d_kps.copy_(torch.from_numpy(np.concatenate([P.pack_keypoints(k) for k in kps])))
+        return imgs, kps
+
+    with torch.cuda.stream(stream):
+        load(0)
+        P.latch_batch_run(gpu_ctx.handle, b, int(stream.cuda_stream))  # warm: kernel attributes, tensor maps
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            P.latch_batch_run(gpu_ctx.handle, b, int(stream.cuda_stream))
+    for s in (1, 2):
+        imgs, kps = load(s)
+        with torch.cuda.stream(stream):
+            d_m.zero_()
+            graph.replay()
+        torch.cuda.synchronize()
+        gpu_ctx.check()
+        wants = oracle_shards.extract_many([(im, w, h, k, triplets, synth.SCALES)
+                                            for im, (w, h), k in zip(imgs, sizes, kps)])
+        descs = d_desc.cpu().numpy()
+        for i in range(len(sizes)):
+            assert np.array_equal(descs[off[i]:off[i + 1]], wants[i]), (s, i)
+        recs = P.matches_from_bytes(d_m.cpu().numpy())
+        for p, (q, t) in enumerate(pairs):
+            _same(recs[mo[p]:mo[p + 1]], oracle.match(wants[q], wants[t], 2, 0.8))
+    del graph

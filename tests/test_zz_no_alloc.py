@@ -59,9 +59,9 @@ def test_noalloc_equals_allocating_path_twice():
 def test_noalloc_rejects_requests_beyond_its_array():
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
-    q = torch.zeros((20000, 64), dtype=torch.uint8, device="cuda")
-    out = torch.zeros((20000, 16), dtype=torch.uint8, device="cuda")
+    q = torch.zeros((40000, 64), dtype=torch.uint8, device="cuda")
+    out = torch.zeros((40000, 16), dtype=torch.uint8, device="cuda")
     with pytest.raises(P.LatchError) as e:
-        P.hamming_match_noalloc(q, 20000, q, 20000, 2, 0.8, out, 0)
+        P.hamming_match_noalloc(q, 40000, q, 40000, 2, 0.8, out, 0)
     assert e.value.status == 1
     assert "static scratch" in P.latch_last_error(None)

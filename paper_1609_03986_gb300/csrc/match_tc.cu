@@ -64,7 +64,7 @@ constexpr int kKBytes = kExpRowBytes;   // expanded descriptor: 512 x 4-bit
 constexpr int kChunk = 128;             // K bytes per swizzle atom / TMA box
 constexpr int kChunks = kKBytes / kChunk;
 constexpr int kMmaKBytes = 32;          // K bytes per MMA: 64 E2M1 values
-constexpr int kStages = kHalves == 2 ? 12 : 7;
+constexpr int kStages = kHalves == 2 ? 10 : 6;
 constexpr int kTileBytes = kRowsA * kChunk;   // 16 KB: a half tile's chunk of 128 rows x 128 B (one TMA box)
 constexpr int kStageBytes = kColsB * kChunk;  // 12 KB: a train chunk of 96 rows x 128 B (one TMA box)
 constexpr int kEpiWarps = 16;                       // epilogue: 4 lane quarters x 2 halves x 2 column groups
@@ -73,20 +73,26 @@ constexpr int kThreads = 128 + kEpiThreads;         // producer, MMA, TMEM, keys
 constexpr int kColGroups = kEpiWarps / (4 * kHalves);
 constexpr int kColsPerThread = kColsB / kColGroups;  // accumulator columns one epilogue thread scans
 constexpr int kLdCols = 16;                          // columns per tcgen05.ld (double-buffered)
-constexpr int kKeyStages = 4;                        // column-key vectors prepared ahead of the epilogue
+constexpr int kKeyStages = 4;                        // per-unit bias operands prepared ahead of the MMAs
+constexpr int kBiasK = 16;                           // K of the bias MMA (BF16)
+constexpr int kBiasRowBytes = kBiasK * 2;            // 32 B per bias row
+constexpr int kBiasABytes = kRowsA * kBiasRowBytes;  // 4 KB: the constant bias rows of A
+constexpr int kBiasBBytes = kColsB * kBiasRowBytes;  // one unit's bias rows of B
 constexpr int kTmemCols = 512;
 constexpr uint32_t kAccStride = 256;  // accumulator set b: half h at TMEM columns 256 b + 96 h, 96 wide
-constexpr uint32_t kSfaCol = 192;     // scale factors of A: 4 columns (128 rows)
-constexpr uint32_t kSfbCol = 224;     // scale factors of B: 4 columns per 128 rows
-constexpr uint32_t kScaleOne = 0x7F7F7F7Fu;  // four UE8M0 scale factors 2^0
+constexpr uint32_t kSfaCol = 192;     // scale factors of A: 4 columns (128 rows), 32 filled
+constexpr uint32_t kSfbCol = 224;     // scale factors of B: 4 columns per 128 rows, 32 filled
+constexpr uint32_t kScaleA = 0x88888888u;    // four UE8M0 scale factors 2^9: A x B = 512 dot
+constexpr uint32_t kScaleB = 0x7F7F7F7Fu;    // four UE8M0 scale factors 2^0
 constexpr uint32_t kIdesc = idesc_mxf4_e2m1(kRowsA, kColsB);
+constexpr uint32_t kIdescBias = idesc_bf16_f32(kRowsA, kColsB);
 static_assert(kHalves * kColsB <= kSfaCol && kSfbCol + 8 <= kAccStride, "TMEM columns overlap");
 static_assert(kColsPerThread == 3 * kLdCols, "epilogue: three 16-column loads per unit");
 
-// min(a, b, c) in one instruction.
-__device__ __forceinline__ float fmin3(float a, float b, float c) {
+// max(a, b, c) in one instruction.
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
     float d;
-    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
     return d;
 }
 
@@ -97,14 +103,16 @@ struct Smem {
     // offsets in the 1024-aligned dynamic buffer
     static constexpr int a = 0;                                        // [kHalves][kChunks] boxes of 16 KB
     static constexpr int b = a + kHalves * kChunks * kTileBytes;       // [kStages] chunks of 12 KB
-    static constexpr int cvec = b + kStages * kStageBytes;             // float [kKeyStages][kColsB]
-    static constexpr int part = cvec + kKeyStages * kColsB * 4;        // uint64 [kEpiThreads][2]
+    static constexpr int bias_a = b + kStages * kStageBytes;           // bias rows of A (4 KB)
+    static constexpr int bias_b = bias_a + kBiasABytes;                // [kKeyStages] bias rows of B
+    static constexpr int part = bias_b + kKeyStages * kBiasBBytes;     // uint64 [kEpiThreads][2]
     static constexpr int bars = part + kEpiThreads * 16;               // uint64 barriers
     static constexpr int nbars = 2 * kStages + 2 + 4 + 2 + 2 * kKeyStages;
     static constexpr int misc = bars + nbars * 8;                      // tmem base, abort flag, last-arrival flag
     static constexpr int total = misc + 16;
 };
 constexpr int kSmemBytes = Smem::total + 1024;
+static_assert(kSmemBytes <= 227 * 1024, "shared memory per block");
 
 // Walks the units of block c: for every problem in turn, the block's share of that
 // problem's U units, [start(c'), start(c' + 1)) with start(x) = floor(x U / G) and
@@ -271,7 +279,8 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* sA = smem + Smem::a;
     uint8_t* sB = smem + Smem::b;
-    float* sC = reinterpret_cast<float*>(smem + Smem::cvec);
+    uint8_t* sBiasA = smem + Smem::bias_a;
+    uint8_t* sBiasB = smem + Smem::bias_b;
     uint64_t* sPart = reinterpret_cast<uint64_t*>(smem + Smem::part);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Smem::bars);
     uint64_t* full = bars;
@@ -305,8 +314,8 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
         mbar_init(&mma_done[0], 1);
         mbar_init(&mma_done[1], 1);
         for (int i = 0; i < kKeyStages; ++i) {
-            mbar_init(&key_full[i], 32);
-            mbar_init(&key_empty[i], kEpiWarps);
+            mbar_init(&key_full[i], 32);  // the key warp's lanes
+            mbar_init(&key_empty[i], 1);  // the commit after the unit's bias MMA
         }
         *abort = 0;
         fence_mbar_init();
@@ -319,15 +328,31 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
         tmem_alloc(tmem_slot, kTmemCols);
         tc_fence_before();
     }
+    // bias operands (BF16, K = 16, no swizzle: element (r, k) at (r / 8) 256 + (k / 8) 128 +
+    // (r % 8) 16 + (k % 8) 2): every row of A is (4096, 256, 1, 0, ...); B's rows are
+    // written per unit by the key warp, its elements 3..15 stay zero
+    for (int i = threadIdx.x; i < (kBiasABytes + kKeyStages * kBiasBBytes) / 16; i += kThreads) {
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (i < kBiasABytes / 16) {
+            const int r = (i >> 4) * 8 + (i & 7), chunk = (i >> 3) & 1;  // 16 chunks per 8-row group
+            if (chunk == 0 && r < kRowsA)
+                v = make_uint4((__float_as_uint(4096.0f) >> 16) | (__float_as_uint(256.0f) & 0xffff0000u),
+                               __float_as_uint(1.0f) >> 16, 0, 0);
+        }
+        reinterpret_cast<uint4*>(sBiasA)[i] = v;
+    }
+    fence_proxy_async_smem();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     if (warp >= 4 && warp < 8) {
-        // every block scale factor 2^0: the scale columns of all 128 lanes (warp w may
-        // address lane quarter w % 4)
-        const uint32_t base = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16) + kSfaCol;
+        // block scale factors: 2^9 for A, 2^0 for B, in the scale columns of all 128
+        // lanes (warp w may address lane quarter w % 4)
+        const uint32_t base = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16);
 #pragma unroll
-        for (uint32_t col = 0; col < kAccStride - kSfaCol; col += 8) tmem_st_32x32b_x8_same(base + col, kScaleOne);
+        for (uint32_t col = kSfaCol; col < kSfbCol; col += 8) tmem_st_32x32b_x8_same(base + col, kScaleA);
+#pragma unroll
+        for (uint32_t col = kSfbCol; col < kAccStride; col += 8) tmem_st_32x32b_x8_same(base + col, kScaleB);
         tmem_st_wait();
     }
     tc_fence_before();
@@ -415,6 +440,8 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
             const uint64_t b_desc0 = umma_desc_sw128(smem_u32(sB));
             const uint32_t sfa = tmem + kSfaCol, sfb = tmem + kSfbCol;
             const uint32_t d0 = tmem + static_cast<uint32_t>(mine) * kAccStride;
+            const uint64_t bias_a_desc = umma_desc_noswizzle(smem_u32(sBiasA), 128, 256);
+            const uint64_t bias_b_desc0 = umma_desc_noswizzle(smem_u32(sBiasB), 128, 256);
             for (; !it.done(batch) && !*abort; ++i, it.next(batch, c)) {
                 const int64_t g = it.g(batch);
                 if (g != prev_g) {
@@ -425,7 +452,15 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                 if ((i & 1) == mine) {
                     if (!mbar_wait(&acc_empty[mine], acc_par ^ 1, abort)) break;
                     acc_par ^= 1;
+                    const int kslot = i % kKeyStages;
+                    if (!mbar_wait(&key_full[kslot], static_cast<uint32_t>(i / kKeyStages) & 1u, abort)) break;
                     tc_fence_after();
+                    // D = -key(column) in every row, then the fp4 MMAs add 512 dot
+#pragma unroll
+                    for (int h = 0; h < kHalves; ++h)
+                        mma_bf16(d0 + static_cast<uint32_t>(h * kColsB), bias_a_desc,
+                                 bias_b_desc0 + static_cast<uint64_t>((kslot * kBiasBBytes) >> 4), kIdescBias, 0);
+                    mma_commit(&key_empty[kslot]);
                     bool ok = true;
                     for (int kc = 0; kc < kChunks; ++kc) {
                         if (!mbar_wait(&full[stage], ring, abort)) {
@@ -441,8 +476,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                             for (int h = 0; h < kHalves; ++h)
                                 mma_mxf4(d0 + static_cast<uint32_t>(h * kColsB),
                                          ad + static_cast<uint64_t>((h * kChunks * kTileBytes + ks * kMmaKBytes) >> 4),
-                                         bd + static_cast<uint64_t>((ks * kMmaKBytes) >> 4), kIdesc, sfa, sfb,
-                                         (kc | ks) != 0);
+                                         bd + static_cast<uint64_t>((ks * kMmaKBytes) >> 4), kIdesc, sfa, sfb, 1);
                         mma_commit(&empty[stage]);
                         if (++stage == kStages) {
                             stage = 0;
@@ -468,23 +502,59 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
             }
         }
     } else if (warp == 3) {
-        // ---------------- column keys: for each unit, key(column j) = (popc(train
-        // row) + 512) << 8 | j, or +inf past the train set, into a ring of
-        // kKeyStages vectors, so that the epilogue never waits on these loads ----------------
+        // ---------------- bias rows: for each unit, row j of B's bias operand is
+        // (-hi, -lo, -j, 0, ...) in BF16 with 16 hi + lo = popc(train row) + 512, so that
+        // the bias MMA sets column j of every accumulator row to -key(j), key(j) =
+        // (popc(train row) + 512) << 8 | j; past the train set (-65536, 0, ...) puts the
+        // column below every key.  Two units at a time: the popcounts of both are
+        // loaded before either is written, so one load latency serves two units ----------------
+        constexpr int kRowsPerLane = kColsB / 32;
         UnitIter it;
         it.init(batch, c);
-        for (int64_t i = 0; !it.done(batch); ++i, it.next(batch, c)) {
-            const int slot = static_cast<int>(i % kKeyStages);
-            const uint32_t par = static_cast<uint32_t>(i / kKeyStages) & 1u;
-            if (!mbar_wait(&key_empty[slot], par ^ 1, abort)) break;
-            float* kv = sC + slot * kColsB;
+        auto load = [&](const UnitIter& u, int (&pv)[kRowsPerLane]) {
 #pragma unroll
-            for (int j = lane; j < kColsB; j += 32) {
-                const int64_t col = static_cast<int64_t>(it.n) * kColsB + j;
-                kv[j] = col < it.nt ? static_cast<float>((pop[it.t_row0 + col] + 512) * 256 + j)
-                                    : __int_as_float(0x7f800000);
+            for (int q = 0; q < kRowsPerLane; ++q) {
+                const int64_t col = static_cast<int64_t>(u.n) * kColsB + lane + 32 * q;
+                pv[q] = col < u.nt ? __ldg(pop + u.t_row0 + col) : -1;
             }
-            mbar_arrive(&key_full[slot]);  // each lane releases its own stores
+        };
+        auto bf16_bits = [](int v) { return __float_as_uint(static_cast<float>(v)) >> 16; };
+        bool ok = true;
+        for (int64_t i = 0; ok && !it.done(batch); i += 2) {
+            int pv0[kRowsPerLane], pv1[kRowsPerLane];
+            UnitIter it1 = it;
+            it1.next(batch, c);
+            const bool two = !it1.done(batch);
+            load(it, pv0);
+            if (two) load(it1, pv1);
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                if (u == 1 && !two) break;
+                const int64_t k = i + u;
+                const int slot = static_cast<int>(k % kKeyStages);
+                if (!mbar_wait(&key_empty[slot], (static_cast<uint32_t>(k / kKeyStages) & 1u) ^ 1u, abort)) {
+                    ok = false;
+                    break;
+                }
+                uint8_t* rows = sBiasB + slot * kBiasBBytes;
+#pragma unroll
+                for (int q = 0; q < kRowsPerLane; ++q) {
+                    const int j = lane + 32 * q;
+                    const int pt = u == 0 ? pv0[q] : pv1[q];
+                    uint4 v;
+                    if (pt >= 0) {
+                        const int hk = pt + 512;
+                        v = make_uint4(bf16_bits(-(hk >> 4)) | (bf16_bits(-(hk & 15)) << 16), bf16_bits(-j), 0, 0);
+                    } else {
+                        v = make_uint4(bf16_bits(-65536), 0, 0, 0);
+                    }
+                    *reinterpret_cast<uint4*>(rows + (j >> 3) * 256 + (j & 7) * 16) = v;
+                }
+                fence_proxy_async_smem();
+                mbar_arrive(&key_full[slot]);  // each lane releases its own stores
+            }
+            it = it1;
+            if (two) it.next(batch, c);
         }
     } else if (warp >= 4) {
         // ---------------- epilogue: kEpiWarps warps; thread = one query row x one
@@ -494,13 +564,14 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
         const int half = ((warp - 4) >> 2) % kHalves;  // 128-row half of the query tile
         const int cg = ((warp - 4) >> 2) / kHalves;    // column group [cg * kColsPerThread, +kColsPerThread)
         const int row_in_tile = half * kRowsA + quarter * 32 + lane;
-        const float kInf = __int_as_float(0x7f800000);
+        const float kNegInf = __int_as_float(0xff800000);
         UnitIter it;
         it.init(batch, c);
         uint32_t acc_par[2] = {0, 0};
         uint64_t k1 = kNoKey, k2 = kNoKey;
         int32_t pq = 0;
-        float thr = kInf;  // unit keys below this can still enter the row's top two
+        // accumulator values (-key) above this can still enter the row's top two
+        float thr = kNegInf;
         bool aborted = false;  // warp-uniform
         int64_t prev_g = -1;
         int i = 0;
@@ -513,25 +584,20 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                 const int64_t row = m * kRowsQ + row_in_tile;
                 pq = row < P.nq ? pop[P.q_row0 + row] : 0;
                 k1 = k2 = kNoKey;
-                thr = kInf;
+                thr = kNegInf;
                 prev_g = g;
             }
-            const int slot = i % kKeyStages;
-            const uint32_t kpar = static_cast<uint32_t>(i / kKeyStages) & 1u;
             // after a failed wait a warp keeps walking the units without work, so that
             // every warp reaches the barriers at the ends of query tiles
-            if (!aborted)
-                aborted = !__all_sync(0xffffffffu, mbar_wait(&acc_full[buf], acc_par[buf], abort) &&
-                                                       mbar_wait(&key_full[slot], kpar, abort));
+            if (!aborted) aborted = !__all_sync(0xffffffffu, mbar_wait(&acc_full[buf], acc_par[buf], abort));
             if (!aborted) {
                 acc_par[buf] ^= 1;
                 tc_fence_after();
-                const float* cv = sC + slot * kColsB + cg * kColsPerThread;
                 const uint32_t base = tmem + (static_cast<uint32_t>(quarter * 32) << 16) +
                                       static_cast<uint32_t>(buf) * kAccStride +
                                       static_cast<uint32_t>(half * kColsB + cg * kColsPerThread);
-                // the thread's columns in one round trip; the accumulator is free again as
-                // soon as they are in registers
+                // the thread's columns (512 dot - key, exact integers) in one round trip;
+                // the accumulator is free again as soon as they are in registers
                 uint32_t va[kLdCols], vb[kLdCols], vc[kLdCols];
                 tmem_ld_32x32b_x16(base, va);
                 tmem_ld_32x32b_x16(base + kLdCols, vb);
@@ -542,55 +608,50 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                 if (lane == 0) mbar_arrive(&acc_empty[buf]);
                 float e[kColsPerThread];
 #pragma unroll
-                for (int j = 0; j < kColsPerThread; j += 4) {
-                    const uint32_t* v = j < kLdCols ? va : (j < 2 * kLdCols ? vb : vc);
-                    const int jj = j % kLdCols;
-                    const float4 cc = *reinterpret_cast<const float4*>(cv + j);
-                    e[j + 0] = fmaf(__uint_as_float(v[jj + 0]), -512.0f, cc.x);
-                    e[j + 1] = fmaf(__uint_as_float(v[jj + 1]), -512.0f, cc.y);
-                    e[j + 2] = fmaf(__uint_as_float(v[jj + 2]), -512.0f, cc.z);
-                    e[j + 3] = fmaf(__uint_as_float(v[jj + 3]), -512.0f, cc.w);
+                for (int j = 0; j < kLdCols; ++j) {
+                    e[j] = __uint_as_float(va[j]);
+                    e[kLdCols + j] = __uint_as_float(vb[j]);
+                    e[2 * kLdCols + j] = __uint_as_float(vc[j]);
                 }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&key_empty[slot]);
-                // the unit's minimum (a tree of 3-input mins); only a unit that reaches
-                // below the row's running second-best takes the top-two update
+                // the unit's largest value (a tree of 3-input maxima); only a unit that
+                // reaches above the row's running threshold takes the top-two update
                 float t16[16], t6[6];
 #pragma unroll
-                for (int k = 0; k < 16; ++k) t16[k] = fmin3(e[3 * k], e[3 * k + 1], e[3 * k + 2]);
+                for (int k = 0; k < 16; ++k) t16[k] = fmax3(e[3 * k], e[3 * k + 1], e[3 * k + 2]);
 #pragma unroll
-                for (int k = 0; k < 5; ++k) t6[k] = fmin3(t16[3 * k], t16[3 * k + 1], t16[3 * k + 2]);
+                for (int k = 0; k < 5; ++k) t6[k] = fmax3(t16[3 * k], t16[3 * k + 1], t16[3 * k + 2]);
                 t6[5] = t16[15];
-                const float umin = fminf(fmin3(t6[0], t6[1], t6[2]), fmin3(t6[3], t6[4], t6[5]));
-                if (__any_sync(0xffffffffu, umin < thr)) {
-                    // two independent min / second-min chains (even and odd columns)
-                    float m1a = kInf, m2a = kInf, m1b = kInf, m2b = kInf;
+                const float umax = fmaxf(fmax3(t6[0], t6[1], t6[2]), fmax3(t6[3], t6[4], t6[5]));
+                if (__any_sync(0xffffffffu, umax > thr)) {
+                    // two independent max / second-max chains (even and odd columns)
+                    float m1a = kNegInf, m2a = kNegInf, m1b = kNegInf, m2b = kNegInf;
 #pragma unroll
                     for (int j = 0; j < kColsPerThread; j += 2) {
-                        const float ha = fmaxf(m1a, e[j]);
-                        m1a = fminf(m1a, e[j]);
-                        m2a = fminf(m2a, ha);
-                        const float hb = fmaxf(m1b, e[j + 1]);
-                        m1b = fminf(m1b, e[j + 1]);
-                        m2b = fminf(m2b, hb);
+                        const float la = fminf(m1a, e[j]);
+                        m1a = fmaxf(m1a, e[j]);
+                        m2a = fmaxf(m2a, la);
+                        const float lb = fminf(m1b, e[j + 1]);
+                        m1b = fmaxf(m1b, e[j + 1]);
+                        m2b = fmaxf(m2b, lb);
                     }
-                    // combine the chains (keys are unique): (a1,a2) + (b1,b2) -> (min, second min)
-                    const float lo = fminf(m1a, m1b), hi = fmaxf(m1a, m1b);
-                    const float m2 = fminf(hi, fminf(m2a, m2b)), m1 = lo;
-                    // the unit's two best (exact integers below 2^19) -> (distance << 32 | index) keys
+                    // combine the chains (values are unique): (a1,a2) + (b1,b2) -> (max, second max)
+                    const float hi = fmaxf(m1a, m1b), lo = fminf(m1a, m1b);
+                    const float m2 = fmaxf(lo, fmaxf(m2a, m2b)), m1 = hi;
+                    // the unit's two best -> (distance << 32 | index) keys; values at or
+                    // below -2^20 are columns past the train set
 #pragma unroll
                     for (int b = 0; b < 2; ++b) {
-                        const float mk = b == 0 ? m1 : m2;
-                        if (mk < 1.0e30f) {
-                            const uint32_t kk = static_cast<uint32_t>(mk);
+                        const float mv = b == 0 ? m1 : m2;
+                        if (mv > -1048576.0f) {
+                            const uint32_t kk = static_cast<uint32_t>(-mv);
                             const int32_t d = pq + static_cast<int32_t>(kk >> 8) - 512;
                             const uint64_t idx = static_cast<uint64_t>(n * kColsB + (kk & 255u));
                             top2_insert_u64((static_cast<uint64_t>(d) << 32) | idx, k1, k2);
                         }
                     }
-                    // later units of this tile have larger train indices: a key there
+                    // later units of this tile have larger train indices: a column there
                     // enters the top two only with a distance below the second-best's
-                    if (k2 != kNoKey) thr = static_cast<float>((static_cast<int32_t>(k2 >> 32) - pq + 512) * 256);
+                    if (k2 != kNoKey) thr = -static_cast<float>((static_cast<int32_t>(k2 >> 32) - pq + 512) * 256);
                 }
             }
             if (it.last_of_tile(batch)) {

@@ -143,6 +143,33 @@ __device__ __forceinline__ void mma_mxf4(uint32_t d_tmem, uint64_t a_desc, uint6
         : "memory");
 }
 
+// D[tmem] (+)= A[smem] * B[smem]^T, BF16 operands, fp32 accumulate.
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Shared-memory descriptor: K-major operand without swizzle, core matrices of 8 rows
+// x 16 bytes (128 contiguous bytes); `lbo` bytes between core matrices along K,
+// `sbo` bytes between 8-row groups.
+__device__ __forceinline__ uint64_t umma_desc_noswizzle(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((addr & 0x3FFFFu) >> 4);
+    d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16;
+    d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32;
+    d |= static_cast<uint64_t>(1) << 46;  // descriptor version (sm_100 family); layout type 0: no swizzle
+    return d;
+}
+
+// Makes this thread's generic-proxy shared-memory writes visible to the async proxy
+// (tensor-core operand reads, TMA).
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 // Stores `v` into 8 consecutive 32-bit TMEM columns of 32 lanes: thread i of the
 // warp writes lane (taddr.lane + i), columns taddr.col .. +7.
 __device__ __forceinline__ void tmem_st_32x32b_x8_same(uint32_t taddr, uint32_t v) {
@@ -198,6 +225,14 @@ __device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t addr) {
     d |= static_cast<uint64_t>(1) << 46;                  // descriptor version (sm_100 family)
     d |= static_cast<uint64_t>(2) << 61;                  // swizzle: 128 B
     return d;
+}
+
+// Instruction descriptor for kind::f16: A, B = BF16, D = F32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int m, int n) {
+    return (1u << 4)                                   // D format F32
+           | (1u << 7) | (1u << 10)                    // A, B = BF16
+           | (static_cast<uint32_t>(n >> 3) << 17)     // N / 8
+           | (static_cast<uint32_t>(m >> 4) << 24);    // M / 16
 }
 
 // Instruction descriptor for kind::mxf4 (block-scaled): A, B = E2M1, scales UE8M0,

@@ -207,6 +207,38 @@ struct UnitIter {
     }
 };
 
+// The block's walk as runs: a run is the consecutive units of one query tile (a run
+// ends where its tile or its share ends, so consecutive runs are different tiles).
+// The MMA issuers step through runs and count units inside them, which keeps the
+// iterator off their per-unit path.
+struct RunIter {
+    UnitIter u;     // at the run's first unit
+    int32_t len;    // units in the run
+    template <class B>
+    __device__ __forceinline__ void init(const B& b, int64_t c) {
+        u.init(b, c);
+        set(b);
+    }
+    template <class B>
+    __device__ __forceinline__ void set(const B& b) {
+        const int64_t rest = static_cast<int64_t>(u.ntl - u.n);
+        len = u.done(b) ? 0 : static_cast<int32_t>(u.left < rest ? u.left : rest);
+    }
+    template <class B>
+    __device__ __forceinline__ bool done(const B& b) const { return u.done(b); }
+    template <class B>
+    __device__ __forceinline__ void next(const B& b, int64_t c) {
+        if (len == u.left) {
+            u.take(b, u.p + 1, c);  // the share ends with this run
+        } else {
+            u.left -= len;          // the run ends with its tile
+            ++u.m;
+            u.n = 0;
+        }
+        set(b);
+    }
+};
+
 // Calls f(c') for the share index of every block that holds a record of query tile
 // m of problem P, and returns how many there are.  With U >= G every share is
 // non-empty and the owners are the contiguous range from the share of the tile's
@@ -369,9 +401,9 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
             it.init(batch, c);
             int stage = 0;
             uint32_t ring = 0, a_par = 0;
-            uint32_t fill_par[kStages];
-            bool filled[kStages];
-            for (int s = 0; s < kStages; ++s) filled[s] = false, fill_par[s] = 0;
+            // bit s: stage s has a copy issued / the parity of its latest fill (bit masks
+            // rather than arrays, which a run-time index would put in local memory)
+            uint32_t filled = 0, fill_par = 0;
             int64_t prev_g = -1;
             for (; !it.done(batch); it.next(batch, c)) {
                 const MatchProblem& P = batch.p[it.p];
@@ -398,8 +430,8 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                     mbar_arrive_expect_tx(&full[stage], kStageBytes);
                     tma_load_2d(sB + stage * kStageBytes, &tmt, kc * kChunk, static_cast<int32_t>(it.t_row0 + n * kColsB),
                                 &full[stage]);
-                    filled[stage] = true;
-                    fill_par[stage] = ring;
+                    filled |= 1u << stage;
+                    fill_par = (fill_par & ~(1u << stage)) | (ring << stage);
                     if (++stage == kStages) {
                         stage = 0;
                         ring ^= 1;
@@ -411,7 +443,8 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                 // let copies still in flight land before the block exits (bounded)
                 const uint64_t t0 = globaltimer();
                 for (int s = 0; s < kStages; ++s)
-                    while (filled[s] && !mbar_try_wait(&full[s], fill_par[s]) && globaltimer() - t0 < 200000000ull) {
+                    while (((filled >> s) & 1u) && !mbar_try_wait(&full[s], (fill_par >> s) & 1u) &&
+                           globaltimer() - t0 < 200000000ull) {
                     }
                 if (prev_g >= 0)  // the last A load completes the a_full phase of parity a_par
                     while (!mbar_try_wait(a_full, a_par) && globaltimer() - t0 < 200000000ull) {
@@ -427,12 +460,9 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
         // query tile and commit a_empty (count 2) at every tile's end. ----------------
         if (lane == 0) {
             const int mine = warp - 1;
-            UnitIter it;
-            it.init(batch, c);
-            int stage = 0;
-            uint32_t ring = 0, a_par = 0, acc_par = 0;
-            int64_t prev_g = -1;
-            int i = 0;
+            RunIter run;
+            run.init(batch, c);
+            uint32_t a_par = 0, acc_par = 0;
             // shared-memory descriptors of the first query box and train chunk; the others
             // differ only in the start-address field (bits 0-13: address / 16), so each MMA
             // adds a constant to them
@@ -442,18 +472,23 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
             const uint32_t d0 = tmem + static_cast<uint32_t>(mine) * kAccStride;
             const uint64_t bias_a_desc = umma_desc_noswizzle(smem_u32(sBiasA), 128, 256);
             const uint64_t bias_b_desc0 = umma_desc_noswizzle(smem_u32(sBiasB), 128, 256);
-            for (; !it.done(batch) && !*abort; ++i, it.next(batch, c)) {
-                const int64_t g = it.g(batch);
-                if (g != prev_g) {
-                    if (!mbar_wait(a_full, a_par, abort)) break;
-                    a_par ^= 1;
-                    prev_g = g;
-                }
-                if ((i & 1) == mine) {
-                    if (!mbar_wait(&acc_empty[mine], acc_par ^ 1, abort)) break;
+            int i = 0;  // the run's first unit in the block's walk
+            bool ok = true;
+            for (; ok && !run.done(batch); run.next(batch, c)) {
+                if (!mbar_wait(a_full, a_par, abort)) break;  // every run is a new query tile
+                a_par ^= 1;
+                const int end = i + run.len;
+                for (int j = i + ((i & 1) ^ mine); ok && j < end; j += 2) {
+                    if (!mbar_wait(&acc_empty[mine], acc_par ^ 1, abort)) {
+                        ok = false;
+                        break;
+                    }
                     acc_par ^= 1;
-                    const int kslot = i % kKeyStages;
-                    if (!mbar_wait(&key_full[kslot], static_cast<uint32_t>(i / kKeyStages) & 1u, abort)) break;
+                    const int kslot = j % kKeyStages;
+                    if (!mbar_wait(&key_full[kslot], static_cast<uint32_t>(j / kKeyStages) & 1u, abort)) {
+                        ok = false;
+                        break;
+                    }
                     tc_fence_after();
                     // D = -key(column) in every row, then the fp4 MMAs add 512 dot
 #pragma unroll
@@ -461,9 +496,12 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                         mma_bf16(d0 + static_cast<uint32_t>(h * kColsB), bias_a_desc,
                                  bias_b_desc0 + static_cast<uint64_t>((kslot * kBiasBBytes) >> 4), kIdescBias, 0);
                     mma_commit(&key_empty[kslot]);
-                    bool ok = true;
+                    // unit j reads ring positions 2 j and 2 j + 1
+#pragma unroll
                     for (int kc = 0; kc < kChunks; ++kc) {
-                        if (!mbar_wait(&full[stage], ring, abort)) {
+                        const int pos = kChunks * j + kc;
+                        const int stage = pos % kStages;
+                        if (!mbar_wait(&full[stage], static_cast<uint32_t>(pos / kStages) & 1u, abort)) {
                             ok = false;
                             break;
                         }
@@ -478,22 +516,11 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                                          ad + static_cast<uint64_t>((h * kChunks * kTileBytes + ks * kMmaKBytes) >> 4),
                                          bd + static_cast<uint64_t>((ks * kMmaKBytes) >> 4), kIdesc, sfa, sfb, 1);
                         mma_commit(&empty[stage]);
-                        if (++stage == kStages) {
-                            stage = 0;
-                            ring ^= 1;
-                        }
                     }
-                    if (!ok) break;
-                    mma_commit(&acc_full[mine]);
-                } else {
-                    // the other issuer's unit: its stages
-                    stage += kChunks;
-                    if (stage >= kStages) {
-                        stage -= kStages;
-                        ring ^= 1;
-                    }
+                    if (ok) mma_commit(&acc_full[mine]);
                 }
-                if (it.last_of_tile(batch)) mma_commit(a_empty);
+                i = end;
+                if (ok) mma_commit(a_empty);
             }
             // every issued MMA has finished before TMEM is released
             mma_commit(&mma_done[mine]);
@@ -567,7 +594,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
         const float kNegInf = __int_as_float(0xff800000);
         UnitIter it;
         it.init(batch, c);
-        uint32_t acc_par[2] = {0, 0};
+        uint32_t acc_par = 0;  // bit b: the phase parity of accumulator b
         uint64_t k1 = kNoKey, k2 = kNoKey;
         int32_t pq = 0;
         // accumulator values (-key) above this can still enter the row's top two
@@ -589,9 +616,9 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
             }
             // after a failed wait a warp keeps walking the units without work, so that
             // every warp reaches the barriers at the ends of query tiles
-            if (!aborted) aborted = !__all_sync(0xffffffffu, mbar_wait(&acc_full[buf], acc_par[buf], abort));
+            if (!aborted) aborted = !__all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (acc_par >> buf) & 1u, abort));
             if (!aborted) {
-                acc_par[buf] ^= 1;
+                acc_par ^= 1u << buf;
                 tc_fence_after();
                 const uint32_t base = tmem + (static_cast<uint32_t>(quarter * 32) << 16) +
                                       static_cast<uint32_t>(buf) * kAccStride +

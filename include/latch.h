@@ -351,7 +351,7 @@ typedef struct {
 } latch_session_stats;
 
 /* hbm_budget: device bytes the session may hold (arena of max_gallery_rows +
- * 2 x max_batch_kps expanded rows, the rest split between the two lanes; each lane
+ * lanes x max_batch_kps expanded rows, the rest split between the lanes; each lane
  * needs at least 64 MB).  The budget is clamped to the free device memory measured
  * at creation less 512 MiB, and the session reserves all of it then, so admission
  * (latch_submit, and the scheduler filling a lane) is against memory that is really
@@ -362,6 +362,11 @@ typedef struct {
  * wait gave up; results incomplete) or LATCH_EDEVICE. */
 latch_status latch_session_create(int device, size_t hbm_budget, int64_t max_gallery_rows, int32_t max_batch,
                                   int64_t max_batch_kps, const latch_triplet *h_triplets, latch_session **out);
+/* As latch_session_create with `lanes` (1..8) lanes instead of 2: micro-batches that
+ * run concurrently, each on its own stream with its own share of the budget. */
+latch_status latch_session_create_lanes(int device, size_t hbm_budget, int64_t max_gallery_rows, int32_t max_batch,
+                                        int64_t max_batch_kps, int32_t lanes, const latch_triplet *h_triplets,
+                                        latch_session **out);
 /* Stops the scheduler, waits for work in flight, frees everything. */
 latch_status latch_session_destroy(latch_session *s);
 /* Copy n packed descriptors (host) into a new resident gallery (synchronous). */

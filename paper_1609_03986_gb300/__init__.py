@@ -113,6 +113,8 @@ EXPORTS = [
     ("latch_batch_run_host", ctypes.c_int, [_P, ctypes.POINTER(latch_host_batch_desc), _P]),
     ("latch_session_create", ctypes.c_int, [ctypes.c_int, ctypes.c_size_t, _I64, _I32, _I64, _P,
                                             ctypes.POINTER(_P)]),
+    ("latch_session_create_lanes", ctypes.c_int, [ctypes.c_int, ctypes.c_size_t, _I64, _I32, _I64, _I32, _P,
+                                                  ctypes.POINTER(_P)]),
     ("latch_session_destroy", ctypes.c_int, [_P]),
     ("latch_gallery_add", ctypes.c_int, [_P, _P, _I32, ctypes.POINTER(_I32)]),
     ("latch_submit", ctypes.c_int, [_P, ctypes.POINTER(latch_request), ctypes.POINTER(ctypes.c_uint64)]),
@@ -344,14 +346,23 @@ def _scheck(sess, status: int):
 
 
 def latch_session_create(device: int, hbm_budget: int, max_gallery_rows: int, max_batch: int, max_batch_kps: int,
-                         triplets):
+                         triplets, lanes: int = 2):
     t = np.ascontiguousarray(triplets, dtype=np.uint8).reshape(-1)
     h = ctypes.c_void_p()
-    st = library().latch_session_create(device, hbm_budget, max_gallery_rows, max_batch, max_batch_kps,
-                                        t.ctypes.data, ctypes.byref(h))
+    if lanes == 2:  # the default lane count
+        st = library().latch_session_create(device, hbm_budget, max_gallery_rows, max_batch, max_batch_kps,
+                                            t.ctypes.data, ctypes.byref(h))
+    else:
+        st = library().latch_session_create_lanes(device, hbm_budget, max_gallery_rows, max_batch, max_batch_kps,
+                                                  lanes, t.ctypes.data, ctypes.byref(h))
     if st != 0:
         raise LatchError(st, "latch_session_create failed")
     return h
+
+
+def latch_session_create_lanes(device: int, hbm_budget: int, max_gallery_rows: int, max_batch: int,
+                               max_batch_kps: int, lanes: int, triplets):
+    return latch_session_create(device, hbm_budget, max_gallery_rows, max_batch, max_batch_kps, triplets, lanes)
 
 
 def latch_session_destroy(sess) -> None:
@@ -415,8 +426,9 @@ class Session:
     the session's host<->device copies fully asynchronous)."""
 
     def __init__(self, triplets, device: int = 0, hbm_budget: int = 8 << 30, max_gallery_rows: int = 1 << 22,
-                 max_batch: int = 16, max_batch_kps: int = 1 << 18):
-        self.handle = latch_session_create(device, hbm_budget, max_gallery_rows, max_batch, max_batch_kps, triplets)
+                 max_batch: int = 16, max_batch_kps: int = 1 << 18, lanes: int = 2):
+        self.handle = latch_session_create(device, hbm_budget, max_gallery_rows, max_batch, max_batch_kps, triplets,
+                                           lanes)
         self._live = {}
 
     def close(self):

@@ -2,7 +2,7 @@
 // sets ("galleries"), with continuous batching.
 //
 // Host side, one scheduler thread.  Requests wait in a FIFO.  Whenever one of the
-// session's two lanes is free, the scheduler takes requests from the head of the
+// session's lanes (2 by default, up to 8) is free, the scheduler takes requests from the head of the
 // queue for as long as they fit the lane (count, keypoints, and the lane's share of
 // the HBM budget -- admission by free device memory) and enqueues them on the
 // lane's stream as one micro-batch:
@@ -13,8 +13,8 @@
 //   galleries sit pre-expanded in the same arena, so one TMA map covers both),
 //   device -> host copies of the matches (and descriptors if asked for),
 //   a host callback that completes the batch's tickets.
-// The two lanes alternate, so a batch's copies and kernels overlap the other
-// lane's, and requests that arrive while a batch runs are admitted into the next
+// The lanes take turns, so a batch's copies and kernels overlap the other
+// lanes', and requests that arrive while a batch runs are admitted into the next
 // one as soon as a lane frees up.  Results are bit-identical to latch_extract +
 // hamming_match on each request alone.
 #include <algorithm>
@@ -34,7 +34,7 @@
 namespace latch {
 namespace {
 
-constexpr int kLanes = 2;
+constexpr int kMaxLanes = 8;
 constexpr int64_t kRowBytes = kExpRowBytes + 4;  // expanded row + popcount
 constexpr size_t kFreeMargin = size_t(512) << 20;  // device memory left free at session creation
 
@@ -83,14 +83,15 @@ struct latch_session {
     int64_t max_batch_kps = 0;
     size_t lane_bytes = 0;
     size_t budget = 0;  // device bytes the session holds: min(caller's budget, free memory - margin)
-    // arena: [gallery rows | lane 0 query rows | lane 1 query rows] x kExpRowBytes, then popcounts
+    // arena: [gallery rows | lane 0 query rows | lane 1 query rows | ...] x kExpRowBytes, then popcounts
     uint8_t* arena = nullptr;
     int32_t* arena_pop = nullptr;
     int64_t arena_rows = 0;
     int64_t gallery_cap = 0;
     int64_t gallery_used = 0;
     std::vector<latch::Gallery> galleries;
-    latch::Lane lanes[latch::kLanes];
+    int nlanes = 0;
+    latch::Lane lanes[latch::kMaxLanes];
     std::mutex mu;
     std::condition_variable cv_sched;  // scheduler: new work or a free lane
     std::condition_variable cv_done;   // waiters: a ticket completed
@@ -254,7 +255,7 @@ void scheduler(latch_session* s) {
         s->cv_sched.wait(lock, [&] {
             if (s->stop) return true;
             if (s->queue.empty()) return false;
-            for (int i = 0; i < kLanes; ++i)
+            for (int i = 0; i < s->nlanes; ++i)
                 if (!s->lanes[i].busy) {
                     li = i;
                     return true;
@@ -303,20 +304,28 @@ extern "C" {
 
 latch_status latch_session_create(int device, size_t hbm_budget, int64_t max_gallery_rows, int32_t max_batch,
                                   int64_t max_batch_kps, const latch_triplet* h_triplets, latch_session** out) {
+    return latch_session_create_lanes(device, hbm_budget, max_gallery_rows, max_batch, max_batch_kps, 2, h_triplets,
+                                      out);
+}
+
+latch_status latch_session_create_lanes(int device, size_t hbm_budget, int64_t max_gallery_rows, int32_t max_batch,
+                                        int64_t max_batch_kps, int32_t lanes, const latch_triplet* h_triplets,
+                                        latch_session** out) {
     if (!out || !h_triplets) return LATCH_EINVAL;
     *out = nullptr;
-    if (max_batch < 1 || max_batch > 64 || max_batch_kps < 1 || max_gallery_rows < 1 ||
-        max_gallery_rows + kLanes * max_batch_kps > INT32_MAX / 2)
+    if (lanes < 1 || lanes > kMaxLanes || max_batch < 1 || max_batch > 64 || max_batch_kps < 1 ||
+        max_gallery_rows < 1 || max_gallery_rows + lanes * max_batch_kps > INT32_MAX / 2)
         return LATCH_EINVAL;
     latch_session* s = new (std::nothrow) latch_session();
     if (!s) return LATCH_ENOMEM;
+    s->nlanes = lanes;
     s->t0 = std::chrono::steady_clock::now();
     latch_status st = latch_context_create(device, &s->ctx);
     if (st == LATCH_OK) st = latch_set_triplets(s->ctx, h_triplets);
     s->max_batch = max_batch;
     s->max_batch_kps = max_batch_kps;
     s->gallery_cap = max_gallery_rows;
-    s->arena_rows = max_gallery_rows + kLanes * max_batch_kps;
+    s->arena_rows = max_gallery_rows + lanes * max_batch_kps;
     const size_t arena_bytes = static_cast<size_t>(s->arena_rows) * kRowBytes + 4096;
     // admission by free device memory: the session never holds more than the device
     // has free when it is created, less a margin for the context's own tables and
@@ -329,15 +338,15 @@ latch_status latch_session_create(int device, size_t hbm_budget, int64_t max_gal
         s->stats.hbm_free = static_cast<int64_t>(free_b);
         s->stats.hbm_budget = static_cast<int64_t>(s->budget);
     }
-    if (st == LATCH_OK && (s->budget <= arena_bytes || (s->budget - arena_bytes) / kLanes < (size_t(64) << 20)))
-        st = LATCH_ENOMEM;  // budget (or free memory) too small for the arena plus two lanes of 64 MB
+    if (st == LATCH_OK && (s->budget <= arena_bytes || (s->budget - arena_bytes) / lanes < (size_t(64) << 20)))
+        st = LATCH_ENOMEM;  // budget (or free memory) too small for the arena plus lanes of 64 MB
     if (st == LATCH_OK) {
-        s->lane_bytes = (s->budget - arena_bytes) / kLanes / 256 * 256;
+        s->lane_bytes = (s->budget - arena_bytes) / lanes / 256 * 256;
         if (cudaMalloc(&s->arena, arena_bytes) != cudaSuccess) st = LATCH_ENOMEM;
     }
     if (st == LATCH_OK) {
         s->arena_pop = reinterpret_cast<int32_t*>(s->arena + round_up(static_cast<size_t>(s->arena_rows) * kExpRowBytes, 1024));
-        for (int i = 0; i < kLanes && st == LATCH_OK; ++i) {
+        for (int i = 0; i < lanes && st == LATCH_OK; ++i) {
             Lane& L = s->lanes[i];
             L.qrow0 = max_gallery_rows + i * max_batch_kps;
             L.done = DoneArg{s, i};

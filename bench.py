@@ -728,8 +728,12 @@ def _serve_inputs(args):
             pool[(si, j)] = (im, w, h, P.pinned_copy(P.pack_keypoints(kp)))
     gal_n = synth.batch_keypoint_counts(32, 10000, 200000, config=5)
     gals = [synth.random_descriptors(synth.seed(5, 1000 + g, synth.KIND_GALLERY), int(n)) for g, n in enumerate(gal_n)]
-    arr = synth.arrivals(synth.seed(5, 0, synth.KIND_ARRIVALS), args.rate, args.duration, len(sizes), 1000, 64000, 32)
-    return sizes, per_size, pool, gal_n, gals, arr
+    return sizes, per_size, pool, gal_n, gals
+
+
+def _serve_arrivals(rate, duration, n_sizes, stream=0):
+    from paper_1609_03986_gb300 import synth
+    return synth.arrivals(synth.seed(5, stream, synth.KIND_ARRIVALS), rate, duration, n_sizes, 1000, 64000, 32)
 
 
 def _latency_summary(lat_ms, first, last, ndesc, pairs, n_req):
@@ -770,28 +774,16 @@ def _drive(n_req, t_arr, submit, wait):
     return lat, first, last, bsz
 
 
-def bench_serve(args, local):
-    """The Poisson request stream through the session (continuous batching), then the
-    same stream through the plain per-request calls (upload, latch_extract,
-    hamming_match against the resident gallery, download; one request at a time in
-    arrival order)."""
-    import queue as _q
-    import torch
+def _serve_session(local, inputs, arr, lanes, name, sustained_roof=True):
+    """One request stream through a session with `lanes` lanes (continuous batching)."""
     import paper_1609_03986_gb300 as P
     from paper_1609_03986_gb300 import roofline, synth
-    dev = torch.device("cuda", local)
-    sizes, per_size, pool, gal_n, gals, (t_arr, size_i, kps_n, gal_i) = _serve_inputs(args)
+    sizes, per_size, pool, gal_n, gals = inputs
+    t_arr, size_i, kps_n, gal_i = arr
     n_req = len(t_arr)
     pairs = float(sum(int(kps_n[i]) * int(gal_n[gal_i[i]]) for i in range(n_req)))
-    ndesc_all = int(kps_n.sum())
-    name = f"serve_poisson_{args.rate:g}rps_{args.duration:g}s"
-    out = {"workload": name, "requests": n_req, "offered_rps": args.rate,
-           "request_mix": "640x480..4000x3000 images, 1k-64k oriented keypoints, 32 resident galleries of "
-                          "10k-200k descriptors"}
-
-    # ---- the session
     sess = P.Session(synth.triplets(), device=local, hbm_budget=12 << 30, max_gallery_rows=int(gal_n.sum()) + 1,
-                     max_batch=16, max_batch_kps=1 << 18)
+                     max_batch=16, max_batch_kps=1 << 18, lanes=lanes)
     for g in gals:
         sess.add_gallery(g)
     for i in range(8):
@@ -811,14 +803,28 @@ def bench_serve(args, local):
     clk = clocks.stop()
     st = sess.stats()
     sess.close()
-    rec = _latency_summary(lat, first, last, ndesc_all, pairs, n_req)
-    rec.update({"entry": "latch_session_* (continuous batching, 2 lanes)", "mean_batch": float(np.mean(bsz)),
-                "max_batch": int(np.max(bsz)), "stats": st, "clocks": clk})
-    rec["roofline"] = roofline.tensor_match((last - first) * 1e3, pairs, name, PEAKS, sustained=True)
-    rec["roofline"]["note"] = "pairs over the whole stream's span: a latency workload at this offered rate"
-    out["session"] = rec
+    rec = _latency_summary(lat, first, last, int(kps_n.sum()), pairs, n_req)
+    rec.update({"entry": f"latch_session_* (continuous batching, {lanes} lanes)", "lanes": lanes,
+                "mean_batch": float(np.mean(bsz)), "max_batch": int(np.max(bsz)), "stats": st, "clocks": clk})
+    if sustained_roof:
+        rec["roofline"] = roofline.tensor_match((last - first) * 1e3, pairs, name, PEAKS, sustained=True)
+        rec["roofline"]["note"] = "pairs over the whole stream's span: a latency workload at this offered rate"
+    return rec
 
-    # ---- the plain per-request calls, one request at a time
+
+def _serve_plain(local, inputs, arr):
+    """The same stream through the plain per-request calls (upload, latch_extract,
+    hamming_match against the resident gallery, download), one request at a time in
+    arrival order."""
+    import queue as _q
+    import torch
+    import paper_1609_03986_gb300 as P
+    from paper_1609_03986_gb300 import synth
+    dev = torch.device("cuda", local)
+    sizes, per_size, pool, gal_n, gals = inputs
+    t_arr, size_i, kps_n, gal_i = arr
+    n_req = len(t_arr)
+    pairs = float(sum(int(kps_n[i]) * int(gal_n[gal_i[i]]) for i in range(n_req)))
     ctx = P.Context(local, triplets=synth.triplets())
     P.latch_reserve(ctx.handle, 64000, 64000, int(gal_n.max()))
     d_gals = [torch.from_numpy(g_).to(dev) for g_ in gals]
@@ -878,11 +884,34 @@ def bench_serve(args, local):
     th.join()
     ctx.check()
     ctx.close()
-    rec = _latency_summary(lat, first, last, ndesc_all, pairs, n_req)
+    rec = _latency_summary(lat, first, last, int(kps_n.sum()), pairs, n_req)
     rec.update({"entry": "per request: upload, latch_extract, hamming_match (path per shape) against the "
                          "resident packed gallery, download; one request at a time in arrival order",
                 "clocks": clk})
-    out["plain_per_request"] = rec
+    return rec
+
+
+def bench_serve(args, local):
+    """The Poisson request stream (--rate, --duration) through the session (continuous
+    batching, 2 lanes) and through the plain per-request calls; then an overload stream
+    (1,000 req/s for 6 s, beyond one-at-a-time capacity) through sessions of 2 and 4
+    lanes and the plain calls, where requests queue and micro-batches form."""
+    inputs = _serve_inputs(args)
+    sizes = inputs[0]
+    arr = _serve_arrivals(args.rate, args.duration, len(sizes))
+    name = f"serve_poisson_{args.rate:g}rps_{args.duration:g}s"
+    out = {"workload": name, "requests": len(arr[0]), "offered_rps": args.rate,
+           "request_mix": "640x480..4000x3000 images, 1k-64k oriented keypoints, 32 resident galleries of "
+                          "10k-200k descriptors"}
+    out["session"] = _serve_session(local, inputs, arr, 2, name)
+    out["plain_per_request"] = _serve_plain(local, inputs, arr)
+    over_rate, over_s = 1000.0, 6.0
+    arr_o = _serve_arrivals(over_rate, over_s, len(sizes), stream=1)
+    over = {"offered_rps": over_rate, "duration_s": over_s, "requests": len(arr_o[0])}
+    for lanes in (2, 4):
+        over[f"session_{lanes}_lanes"] = _serve_session(local, inputs, arr_o, lanes, name, sustained_roof=False)
+    over["plain_per_request"] = _serve_plain(local, inputs, arr_o)
+    out["overload"] = over
     return out
 
 

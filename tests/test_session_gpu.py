@@ -176,3 +176,30 @@ def test_bad_scale_is_refused_and_the_mix_stays_exact(served, gpu_ctx):
     st = sess.stats()
     assert st["failed"] == 0
     assert 0 < st["hbm_budget"] <= st["hbm_free"]
+
+
+@pytest.mark.parametrize("lanes", [1, 4])
+def test_lane_counts(triplets, gpu_ctx, lanes):
+    """Sessions with one and with four lanes give the bytes of the plain calls for a
+    burst of requests (with four lanes, several micro-batches run at once)."""
+    sess = P.Session(triplets, hbm_budget=2 << 30, max_gallery_rows=1 << 18, max_batch=8, max_batch_kps=1 << 16,
+                     lanes=lanes)
+    try:
+        gals = [synth.random_descriptors(synth.seed(46, g, synth.KIND_GALLERY), n) for g, n in
+                enumerate((3000, 12007, 1))]
+        assert [sess.add_gallery(g) for g in gals] == [0, 1, 2]
+        reqs = _requests(16, seed=47)
+        want = [_single_call(gpu_ctx, r, gals) for r in reqs]
+        tickets = [sess.submit(r["img"], r["w"], r["h"], r["kps"], r["gallery"], r["k"], r["ratio"], want_desc=True)
+                   for r in reqs]
+        for t, (wd, wm) in zip(tickets, want):
+            res, m, d = sess.wait(t)
+            assert res.status == 0
+            assert np.array_equal(d, wd)
+            _same(m, wm)
+        st = sess.stats()
+        assert st["failed"] == 0 and st["completed"] == len(reqs)
+    finally:
+        sess.close()
+    with pytest.raises(P.LatchError):
+        P.latch_session_create_lanes(0, 1 << 30, 1000, 4, 1000, 9, triplets)

@@ -23,20 +23,22 @@ constexpr double kMaxScale = 2.25;
 constexpr int kMaxReach = 77;               // max |offset| at scale 2.25 (24*sqrt(2)*2.25 = 76.4)
 
 // The tensor matcher's input row of one descriptor: its 512 bits as 4-bit E2M1
-// floats, two per byte, bit t -> value t (1.0 = 0x2 when set, 0 otherwise; value t
-// in the low nibble of byte t / 2 when t is even), so a dot product of two rows
-// counts the bits the descriptors share.
+// floats, two per byte, bit t -> value t = 1 - 2 bit (+1.0 = 0x2 when clear, -1.0 =
+// 0xA when set; value t in the low nibble of byte t / 2 when t is even).  The dot
+// product of two rows is then (bits that agree) - (bits that differ) =
+// 512 - 2 Hamming, so one contraction gives the distance with no popcount term.
 constexpr int kExpRowBytes = 256;
 
 #ifdef __CUDACC__
-// Byte -> its 8 bits as 8 E2M1 values (nibble q = 2 * bit q), by spreading the bits
-// in three mask-and-shift steps (4-bit groups, then pairs, then single bits).
+// Byte -> its 8 bits as 8 E2M1 values (nibble q = 0x2 | 8 bit q), by spreading the
+// bits in three mask-and-shift steps (4-bit groups, then pairs, then single bits) to
+// the sign position of their nibbles.
 __device__ __forceinline__ uint32_t expand_byte_e2m1(uint32_t b) {
     uint32_t x = b & 0xffu;
     x = (x | (x << 12)) & 0x000F000Fu;
     x = (x | (x << 6)) & 0x03030303u;
     x = (x | (x << 3)) & 0x11111111u;
-    return x << 1;
+    return (x << 3) | 0x22222222u;
 }
 // 32 descriptor bits (bit q = descriptor bit 32 i + q) -> their 16 expanded bytes.
 __device__ __forceinline__ uint4 expand_word_e2m1(uint32_t w) {

@@ -1,42 +1,39 @@
 // Brute-force Hamming matching on the 5th-generation tensor cores (Sec. 4's
 // all-pairs distance computation, done as a dense contraction).
 //
-// With every descriptor bit expanded to a 4-bit E2M1 float that is exactly 0 or 1
-// (two per byte), the dot product of two expanded descriptors counts their common
-// 1-bits, and Hamming(q, t) = popc(q) + popc(t) - 2 * dot(q, t).  The block-scaled
-// fp4 MMA (kind::mxf4, every scale factor 2^0) issues twice the products per clock
-// of the 8-bit kind; products are 0/1 and sums are at most 512, so fp32
-// accumulation is exact.
+// Every descriptor bit b is expanded to the 4-bit E2M1 float 1 - 2 b (+1 or -1, two
+// per byte), so the dot product of two expanded descriptors is (bits that agree) -
+// (bits that differ) = 512 - 2 Hamming(q, t): one contraction gives the distance,
+// with no popcount term.  The block-scaled fp4 MMA (kind::mxf4, every scale factor
+// 2^0) issues twice the products per clock of the 8-bit kind; the products are +-1
+// and the sums at most 512 in magnitude, so fp32 accumulation is exact.
 //
 // One launch serves a batch of matching problems (query set x train set pairs; a
 // single hamming_match call is a batch of one).  All descriptors live in one
-// expanded buffer (two TMA tensor maps over it: 128-row query boxes, 96-row train
-// boxes).  The units (problem, 256-query tile, 96-train tile) of all problems are
+// expanded buffer (two TMA tensor maps over it: 128-row query boxes, 160-row train
+// boxes).  The units (problem, 128-query tile, 160-train tile) of all problems are
 // linearised and split into one contiguous range per block (one block per SM,
-// persistent); a unit is two M=128 halves that share each train chunk, so every
-// train byte loaded feeds 256 query rows:
-//   warp 0     TMA producer: the query tile (256 rows x 256 B, 64 KB) stays resident
-//              while consecutive units share it; train chunks (96 rows x 128 bytes,
-//              half of K) go through a 12-stage ring, 128-byte swizzle;
-//   warp 1     MMA issuer: per unit 16 tcgen05.mma (M=128, N=96, K=64), two per K
-//              step (one per half), into one of two double-buffered sets of two
-//              96-column TMEM accumulators;
-//   warp 2     TMEM allocator (all 512 columns: accumulator sets at columns 0 and
-//              256, the constant scale factors between them);
-//   warp 3     column keys: per unit, (popc(train row) + 512) << 8 | column into a
-//              4-deep ring in shared memory, ahead of the epilogue;
-//   warps 4-19 epilogue (one query row and 48 columns per thread): tcgen05.ld of the
-//              fp32 dot products 16 columns at a time, key =
-//              ((popc(t) - 2*dot + 512) << 8 | column) formed exactly in fp32 by
-//              one FMA; a group of 16 keys whose minimum is not below the row's
-//              running second-best (no key of it can enter the top two: its train
-//              indices are larger than every one seen) costs one min tree, the
-//              others update the min / second-min chains; the tile's two best are
-//              merged into the row's (distance << 32 | index) keys, and when the
-//              block leaves a query tile the row's two keys go to a partial record;
-//              the last block to leave a tile (a per-tile arrival counter) combines
-//              the records of its rows and writes their matches (ties to the lowest
-//              train index, ratio test).
+// persistent):
+//   warp 0     TMA producer: the query tile (128 rows x 256 B, 32 KB) stays resident
+//              while consecutive units share it; train chunks (160 rows x 128 B, half
+//              of K) go through an 8-stage ring, 128-byte swizzle;
+//   warps 1-2  MMA issuers (even / odd units): per unit 8 tcgen05.mma (M=128,
+//              N=160, K=64) into one of three 160-column TMEM accumulators in
+//              rotation (columns 0, 160, 320; the constant scale factors in 480-511);
+//              warp 2 also allocates TMEM;
+//   warp 3     idle;
+//   warps 4-23 epilogue (one query row and 32 columns per thread): two reducing
+//              TMEM loads (tcgen05.ld.red .max) bring the 32 values and the largest
+//              of each 16, and the accumulator is released at once.  A half whose
+//              largest value is not above the row's running threshold (the value of
+//              its second-best match: later columns have larger train indices, so
+//              they enter the top two only with a smaller distance) costs nothing
+//              more; the others take the top-two update (max / second-max chains over
+//              64 v - column, unique values that break ties to the lower index).  When
+//              the block leaves a query tile the row's two (distance << 32 | index)
+//              keys go to a partial record; the last block to leave a tile (a per-tile
+//              arrival counter) combines the records of its rows and writes their
+//              matches (ties to the lowest train index, ratio test).
 // match_merge_kernel does the same combination as a separate pass; it serves the
 // batches in which some problem has queries but an empty train set (no unit, so no
 // block visits its tiles).  All mbarrier waits are bounded (sm103.h); on a timeout
@@ -55,39 +52,33 @@ namespace {
 
 using namespace sm103;
 
-constexpr int kRowsA = 128;             // rows per MMA (M)
-constexpr int kHalves = 1;              // MMAs per K step: the tile's two 128-row halves
-constexpr int kRowsQ = kHalves * kRowsA;  // queries per tile
-constexpr int kColsB = 192 / kHalves;   // train rows per unit (N)
+constexpr int kRowsA = 128;             // rows per MMA (M) = queries per tile
+constexpr int kRowsQ = kRowsA;
+constexpr int kColsB = 160;             // train rows per unit (N)
 constexpr int kRowsP = kRowsQ;          // partial records per tile slot: one per query row
 constexpr int kKBytes = kExpRowBytes;   // expanded descriptor: 512 x 4-bit
 constexpr int kChunk = 128;             // K bytes per swizzle atom / TMA box
 constexpr int kChunks = kKBytes / kChunk;
 constexpr int kMmaKBytes = 32;          // K bytes per MMA: 64 E2M1 values
-constexpr int kStages = kHalves == 2 ? 10 : 6;
-constexpr int kTileBytes = kRowsA * kChunk;   // 16 KB: a half tile's chunk of 128 rows x 128 B (one TMA box)
-constexpr int kStageBytes = kColsB * kChunk;  // 12 KB: a train chunk of 96 rows x 128 B (one TMA box)
-constexpr int kEpiWarps = 16;                       // epilogue: 4 lane quarters x 2 halves x 2 column groups
+constexpr int kStages = 8;              // train chunks in flight: four units
+constexpr int kTileBytes = kRowsA * kChunk;   // 16 KB: a query chunk of 128 rows x 128 B (one TMA box)
+constexpr int kStageBytes = kColsB * kChunk;  // 20 KB: a train chunk of 160 rows x 128 B (one TMA box)
+constexpr int kAccs = 3;                // TMEM accumulators in rotation (unit i uses i % 3)
+constexpr int kEpiWarps = 20;           // epilogue: 4 lane quarters x 5 column groups
 constexpr int kEpiThreads = kEpiWarps * 32;
-constexpr int kThreads = 128 + kEpiThreads;         // producer, MMA, TMEM, keys, then the epilogue
-constexpr int kColGroups = kEpiWarps / (4 * kHalves);
+constexpr int kThreads = 128 + kEpiThreads;         // producer, two MMA issuers, an idle warp, then the epilogue
+constexpr int kColGroups = kEpiWarps / 4;
 constexpr int kColsPerThread = kColsB / kColGroups;  // accumulator columns one epilogue thread scans
-constexpr int kLdCols = 16;                          // columns per tcgen05.ld (double-buffered)
-constexpr int kKeyStages = 4;                        // per-unit bias operands prepared ahead of the MMAs
-constexpr int kBiasK = 16;                           // K of the bias MMA (BF16)
-constexpr int kBiasRowBytes = kBiasK * 2;            // 32 B per bias row
-constexpr int kBiasABytes = kRowsA * kBiasRowBytes;  // 4 KB: the constant bias rows of A
-constexpr int kBiasBBytes = kColsB * kBiasRowBytes;  // one unit's bias rows of B
+constexpr int kLdCols = 16;                          // columns per tcgen05.ld
 constexpr int kTmemCols = 512;
-constexpr uint32_t kAccStride = 256;  // accumulator set b: half h at TMEM columns 256 b + 96 h, 96 wide
-constexpr uint32_t kSfaCol = 192;     // scale factors of A: 4 columns (128 rows), 32 filled
-constexpr uint32_t kSfbCol = 224;     // scale factors of B: 4 columns per 128 rows, 32 filled
-constexpr uint32_t kScaleA = 0x88888888u;    // four UE8M0 scale factors 2^9: A x B = 512 dot
-constexpr uint32_t kScaleB = 0x7F7F7F7Fu;    // four UE8M0 scale factors 2^0
+constexpr uint32_t kSfaCol = 480;       // scale factors of A: 4 columns (128 rows)
+constexpr uint32_t kSfbCol = 488;       // scale factors of B: 4 columns per 128 rows
+constexpr uint32_t kScaleOne = 0x7F7F7F7Fu;  // four UE8M0 scale factors 2^0 (columns 480-511 all hold it)
 constexpr uint32_t kIdesc = idesc_mxf4_e2m1(kRowsA, kColsB);
-constexpr uint32_t kIdescBias = idesc_bf16_f32(kRowsA, kColsB);
-static_assert(kHalves * kColsB <= kSfaCol && kSfbCol + 8 <= kAccStride, "TMEM columns overlap");
-static_assert(kColsPerThread == 3 * kLdCols, "epilogue: three 16-column loads per unit");
+static_assert(kAccs * kColsB <= static_cast<int>(kSfaCol) && kSfbCol + 8 * ((kColsB + 127) / 128) <= kTmemCols,
+              "TMEM columns overlap");
+static_assert(kColsPerThread == 2 * kLdCols, "epilogue: two 16-column loads per unit");
+static_assert(kColsB % 32 == 0 && kColsB <= 256 && kColsPerThread < 64, "unit shape");
 
 // max(a, b, c) in one instruction.
 __device__ __forceinline__ float fmax3(float a, float b, float c) {
@@ -101,13 +92,11 @@ __device__ __forceinline__ void group_sync() { asm volatile("bar.sync 1, %0;" ::
 
 struct Smem {
     // offsets in the 1024-aligned dynamic buffer
-    static constexpr int a = 0;                                        // [kHalves][kChunks] boxes of 16 KB
-    static constexpr int b = a + kHalves * kChunks * kTileBytes;       // [kStages] chunks of 12 KB
-    static constexpr int bias_a = b + kStages * kStageBytes;           // bias rows of A (4 KB)
-    static constexpr int bias_b = bias_a + kBiasABytes;                // [kKeyStages] bias rows of B
-    static constexpr int part = bias_b + kKeyStages * kBiasBBytes;     // uint64 [kEpiThreads][2]
+    static constexpr int a = 0;                                        // [kChunks] boxes of 16 KB
+    static constexpr int b = a + kChunks * kTileBytes;                 // [kStages] chunks of 20 KB
+    static constexpr int part = b + kStages * kStageBytes;             // uint64 [kEpiThreads][2]
     static constexpr int bars = part + kEpiThreads * 16;               // uint64 barriers
-    static constexpr int nbars = 2 * kStages + 2 + 4 + 2 + 2 * kKeyStages;
+    static constexpr int nbars = 2 * kStages + 2 + 2 * kAccs + 2;
     static constexpr int misc = bars + nbars * 8;                      // tmem base, abort flag, last-arrival flag
     static constexpr int total = misc + 16;
 };
@@ -311,19 +300,15 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* sA = smem + Smem::a;
     uint8_t* sB = smem + Smem::b;
-    uint8_t* sBiasA = smem + Smem::bias_a;
-    uint8_t* sBiasB = smem + Smem::bias_b;
     uint64_t* sPart = reinterpret_cast<uint64_t*>(smem + Smem::part);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Smem::bars);
     uint64_t* full = bars;
     uint64_t* empty = bars + kStages;
     uint64_t* a_full = bars + 2 * kStages;
     uint64_t* a_empty = a_full + 1;
-    uint64_t* acc_full = a_full + 2;
-    uint64_t* acc_empty = a_full + 4;
-    uint64_t* mma_done = a_full + 6;               // [2]: one per MMA warp
-    uint64_t* key_full = a_full + 8;               // [kKeyStages]
-    uint64_t* key_empty = key_full + kKeyStages;   // [kKeyStages]
+    uint64_t* acc_full = a_full + 2;               // [kAccs]
+    uint64_t* acc_empty = acc_full + kAccs;        // [kAccs]
+    uint64_t* mma_done = acc_empty + kAccs;        // [2]: one per MMA warp
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + Smem::misc);
     volatile int* abort = reinterpret_cast<volatile int*>(smem + Smem::misc + 4);
     volatile int* last_arrival = reinterpret_cast<volatile int*>(smem + Smem::misc + 8);
@@ -339,16 +324,12 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
         }
         mbar_init(a_full, 1);
         mbar_init(a_empty, 2);  // both MMA warps commit once per query tile
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < kAccs; ++i) {
             mbar_init(&acc_full[i], 1);
             mbar_init(&acc_empty[i], kEpiThreads / 32);
         }
         mbar_init(&mma_done[0], 1);
         mbar_init(&mma_done[1], 1);
-        for (int i = 0; i < kKeyStages; ++i) {
-            mbar_init(&key_full[i], 32);  // the key warp's lanes
-            mbar_init(&key_empty[i], 1);  // the commit after the unit's bias MMA
-        }
         *abort = 0;
         fence_mbar_init();
     }
@@ -360,31 +341,15 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
         tmem_alloc(tmem_slot, kTmemCols);
         tc_fence_before();
     }
-    // bias operands (BF16, K = 16, no swizzle: element (r, k) at (r / 8) 256 + (k / 8) 128 +
-    // (r % 8) 16 + (k % 8) 2): every row of A is (4096, 256, 1, 0, ...); B's rows are
-    // written per unit by the key warp, its elements 3..15 stay zero
-    for (int i = threadIdx.x; i < (kBiasABytes + kKeyStages * kBiasBBytes) / 16; i += kThreads) {
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (i < kBiasABytes / 16) {
-            const int r = (i >> 4) * 8 + (i & 7), chunk = (i >> 3) & 1;  // 16 chunks per 8-row group
-            if (chunk == 0 && r < kRowsA)
-                v = make_uint4((__float_as_uint(4096.0f) >> 16) | (__float_as_uint(256.0f) & 0xffff0000u),
-                               __float_as_uint(1.0f) >> 16, 0, 0);
-        }
-        reinterpret_cast<uint4*>(sBiasA)[i] = v;
-    }
-    fence_proxy_async_smem();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     if (warp >= 4 && warp < 8) {
-        // block scale factors: 2^9 for A, 2^0 for B, in the scale columns of all 128
-        // lanes (warp w may address lane quarter w % 4)
+        // block scale factors 2^0 in columns kSfaCol..511 of all 128 lanes (warp w may
+        // address lane quarter w % 4)
         const uint32_t base = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16);
 #pragma unroll
-        for (uint32_t col = kSfaCol; col < kSfbCol; col += 8) tmem_st_32x32b_x8_same(base + col, kScaleA);
-#pragma unroll
-        for (uint32_t col = kSfbCol; col < kAccStride; col += 8) tmem_st_32x32b_x8_same(base + col, kScaleB);
+        for (uint32_t col = kSfaCol; col < kTmemCols; col += 8) tmem_st_32x32b_x8_same(base + col, kScaleOne);
         tmem_st_wait();
     }
     tc_fence_before();
@@ -414,11 +379,10 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                         if (!mbar_wait(a_empty, a_par, abort)) break;
                         a_par ^= 1;
                     }
-                    mbar_arrive_expect_tx(a_full, kHalves * kChunks * kTileBytes);
-                    for (int h = 0; h < kHalves; ++h)
-                        for (int kc = 0; kc < kChunks; ++kc)
-                            tma_load_2d(sA + (h * kChunks + kc) * kTileBytes, &tmq, kc * kChunk,
-                                        static_cast<int32_t>(P.q_row0 + m * kRowsQ + h * kRowsA), a_full);
+                    mbar_arrive_expect_tx(a_full, kChunks * kTileBytes);
+                    for (int kc = 0; kc < kChunks; ++kc)
+                        tma_load_2d(sA + kc * kTileBytes, &tmq, kc * kChunk, static_cast<int32_t>(P.q_row0 + m * kRowsQ),
+                                    a_full);
                     prev_g = g;
                 }
                 bool ok = true;
@@ -455,23 +419,20 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
         // ---------------- MMA issuers: warp 1 issues the even units, warp 2 the odd ones
         // (a thread's tcgen05.mma waits until the tensor pipe takes it, so a single
         // issuer leaves the pipe idle while it waits on barriers between units; with two,
-        // one issuer's waits overlap the other's MMAs).  Unit i uses accumulator i % 2 and
-        // stages 2 i, 2 i + 1 of the ring; both issuers walk every unit, wait for every
-        // query tile and commit a_empty (count 2) at every tile's end. ----------------
+        // one issuer's waits overlap the other's MMAs).  Unit i uses accumulator i % 3
+        // and stages 2 i, 2 i + 1 of the ring; both issuers walk every unit, wait for
+        // every query tile and commit a_empty (count 2) at every tile's end. ----------------
         if (lane == 0) {
             const int mine = warp - 1;
             RunIter run;
             run.init(batch, c);
-            uint32_t a_par = 0, acc_par = 0;
+            uint32_t a_par = 0;
             // shared-memory descriptors of the first query box and train chunk; the others
             // differ only in the start-address field (bits 0-13: address / 16), so each MMA
             // adds a constant to them
             const uint64_t a_desc0 = umma_desc_sw128(smem_u32(sA));
             const uint64_t b_desc0 = umma_desc_sw128(smem_u32(sB));
             const uint32_t sfa = tmem + kSfaCol, sfb = tmem + kSfbCol;
-            const uint32_t d0 = tmem + static_cast<uint32_t>(mine) * kAccStride;
-            const uint64_t bias_a_desc = umma_desc_noswizzle(smem_u32(sBiasA), 128, 256);
-            const uint64_t bias_b_desc0 = umma_desc_noswizzle(smem_u32(sBiasB), 128, 256);
             int i = 0;  // the run's first unit in the block's walk
             bool ok = true;
             for (; ok && !run.done(batch); run.next(batch, c)) {
@@ -479,24 +440,14 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                 a_par ^= 1;
                 const int end = i + run.len;
                 for (int j = i + ((i & 1) ^ mine); ok && j < end; j += 2) {
-                    if (!mbar_wait(&acc_empty[mine], acc_par ^ 1, abort)) {
-                        ok = false;
-                        break;
-                    }
-                    acc_par ^= 1;
-                    const int kslot = j % kKeyStages;
-                    if (!mbar_wait(&key_full[kslot], static_cast<uint32_t>(j / kKeyStages) & 1u, abort)) {
+                    const int acc = j % kAccs;
+                    if (!mbar_wait(&acc_empty[acc], static_cast<uint32_t>((j / kAccs) & 1) ^ 1u, abort)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    // D = -key(column) in every row, then the fp4 MMAs add 512 dot
-#pragma unroll
-                    for (int h = 0; h < kHalves; ++h)
-                        mma_bf16(d0 + static_cast<uint32_t>(h * kColsB), bias_a_desc,
-                                 bias_b_desc0 + static_cast<uint64_t>((kslot * kBiasBBytes) >> 4), kIdescBias, 0);
-                    mma_commit(&key_empty[kslot]);
-                    // unit j reads ring positions 2 j and 2 j + 1
+                    const uint32_t d = tmem + static_cast<uint32_t>(acc * kColsB);
+                    // unit j reads ring positions 2 j and 2 j + 1; its first MMA overwrites D
 #pragma unroll
                     for (int kc = 0; kc < kChunks; ++kc) {
                         const int pos = kChunks * j + kc;
@@ -510,14 +461,12 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                         const uint64_t ad = a_desc0 + static_cast<uint64_t>((kc * kTileBytes) >> 4);
 #pragma unroll
                         for (int ks = 0; ks < kChunk / kMmaKBytes; ++ks)
-#pragma unroll
-                            for (int h = 0; h < kHalves; ++h)
-                                mma_mxf4(d0 + static_cast<uint32_t>(h * kColsB),
-                                         ad + static_cast<uint64_t>((h * kChunks * kTileBytes + ks * kMmaKBytes) >> 4),
-                                         bd + static_cast<uint64_t>((ks * kMmaKBytes) >> 4), kIdesc, sfa, sfb, 1);
+                            mma_mxf4(d, ad + static_cast<uint64_t>((ks * kMmaKBytes) >> 4),
+                                     bd + static_cast<uint64_t>((ks * kMmaKBytes) >> 4), kIdesc, sfa, sfb,
+                                     (kc | ks) != 0);
                         mma_commit(&empty[stage]);
                     }
-                    if (ok) mma_commit(&acc_full[mine]);
+                    if (ok) mma_commit(&acc_full[acc]);
                 }
                 i = end;
                 if (ok) mma_commit(a_empty);
@@ -528,197 +477,149 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
             while (!mbar_try_wait(&mma_done[mine], 0) && globaltimer() - t0 < 200000000ull) {
             }
         }
-    } else if (warp == 3) {
-        // ---------------- bias rows: for each unit, row j of B's bias operand is
-        // (-hi, -lo, -j, 0, ...) in BF16 with 16 hi + lo = popc(train row) + 512, so that
-        // the bias MMA sets column j of every accumulator row to -key(j), key(j) =
-        // (popc(train row) + 512) << 8 | j; past the train set (-65536, 0, ...) puts the
-        // column below every key.  Two units at a time: the popcounts of both are
-        // loaded before either is written, so one load latency serves two units ----------------
-        constexpr int kRowsPerLane = kColsB / 32;
-        UnitIter it;
-        it.init(batch, c);
-        auto load = [&](const UnitIter& u, int (&pv)[kRowsPerLane]) {
-#pragma unroll
-            for (int q = 0; q < kRowsPerLane; ++q) {
-                const int64_t col = static_cast<int64_t>(u.n) * kColsB + lane + 32 * q;
-                pv[q] = col < u.nt ? __ldg(pop + u.t_row0 + col) : -1;
-            }
-        };
-        auto bf16_bits = [](int v) { return __float_as_uint(static_cast<float>(v)) >> 16; };
-        bool ok = true;
-        for (int64_t i = 0; ok && !it.done(batch); i += 2) {
-            int pv0[kRowsPerLane], pv1[kRowsPerLane];
-            UnitIter it1 = it;
-            it1.next(batch, c);
-            const bool two = !it1.done(batch);
-            load(it, pv0);
-            if (two) load(it1, pv1);
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                if (u == 1 && !two) break;
-                const int64_t k = i + u;
-                const int slot = static_cast<int>(k % kKeyStages);
-                if (!mbar_wait(&key_empty[slot], (static_cast<uint32_t>(k / kKeyStages) & 1u) ^ 1u, abort)) {
-                    ok = false;
-                    break;
-                }
-                uint8_t* rows = sBiasB + slot * kBiasBBytes;
-#pragma unroll
-                for (int q = 0; q < kRowsPerLane; ++q) {
-                    const int j = lane + 32 * q;
-                    const int pt = u == 0 ? pv0[q] : pv1[q];
-                    uint4 v;
-                    if (pt >= 0) {
-                        const int hk = pt + 512;
-                        v = make_uint4(bf16_bits(-(hk >> 4)) | (bf16_bits(-(hk & 15)) << 16), bf16_bits(-j), 0, 0);
-                    } else {
-                        v = make_uint4(bf16_bits(-65536), 0, 0, 0);
-                    }
-                    *reinterpret_cast<uint4*>(rows + (j >> 3) * 256 + (j & 7) * 16) = v;
-                }
-                fence_proxy_async_smem();
-                mbar_arrive(&key_full[slot]);  // each lane releases its own stores
-            }
-            it = it1;
-            if (two) it.next(batch, c);
-        }
     } else if (warp >= 4) {
         // ---------------- epilogue: kEpiWarps warps; thread = one query row x one
-        // group of kColsPerThread accumulator columns ----------------
+        // group of kColsPerThread accumulator columns.  The walk goes by runs (the
+        // consecutive units of one query tile), so the per-unit path touches only
+        // counters in registers; the problem table is read where a run ends. ----------------
         const int et = threadIdx.x - 128;  // 0 .. kEpiThreads-1 = cg * kRowsQ + row_in_tile
         const int quarter = warp & 3;      // TMEM lane quarter this warp may access
-        const int half = ((warp - 4) >> 2) % kHalves;  // 128-row half of the query tile
-        const int cg = ((warp - 4) >> 2) / kHalves;    // column group [cg * kColsPerThread, +kColsPerThread)
-        const int row_in_tile = half * kRowsA + quarter * 32 + lane;
+        const int cg = (warp - 4) >> 2;    // column group [cg * kColsPerThread, +kColsPerThread)
+        const int col0 = cg * kColsPerThread;
+        const int row_in_tile = quarter * 32 + lane;
+        const uint32_t lane_base = tmem + (static_cast<uint32_t>(quarter * 32) << 16) + static_cast<uint32_t>(col0);
         const float kNegInf = __int_as_float(0xff800000);
-        UnitIter it;
-        it.init(batch, c);
-        uint32_t acc_par = 0;  // bit b: the phase parity of accumulator b
-        uint64_t k1 = kNoKey, k2 = kNoKey;
-        int32_t pq = 0;
-        // accumulator values (-key) above this can still enter the row's top two
-        float thr = kNegInf;
+        RunIter run;
+        run.init(batch, c);
+        int acc = 0;           // accumulator of the next unit (unit i uses i % kAccs)
+        uint32_t acc_par = 0;  // bit a: the phase parity of accumulator a
         bool aborted = false;  // warp-uniform
-        int64_t prev_g = -1;
-        int i = 0;
-        for (; !it.done(batch); ++i, it.next(batch, c)) {
-            const MatchProblem& P = batch.p[it.p];
-            const int64_t m = it.m, n = it.n;
-            const int64_t g = it.g(batch);
-            const int buf = i & 1;
-            if (g != prev_g) {
-                const int64_t row = m * kRowsQ + row_in_tile;
-                pq = row < P.nq ? pop[P.q_row0 + row] : 0;
-                k1 = k2 = kNoKey;
-                thr = kNegInf;
-                prev_g = g;
-            }
-            // after a failed wait a warp keeps walking the units without work, so that
-            // every warp reaches the barriers at the ends of query tiles
-            if (!aborted) aborted = !__all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (acc_par >> buf) & 1u, abort));
-            if (!aborted) {
-                acc_par ^= 1u << buf;
-                tc_fence_after();
-                const uint32_t base = tmem + (static_cast<uint32_t>(quarter * 32) << 16) +
-                                      static_cast<uint32_t>(buf) * kAccStride +
-                                      static_cast<uint32_t>(half * kColsB + cg * kColsPerThread);
-                // the thread's columns (512 dot - key, exact integers) in one round trip;
-                // the accumulator is free again as soon as they are in registers
-                uint32_t va[kLdCols], vb[kLdCols], vc[kLdCols];
-                tmem_ld_32x32b_x16(base, va);
-                tmem_ld_32x32b_x16(base + kLdCols, vb);
-                tmem_ld_32x32b_x16(base + 2 * kLdCols, vc);
-                tmem_ld_wait();
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&acc_empty[buf]);
-                float e[kColsPerThread];
+        for (; !run.done(batch); run.next(batch, c)) {
+            const UnitIter& u = run.u;  // the run's first unit
+            uint64_t k1 = kNoKey, k2 = kNoKey;
+            // accumulator values (512 - 2 distance) above this can still enter the row's top two
+            float thr = kNegInf;
+            // the thread's columns in the problem's last train tile that lie inside the
+            // train set (the rest are rows of zeros or of the next problem)
+            const int32_t n_last = u.ntl - 1;
+            const int32_t lim_last = u.nt - n_last * kColsB - col0;
+            // the top-two update from 16 of the thread's columns (h = 0: columns 0-15,
+            // 1: 16-31) of train tile n.  w = 64 v - j orders the columns by value, then
+            // by lower index, and is unique (|v| <= 512, j < 64: exact in fp32); two
+            // independent max / second-max chains (even and odd columns)
+            auto update = [&](const float (&e)[kColsPerThread], int h, int32_t n) {
+                float m1a = kNegInf, m2a = kNegInf, m1b = kNegInf, m2b = kNegInf;
 #pragma unroll
-                for (int j = 0; j < kLdCols; ++j) {
-                    e[j] = __uint_as_float(va[j]);
-                    e[kLdCols + j] = __uint_as_float(vb[j]);
-                    e[2 * kLdCols + j] = __uint_as_float(vc[j]);
+                for (int q = 0; q < kLdCols; q += 2) {
+                    const int j = h * kLdCols + q;
+                    const float wa = fmaf(e[j], 64.0f, -static_cast<float>(j));
+                    const float wb = fmaf(e[j + 1], 64.0f, -static_cast<float>(j + 1));
+                    const float la = fminf(m1a, wa);
+                    m1a = fmaxf(m1a, wa);
+                    m2a = fmaxf(m2a, la);
+                    const float lb = fminf(m1b, wb);
+                    m1b = fmaxf(m1b, wb);
+                    m2b = fmaxf(m2b, lb);
                 }
-                // the unit's largest value (a tree of 3-input maxima); only a unit that
-                // reaches above the row's running threshold takes the top-two update
-                float t16[16], t6[6];
+                // combine the chains (values are unique): (a1,a2) + (b1,b2) -> (max, second max)
+                const float hi = fmaxf(m1a, m1b), lo = fminf(m1a, m1b);
+                const float m2 = fmaxf(lo, fmaxf(m2a, m2b)), m1 = hi;
+                // the two best -> (distance << 32 | index) keys; -inf marks masked columns
 #pragma unroll
-                for (int k = 0; k < 16; ++k) t16[k] = fmax3(e[3 * k], e[3 * k + 1], e[3 * k + 2]);
-#pragma unroll
-                for (int k = 0; k < 5; ++k) t6[k] = fmax3(t16[3 * k], t16[3 * k + 1], t16[3 * k + 2]);
-                t6[5] = t16[15];
-                const float umax = fmaxf(fmax3(t6[0], t6[1], t6[2]), fmax3(t6[3], t6[4], t6[5]));
-                if (__any_sync(0xffffffffu, umax > thr)) {
-                    // two independent max / second-max chains (even and odd columns)
-                    float m1a = kNegInf, m2a = kNegInf, m1b = kNegInf, m2b = kNegInf;
-#pragma unroll
-                    for (int j = 0; j < kColsPerThread; j += 2) {
-                        const float la = fminf(m1a, e[j]);
-                        m1a = fmaxf(m1a, e[j]);
-                        m2a = fmaxf(m2a, la);
-                        const float lb = fminf(m1b, e[j + 1]);
-                        m1b = fmaxf(m1b, e[j + 1]);
-                        m2b = fmaxf(m2b, lb);
+                for (int b = 0; b < 2; ++b) {
+                    const float mv = b == 0 ? m1 : m2;
+                    if (mv != kNegInf) {
+                        const int32_t w = static_cast<int32_t>(mv);
+                        const int32_t j = (-w) & 63;
+                        const int32_t d = 256 - ((w + j) >> 7);  // v = (w + j) / 64, d = (512 - v) / 2
+                        const uint32_t idx = static_cast<uint32_t>(n) * kColsB + static_cast<uint32_t>(col0 + j);
+                        top2_insert_u64((static_cast<uint64_t>(d) << 32) | idx, k1, k2);
                     }
-                    // combine the chains (values are unique): (a1,a2) + (b1,b2) -> (max, second max)
-                    const float hi = fmaxf(m1a, m1b), lo = fminf(m1a, m1b);
-                    const float m2 = fmaxf(lo, fmaxf(m2a, m2b)), m1 = hi;
-                    // the unit's two best -> (distance << 32 | index) keys; values at or
-                    // below -2^20 are columns past the train set
+                }
+                // later columns of this tile have larger train indices: one enters the
+                // top two only with a distance below the second-best's
+                if (k2 != kNoKey) thr = static_cast<float>(512 - 2 * static_cast<int32_t>(k2 >> 32));
+            };
+            const int32_t n_end = u.n + run.len;
+            for (int32_t n = u.n; n < n_end; ++n) {
+                // after a failed wait a warp keeps walking the units without work, so that
+                // every warp reaches the barriers at the ends of query tiles
+                if (!aborted) aborted = !__all_sync(0xffffffffu, mbar_wait(&acc_full[acc], (acc_par >> acc) & 1u, abort));
+                if (!aborted) {
+                    acc_par ^= 1u << acc;
+                    tc_fence_after();
+                    // the thread's columns (512 - 2 Hamming, exact integers) and the largest
+                    // of each half in one round trip; the accumulator is free again as soon
+                    // as they are in registers
+                    const uint32_t base = lane_base + static_cast<uint32_t>(acc * kColsB);
+                    uint32_t va[kLdCols], vb[kLdCols];
+                    float ma, mb;
+                    tmem_ld_red_max_32x32b_x16(base, va, ma);
+                    tmem_ld_red_max_32x32b_x16(base + kLdCols, vb, mb);
+                    tmem_ld_wait();
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&acc_empty[acc]);
+                    float e[kColsPerThread];
 #pragma unroll
-                    for (int b = 0; b < 2; ++b) {
-                        const float mv = b == 0 ? m1 : m2;
-                        if (mv > -1048576.0f) {
-                            const uint32_t kk = static_cast<uint32_t>(-mv);
-                            const int32_t d = pq + static_cast<int32_t>(kk >> 8) - 512;
-                            const uint64_t idx = static_cast<uint64_t>(n * kColsB + (kk & 255u));
-                            top2_insert_u64((static_cast<uint64_t>(d) << 32) | idx, k1, k2);
+                    for (int j = 0; j < kLdCols; ++j) {
+                        e[j] = __uint_as_float(va[j]);
+                        e[kLdCols + j] = __uint_as_float(vb[j]);
+                    }
+                    if (n == n_last && lim_last < kColsPerThread) {
+                        ma = mb = kNegInf;
+#pragma unroll
+                        for (int j = 0; j < kColsPerThread; ++j) {
+                            if (j >= lim_last) e[j] = kNegInf;
+                            if (j < kLdCols) ma = fmaxf(ma, e[j]); else mb = fmaxf(mb, e[j]);
                         }
                     }
-                    // later units of this tile have larger train indices: a column there
-                    // enters the top two only with a distance below the second-best's
-                    if (k2 != kNoKey) thr = -static_cast<float>((static_cast<int32_t>(k2 >> 32) - pq + 512) * 256);
+                    // only a half that reaches above the row's running threshold takes the
+                    // top-two update
+                    if (__any_sync(0xffffffffu, ma > thr)) update(e, 0, n);
+                    if (__any_sync(0xffffffffu, mb > thr)) update(e, 1, n);
                 }
+                if (++acc == kAccs) acc = 0;
             }
-            if (it.last_of_tile(batch)) {
-                // the column groups of each row meet in shared memory; group 0 writes the
-                // row's partial record (slot g + c)
-                sPart[2 * et] = k1;
-                sPart[2 * et + 1] = k2;
-                group_sync();
-                if (cg == 0) {
+            // the run ends where the block leaves its query tile: the column groups of
+            // each row meet in shared memory; group 0 writes the row's partial record
+            // (slot g + c')
+            const MatchProblem& P = batch.p[u.p];
+            const int64_t m = u.m;
+            const int64_t g = u.g(batch);
+            sPart[2 * et] = k1;
+            sPart[2 * et + 1] = k2;
+            group_sync();
+            if (cg == 0) {
 #pragma unroll
-                    for (int q = 1; q < kColGroups; ++q) {
-                        top2_insert_u64(sPart[2 * (q * kRowsQ + row_in_tile)], k1, k2);
-                        top2_insert_u64(sPart[2 * (q * kRowsQ + row_in_tile) + 1], k1, k2);
-                    }
-                    uint64_t* rec = partials + (it.slot(batch) * kRowsP + row_in_tile) * 2;
-                    rec[0] = k1;
-                    rec[1] = k2;
+                for (int q = 1; q < kColGroups; ++q) {
+                    top2_insert_u64(sPart[2 * (q * kRowsQ + row_in_tile)], k1, k2);
+                    top2_insert_u64(sPart[2 * (q * kRowsQ + row_in_tile) + 1], k1, k2);
                 }
-                if (tile_cnt) {
-                    // publish the records; the last owner of the tile to arrive combines them
+                uint64_t* rec = partials + (u.slot(batch) * kRowsP + row_in_tile) * 2;
+                rec[0] = k1;
+                rec[1] = k2;
+                if (tile_cnt) __threadfence();  // the records are published before the arrival below
+            }
+            group_sync();  // the shared records are free for the next run
+            if (tile_cnt) {
+                // the last owner of the tile to arrive combines the records
+                if (et == 0) {
+                    const bool last = atomicAdd(&tile_cnt[g], 1) == tile_owner_count(batch, P, m) - 1;
+                    if (last) tile_cnt[g] = 0;  // no other block touches it again: leave it zero
+                    *last_arrival = last;
+                }
+                group_sync();
+                if (*last_arrival && cg == 0) {
                     __threadfence();
-                    group_sync();
-                    if (et == 0) {
-                        const bool last = atomicAdd(&tile_cnt[g], 1) == tile_owner_count(batch, P, m) - 1;
-                        if (last) tile_cnt[g] = 0;  // no other block touches it again: leave it zero
-                        *last_arrival = last;
-                    }
-                    group_sync();
-                    if (*last_arrival && cg == 0) {
-                        __threadfence();
-                        const int64_t row = m * kRowsQ + row_in_tile;
-                        uint64_t f1 = kNoKey, f2 = kNoKey;
-                        combine_row(batch, it.p, m, g, row_in_tile, partials, f1, f2);
-                        if (row < P.nq) out[P.out0 + row] = final_match(f1, f2, P.k, P.r_milli);
-                    }
+                    const int64_t row = m * kRowsQ + row_in_tile;
+                    uint64_t f1 = kNoKey, f2 = kNoKey;
+                    combine_row(batch, u.p, m, g, row_in_tile, partials, f1, f2);
+                    if (row < P.nq) out[P.out0 + row] = final_match(f1, f2, P.k, P.r_milli);
                 }
             }
         }
     }
-
     __syncthreads();
     if (threadIdx.x == 0 && *abort) atomicOr(flags, kFlagTimeout);
     if (warp == 2) {

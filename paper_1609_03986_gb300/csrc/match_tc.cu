@@ -75,6 +75,7 @@ constexpr uint32_t kSfaCol = 480;       // scale factors of A: 4 columns (128 ro
 constexpr uint32_t kSfbCol = 488;       // scale factors of B: 4 columns per 128 rows
 constexpr uint32_t kScaleOne = 0x7F7F7F7Fu;  // four UE8M0 scale factors 2^0 (columns 480-511 all hold it)
 constexpr uint32_t kIdesc = idesc_mxf4_e2m1(kRowsA, kColsB);
+constexpr int32_t kNoBound = 1024;      // a distance bound above every distance (512 bits)
 static_assert(kAccs * kColsB <= static_cast<int>(kSfaCol) && kSfbCol + 8 * ((kColsB + 127) / 128) <= kTmemCols,
               "TMEM columns overlap");
 static_assert(kColsPerThread == 2 * kLdCols, "epilogue: two 16-column loads per unit");
@@ -95,7 +96,8 @@ struct Smem {
     static constexpr int a = 0;                                        // [kChunks] boxes of 16 KB
     static constexpr int b = a + kChunks * kTileBytes;                 // [kStages] chunks of 20 KB
     static constexpr int part = b + kStages * kStageBytes;             // uint64 [kEpiThreads][2]
-    static constexpr int bars = part + kEpiThreads * 16;               // uint64 barriers
+    static constexpr int bound = part + kEpiThreads * 16;              // int32 [kRowsQ]
+    static constexpr int bars = bound + kRowsQ * 4;                    // uint64 barriers
     static constexpr int nbars = 2 * kStages + 2 + 2 * kAccs + 2;
     static constexpr int misc = bars + nbars * 8;                      // tmem base, abort flag, last-arrival flag
     static constexpr int total = misc + 16;
@@ -301,6 +303,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
     uint8_t* sA = smem + Smem::a;
     uint8_t* sB = smem + Smem::b;
     uint64_t* sPart = reinterpret_cast<uint64_t*>(smem + Smem::part);
+    int32_t* sBound = reinterpret_cast<int32_t*>(smem + Smem::bound);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Smem::bars);
     uint64_t* full = bars;
     uint64_t* empty = bars + kStages;
@@ -341,6 +344,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
         tmem_alloc(tmem_slot, kTmemCols);
         tc_fence_before();
     }
+    for (int r = threadIdx.x; r < kRowsQ; r += kThreads) sBound[r] = kNoBound;
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
@@ -497,8 +501,10 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
         for (; !run.done(batch); run.next(batch, c)) {
             const UnitIter& u = run.u;  // the run's first unit
             uint64_t k1 = kNoKey, k2 = kNoKey;
-            // accumulator values (512 - 2 distance) above this can still enter the row's top two
-            float thr = kNegInf;
+            // 2 + the value (512 - 2 distance) of the thread's second-best key: the
+            // thread's later columns have larger train indices, so one displaces a key
+            // of the thread only with a larger value (values are even integers)
+            float vown2 = kNegInf;
             // the thread's columns in the problem's last train tile that lie inside the
             // train set (the rest are rows of zeros or of the next problem)
             const int32_t n_last = u.ntl - 1;
@@ -536,9 +542,12 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                         top2_insert_u64((static_cast<uint64_t>(d) << 32) | idx, k1, k2);
                     }
                 }
-                // later columns of this tile have larger train indices: one enters the
-                // top two only with a distance below the second-best's
-                if (k2 != kNoKey) thr = static_cast<float>(512 - 2 * static_cast<int32_t>(k2 >> 32));
+                // the row's bound: the smallest second-best distance of its column groups
+                if (k2 != kNoKey) {
+                    const int32_t d2 = static_cast<int32_t>(k2 >> 32);
+                    vown2 = static_cast<float>(514 - 2 * d2);
+                    atomicMin(&sBound[row_in_tile], d2);
+                }
             };
             const int32_t n_end = u.n + run.len;
             for (int32_t n = u.n; n < n_end; ++n) {
@@ -556,6 +565,12 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                     float ma, mb;
                     tmem_ld_red_max_32x32b_x16(base, va, ma);
                     tmem_ld_red_max_32x32b_x16(base + kLdCols, vb, mb);
+                    // some column group of the row holds two keys at distance <= bound, so a
+                    // column enters the row's final top two only at a distance <= bound
+                    // (equal: when its index is lower than a key's of another group), i.e.
+                    // with a value >= 512 - 2 bound, and only above the thread's second best
+                    const float vmin = fmaxf(
+                        static_cast<float>(512 - 2 * *static_cast<volatile int32_t*>(&sBound[row_in_tile])), vown2);
                     tmem_ld_wait();
                     tc_fence_before();
                     __syncwarp();
@@ -574,10 +589,9 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                             if (j < kLdCols) ma = fmaxf(ma, e[j]); else mb = fmaxf(mb, e[j]);
                         }
                     }
-                    // only a half that reaches above the row's running threshold takes the
-                    // top-two update
-                    if (__any_sync(0xffffffffu, ma > thr)) update(e, 0, n);
-                    if (__any_sync(0xffffffffu, mb > thr)) update(e, 1, n);
+                    // only a half that reaches the row's bound takes the top-two update
+                    if (__any_sync(0xffffffffu, ma >= vmin)) update(e, 0, n);
+                    if (__any_sync(0xffffffffu, mb >= vmin)) update(e, 1, n);
                 }
                 if (++acc == kAccs) acc = 0;
             }
@@ -589,8 +603,9 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
             const int64_t g = u.g(batch);
             sPart[2 * et] = k1;
             sPart[2 * et + 1] = k2;
-            group_sync();
+            group_sync();  // every thread is past the run's last bound read
             if (cg == 0) {
+                sBound[row_in_tile] = kNoBound;
 #pragma unroll
                 for (int q = 1; q < kColGroups; ++q) {
                     top2_insert_u64(sPart[2 * (q * kRowsQ + row_in_tile)], k1, k2);

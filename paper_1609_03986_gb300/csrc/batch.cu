@@ -122,11 +122,10 @@ extern "C" latch_status latch_batch_run(latch_context* ctx, const latch_batch_de
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     uint8_t* base = static_cast<uint8_t*>(scratch);
     cudaEvent_t* ev = (ctx->trace_ev && ctx->trace_n < ctx->trace_cap) ? ctx->trace_ev + 3 * ctx->trace_n++ : nullptr;
-    // the extraction also writes the matcher's expanded rows and popcounts when
-    // there is matching to do
+    // the extraction also writes the matcher's expanded rows when there is
+    // matching to do
     const bool matching = b->n_pairs > 0 && plan.total_out > 0;
     uint8_t* mbase = base + plan.ext_bytes;
-    const size_t exp_bytes = (static_cast<size_t>(plan.total_kp) * kExpRowBytes + 1023) / 1024 * 1024;
     if (ev) cudaEventRecord(ev[0], s);
     if (matching) {
         // cleared before the extraction, so that nothing sits between the extraction
@@ -140,8 +139,7 @@ extern "C" latch_status latch_batch_run(latch_context* ctx, const latch_batch_de
     if (plan.total_kp > 0) {
         st = cuda_check(ctx,
                         launch_extract_batch(ctx, b->h_images, plan.kp0.data(), plan.n.data(), b->n_images, b->d_kps,
-                                             b->d_desc, base, s, matching ? mbase : nullptr,
-                                             matching ? reinterpret_cast<int32_t*>(mbase + exp_bytes) : nullptr),
+                                             b->d_desc, base, s, matching ? mbase : nullptr),
                         "batched extraction launch");
         if (st != LATCH_OK) return st;
     }

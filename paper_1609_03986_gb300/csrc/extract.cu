@@ -34,8 +34,7 @@
 //        __dp4a, all exact in 32-bit integers.  Each warp writes its bytes of
 //        every lane's descriptor (bit t = bit t % 8 of byte t / 8) and, when
 //        the caller also wants the tensor matcher's input, its 16 bytes of the
-//        expanded row (4-bit value t = E2M1 1.0 or 0 for bit t) and adds its
-//        bits to the popcount (which the sort zeroes).
+//        expanded row (4-bit value t = E2M1 -1.0 or +1.0 for bit t set or clear).
 //    The stages hand the window buffers over through mbarriers (full: 384
 //    builder arrivals, empty: 16 evaluator arrivals); every wait is bounded.
 #include <cuda.h>
@@ -137,7 +136,7 @@ template <int NI>
 __global__ void __launch_bounds__(kSortThreads) sort_count_kernel(
     const __grid_constant__ ExtractParams<NI> prm, const latch_keypoint* __restrict__ kps, int* __restrict__ cells,
     int* __restrict__ rank, int* __restrict__ img_tot, int* __restrict__ img_done, uint4* __restrict__ out,
-    uint4* __restrict__ exp_out, int32_t* __restrict__ pop_out, uint32_t* __restrict__ flags) {
+    uint4* __restrict__ exp_out, uint32_t* __restrict__ flags) {
     __shared__ int s_part[kSortThreads / 32];
     __shared__ int s_flag;
     griddep_wait();
@@ -160,7 +159,6 @@ __global__ void __launch_bounds__(kSortThreads) sort_count_kernel(
         const int c = i < n ? cell_of(kp[q], prm.nscales, g) : -3;
         if (c >= 0) {
             rank[kp0 + i] = atomicAdd(&cnt[c], 1);
-            if (pop_out) pop_out[kp0 + i] = 0;  // the extraction adds the chunks' counts
             ++valid;
         } else if (c > -3) {
             const uint4 z = make_uint4(0, 0, 0, 0);
@@ -169,10 +167,10 @@ __global__ void __launch_bounds__(kSortThreads) sort_count_kernel(
             d[1] = z;
             d[2] = z;
             d[3] = z;
-            if (exp_out) {
-                uint4* x = exp_out + static_cast<size_t>(kp0 + i) * 32;
-                for (int u = 0; u < 32; ++u) x[u] = z;
-                pop_out[kp0 + i] = 0;
+            if (exp_out) {  // the expanded row of the zero descriptor: every value +1.0
+                uint4* x = exp_out + static_cast<size_t>(kp0 + i) * (kExpRowBytes / 16);
+                const uint4 one = expand_word_e2m1(0u);
+                for (int u = 0; u < kExpRowBytes / 16; ++u) x[u] = one;
             }
             bad |= (c == -2);
         }
@@ -397,8 +395,7 @@ __global__ void __launch_bounds__(kThreads, 1) extract_lanes_kernel(
     const __grid_constant__ ExtractParams<NI> prm, const __grid_constant__ LaneTriplets tt,
     const __grid_constant__ PatchWeights pw,
     const int4* __restrict__ recs, const int* __restrict__ counters, const int16_t* __restrict__ toff,
-    uint8_t* __restrict__ out, uint8_t* __restrict__ exp_out, int32_t* __restrict__ pop_out,
-    uint32_t* __restrict__ flags) {
+    uint8_t* __restrict__ out, uint8_t* __restrict__ exp_out, uint32_t* __restrict__ flags) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ LanesSmem S;
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -588,7 +585,7 @@ __global__ void __launch_bounds__(kThreads, 1) extract_lanes_kernel(
         __syncwarp();
         if (lane == 0) mbar_arrive(&S.empty[buf]);  // the windows and rows are free again
         if (wb == wa) continue;
-        // ---- descriptor bytes [wa, wb), expanded bytes [8 wa, 8 wb), popcount ----
+        // ---- descriptor bytes [wa, wb), expanded bytes [8 wa, 8 wb) ----
         if (wb - wa == 4 && (wa & 3) == 0) {
             if (lane < nk) reinterpret_cast<uint32_t*>(out + static_cast<size_t>(row) * kDescBytes)[wa >> 2] = v;
             if (exp_out && lane < nk)  // the word's 32 expanded values: 16 bytes of the lane's row
@@ -604,7 +601,6 @@ __global__ void __launch_bounds__(kThreads, 1) extract_lanes_kernel(
                         expand_byte_e2m1(byte);
             }
         }
-        if (exp_out && lane < nk) atomicAdd(pop_out + row, __popc(v));
     }
 }
 
@@ -731,7 +727,7 @@ static cudaError_t set_extract_attributes() {
 template <int NI>
 static cudaError_t launch_chunk(const latch_context* ctx, const latch_image* imgs, const int64_t* kp0,
                                 const int64_t* n, int i0, int i1, const latch_keypoint* d_kps, uint8_t* d_out,
-                                uint8_t* exp_out, int32_t* pop_out, uint8_t* scratch, cudaStream_t stream,
+                                uint8_t* exp_out, uint8_t* scratch, cudaStream_t stream,
                                 uint32_t* flags, const int32_t* n_dev) {
     static unsigned long long attr_done[2] = {0, 0};
     const TileGeom tg = tile_geom(ctx->reach);
@@ -780,7 +776,7 @@ static cudaError_t launch_chunk(const latch_context* ctx, const latch_image* img
     if (e == cudaSuccess)
         e = launch_chained(sort_count_kernel<NI>, dim3(blocks), dim3(kSortThreads), 0, stream, *prm, d_kps, cells,
                            rank, img_tot, img_done, reinterpret_cast<uint4*>(d_out),
-                           reinterpret_cast<uint4*>(exp_out), pop_out, flags);
+                           reinterpret_cast<uint4*>(exp_out), flags);
     if (e == cudaSuccess)
         e = launch_chained(sort_scatter_kernel<NI>, dim3(blocks), dim3(kSortThreads), 0, stream, *prm, d_kps,
                            static_cast<const int*>(cells), static_cast<const int*>(rank),
@@ -797,7 +793,7 @@ static cudaError_t launch_chunk(const latch_context* ctx, const latch_image* img
         e = launch_chained(ctx->weighted ? extract_lanes_kernel<NI, true> : extract_lanes_kernel<NI, false>,
                            dim3(static_cast<unsigned>(grid)), dim3(kThreads), extract_smem_bytes(tg), stream, *prm, *tt,
                            pw, static_cast<const int4*>(recs), static_cast<const int*>(counters), ctx->d_tile_offsets,
-                           d_out, exp_out, pop_out, flags);
+                           d_out, exp_out, flags);
         delete tt;
     }
     delete prm;
@@ -806,8 +802,7 @@ static cudaError_t launch_chunk(const latch_context* ctx, const latch_image* img
 
 cudaError_t launch_extract_batch(const latch_context* ctx, const latch_image* imgs, const int64_t* kp0,
                                  const int64_t* n, int count, const latch_keypoint* d_kps, uint8_t* d_out,
-                                 void* scratch, cudaStream_t stream, uint8_t* exp_out, int32_t* pop_out,
-                                 uint32_t* flags) {
+                                 void* scratch, cudaStream_t stream, uint8_t* exp_out, uint32_t* flags) {
     uint8_t* base = static_cast<uint8_t*>(scratch);
     if (!flags) flags = ctx->d_flags;
     for (int i0 = 0; i0 < count; i0 += kBatchImages) {
@@ -819,11 +814,11 @@ cudaError_t launch_extract_batch(const latch_context* ctx, const latch_image* im
             // instance that fits keeps the launch's parameter block small
             const int ni = i1 - i0;
             const cudaError_t e =
-                ni == 1    ? launch_chunk<1>(ctx, imgs, kp0, n, i0, i1, d_kps, d_out, exp_out, pop_out, base, stream, flags, nullptr)
-                : ni <= 4  ? launch_chunk<4>(ctx, imgs, kp0, n, i0, i1, d_kps, d_out, exp_out, pop_out, base, stream, flags, nullptr)
-                : ni <= 16 ? launch_chunk<16>(ctx, imgs, kp0, n, i0, i1, d_kps, d_out, exp_out, pop_out, base, stream, flags, nullptr)
-                           : launch_chunk<kBatchImages>(ctx, imgs, kp0, n, i0, i1, d_kps, d_out, exp_out, pop_out,
-                                                        base, stream, flags, nullptr);
+                ni == 1    ? launch_chunk<1>(ctx, imgs, kp0, n, i0, i1, d_kps, d_out, exp_out, base, stream, flags, nullptr)
+                : ni <= 4  ? launch_chunk<4>(ctx, imgs, kp0, n, i0, i1, d_kps, d_out, exp_out, base, stream, flags, nullptr)
+                : ni <= 16 ? launch_chunk<16>(ctx, imgs, kp0, n, i0, i1, d_kps, d_out, exp_out, base, stream, flags, nullptr)
+                           : launch_chunk<kBatchImages>(ctx, imgs, kp0, n, i0, i1, d_kps, d_out, exp_out, base,
+                                                        stream, flags, nullptr);
             if (e != cudaSuccess) return e;
         }
         base += chunk_layout(imgs, n, i0, i1).total;
@@ -834,7 +829,7 @@ cudaError_t launch_extract_batch(const latch_context* ctx, const latch_image* im
 cudaError_t launch_extract(const latch_context* ctx, const latch_image* img, const latch_keypoint* d_kps, int32_t n,
                            uint8_t* d_out, void* scratch, cudaStream_t stream) {
     const int64_t kp0 = 0, nn = n;
-    return launch_extract_batch(ctx, img, &kp0, &nn, 1, d_kps, d_out, scratch, stream, nullptr, nullptr);
+    return launch_extract_batch(ctx, img, &kp0, &nn, 1, d_kps, d_out, scratch, stream, nullptr);
 }
 
 cudaError_t launch_extract_dev_count(const latch_context* ctx, const latch_image* img, const latch_keypoint* d_kps,
@@ -842,7 +837,7 @@ cudaError_t launch_extract_dev_count(const latch_context* ctx, const latch_image
                                      cudaStream_t stream) {
     if (max_n <= 0) return cudaSuccess;
     const int64_t kp0 = 0, nn = max_n;
-    return launch_chunk<1>(ctx, img, &kp0, &nn, 0, 1, d_kps, d_out, nullptr, nullptr, static_cast<uint8_t*>(scratch),
+    return launch_chunk<1>(ctx, img, &kp0, &nn, 0, 1, d_kps, d_out, nullptr, static_cast<uint8_t*>(scratch),
                            stream, ctx->d_flags, d_n);
 }
 

@@ -146,13 +146,12 @@ cudaError_t launch_extract(const latch_context* ctx, const latch_image* img, con
                            uint8_t* d_out, void* scratch, cudaStream_t stream);
 size_t extract_scratch_bytes(const latch_image* img, int64_t n);
 // Images [0, count) with keypoints d_kps[kp0[i] .. kp0[i] + n[i]) -> d_out rows at the same positions.
-// When exp_out is not NULL, row r of the tensor matcher's input (kExpRowBytes bytes, E2M1 0 / 1.0
-// per bit) and pop_out[r] (the descriptor's popcount) are written as well.
+// When exp_out is not NULL, row r of the tensor matcher's input (kExpRowBytes bytes, E2M1 +-1.0
+// per bit) is written as well.
 // `flags`: the device error word the kernels raise flags in (NULL: the context's).
 cudaError_t launch_extract_batch(const latch_context* ctx, const latch_image* imgs, const int64_t* kp0,
                                  const int64_t* n, int count, const latch_keypoint* d_kps, uint8_t* d_out,
-                                 void* scratch, cudaStream_t stream, uint8_t* exp_out, int32_t* pop_out,
-                                 uint32_t* flags = nullptr);
+                                 void* scratch, cudaStream_t stream, uint8_t* exp_out, uint32_t* flags = nullptr);
 size_t extract_batch_scratch_bytes(const latch_image* imgs, const int64_t* n, int count);
 // One image whose keypoint count is on the device (*d_n, at most max_n keypoints in
 // d_kps); scratch as extract_scratch_bytes(img, max_n).

@@ -63,7 +63,7 @@ __device__ __forceinline__ void top2_insert_u64(uint64_t key, uint64_t& k1, uint
 }
 
 void plan_match_batch(MatchBatch* b, int count, int64_t max_grid);
-// Scratch of the batched layout [expanded rows][popcounts][arrival counters for
+// Scratch of the batched layout [expanded rows][arrival counters for
 // counter_tiles query tiles][partial records]; counter_tiles >= b.tiles.
 size_t match_tc_batch_scratch_bytes(int64_t rows, const MatchBatch& b, int64_t counter_tiles);
 int32_t* match_tc_batch_counters(void* scratch, int64_t rows);
@@ -72,18 +72,17 @@ size_t match_tc_counter_bytes(int64_t tiles);
 // Upper bound of match_tc_partial_bytes + match_tc_counter_bytes (each rounded up
 // to 256 bytes) for any launch over `problems` problems, `queries` query rows.
 size_t match_tc_partial_bound(int64_t queries, int64_t problems, int64_t sms);
-// The batched layout: the expanded rows and popcounts of every problem's query and
+// The batched layout: the expanded rows of every problem's query and
 // train sets must be filled already, and the arrival counters zero (a complete
 // launch leaves them zero, so consecutive launches need one clearing).
 cudaError_t launch_match_tc_batch(const MatchBatch& b, int64_t rows, int64_t counter_tiles, void* scratch,
                                   latch_match* out, uint32_t* flags, cudaStream_t stream);
-// Same with explicit buffers: `exp` holds `rows` expanded rows, `pop` their
-// popcounts, `partials` match_tc_partial_bytes(b) of scratch, `tile_cnt` b.tiles
-// zero counters (NULL: combine the records in a separate pass).
-cudaError_t launch_match_tc_rows(const MatchBatch& b, const uint8_t* exp, int64_t rows, const int32_t* pop,
-                                 uint64_t* partials, int32_t* tile_cnt, latch_match* out, uint32_t* flags,
-                                 cudaStream_t stream);
-cudaError_t launch_expand(const uint8_t* desc, int64_t n, uint8_t* out, int32_t* pop, cudaStream_t stream);
+// Same with explicit buffers: `exp` holds `rows` expanded rows, `partials`
+// match_tc_partial_bytes(b) of scratch, `tile_cnt` b.tiles zero counters (NULL:
+// combine the records in a separate pass).
+cudaError_t launch_match_tc_rows(const MatchBatch& b, const uint8_t* exp, int64_t rows, uint64_t* partials,
+                                 int32_t* tile_cnt, latch_match* out, uint32_t* flags, cudaStream_t stream);
+cudaError_t launch_expand(const uint8_t* desc, int64_t n, uint8_t* out, cudaStream_t stream);
 size_t match_tc_scratch_bytes_sms(int64_t sms, int64_t nq, int64_t nt);
 
 }  // namespace latch

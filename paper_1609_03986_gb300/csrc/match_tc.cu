@@ -293,7 +293,6 @@ template <int NP>
 __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_constant__ CUtensorMap tmq,
                                                               const __grid_constant__ CUtensorMap tmt,
                                                               const __grid_constant__ MatchBatchT<NP> batch,
-                                                              const int32_t* __restrict__ pop,
                                                               uint64_t* __restrict__ partials,
                                                               int32_t* __restrict__ tile_cnt,
                                                               latch_match* __restrict__ out,
@@ -665,21 +664,13 @@ __global__ void match_merge_kernel(const __grid_constant__ MatchBatchT<NP> batch
     out[q] = final_match(k1, k2, P.k, P.r_milli);
 }
 
-// Bits -> E2M1 0/1 values (bit t of a descriptor -> 4-bit value t, kExpRowBytes per
-// row) and per-descriptor popcount; one thread per 32-bit descriptor word.
-__global__ void expand_kernel(const uint32_t* __restrict__ in, int64_t nwords, uint4* __restrict__ out,
-                              int32_t* __restrict__ pop) {
+// Bits -> E2M1 +-1 values (bit t of a descriptor -> 4-bit value t, kExpRowBytes per
+// row); one thread per 32-bit descriptor word.
+__global__ void expand_kernel(const uint32_t* __restrict__ in, int64_t nwords, uint4* __restrict__ out) {
     griddep_wait();
     griddep_launch_dependents();
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    const uint32_t w = i < nwords ? in[i] : 0u;
-    if (i < nwords) out[i] = expand_word_e2m1(w);
-    int p = __popc(w);
-    p += __shfl_xor_sync(0xffffffffu, p, 8);
-    p += __shfl_xor_sync(0xffffffffu, p, 4);
-    p += __shfl_xor_sync(0xffffffffu, p, 2);
-    p += __shfl_xor_sync(0xffffffffu, p, 1);
-    if ((i & 15) == 0 && i < nwords) pop[i >> 4] = p;
+    if (i < nwords) out[i] = expand_word_e2m1(in[i]);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -715,13 +706,13 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 }  // namespace
 
-cudaError_t launch_expand(const uint8_t* desc, int64_t n, uint8_t* out, int32_t* pop, cudaStream_t stream) {
+cudaError_t launch_expand(const uint8_t* desc, int64_t n, uint8_t* out, cudaStream_t stream) {
     if (n == 0) return cudaSuccess;
     const int64_t nwords = n * 16;
     const int threads = 256;
     const int64_t grid = (nwords + threads - 1) / threads;
     return launch_chained(expand_kernel, dim3(static_cast<unsigned>(grid)), dim3(threads), 0, stream,
-                          reinterpret_cast<const uint32_t*>(desc), nwords, reinterpret_cast<uint4*>(out), pop);
+                          reinterpret_cast<const uint32_t*>(desc), nwords, reinterpret_cast<uint4*>(out));
 }
 
 // Fills tiles, unit offsets, query-tile prefixes and the block split.  problems[i]
@@ -763,15 +754,13 @@ size_t match_tc_partial_bound(int64_t queries, int64_t problems, int64_t sms) {
 
 size_t match_tc_batch_scratch_bytes(int64_t rows, const MatchBatch& b, int64_t counter_tiles) {
     const size_t exp_bytes = align_up(static_cast<size_t>(rows) * kKBytes, 1024);
-    const size_t pop_bytes = align_up(static_cast<size_t>(rows) * 4, 256);
-    return exp_bytes + pop_bytes + match_tc_counter_bytes(counter_tiles) + match_tc_partial_bytes(b) + 256;
+    return exp_bytes + match_tc_counter_bytes(counter_tiles) + match_tc_partial_bytes(b) + 256;
 }
 
-// The batched layout's arrival counters: [expanded rows][popcounts][counters][partials].
+// The batched layout's arrival counters: [expanded rows][counters][partials].
 int32_t* match_tc_batch_counters(void* scratch, int64_t rows) {
     const size_t exp_bytes = align_up(static_cast<size_t>(rows) * kKBytes, 1024);
-    const size_t pop_bytes = align_up(static_cast<size_t>(rows) * 4, 256);
-    return reinterpret_cast<int32_t*>(static_cast<uint8_t*>(scratch) + exp_bytes + pop_bytes);
+    return reinterpret_cast<int32_t*>(static_cast<uint8_t*>(scratch) + exp_bytes);
 }
 
 // Copies the header and the first b.count problems into the table of capacity NP.
@@ -792,7 +781,6 @@ static cudaError_t set_match_attributes() {
 
 template <int NP>
 static cudaError_t launch_match_np(const MatchBatch& full, const CUtensorMap& mapq, const CUtensorMap& mapt,
-                                   const int32_t* pop,
                                    uint64_t* partials, int32_t* tile_cnt, latch_match* out, uint32_t* flags,
                                    cudaStream_t stream) {
     static unsigned long long attr_done = 0;
@@ -806,7 +794,7 @@ static cudaError_t launch_match_np(const MatchBatch& full, const CUtensorMap& ma
     cudaError_t e = cudaSuccess;
     if (b->units > 0)
         e = launch_chained(match_tc_kernel<NP>, dim3(static_cast<unsigned>(b->grid)), dim3(kThreads), kSmemBytes,
-                           stream, mapq, mapt, *b, pop, partials, tile_cnt, out, flags);
+                           stream, mapq, mapt, *b, partials, tile_cnt, out, flags);
     if (e == cudaSuccess && !tile_cnt && b->queries > 0) {
         const int threads = 256;
         const int64_t grid = (b->queries + threads - 1) / threads;
@@ -817,8 +805,7 @@ static cudaError_t launch_match_np(const MatchBatch& full, const CUtensorMap& ma
     return e;
 }
 
-cudaError_t launch_match_tc_rows(const MatchBatch& b, const uint8_t* exp, int64_t rows, const int32_t* pop,
-                                 uint64_t* partials, int32_t* tile_cnt, latch_match* out, uint32_t* flags,
+cudaError_t launch_match_tc_rows(const MatchBatch& b, const uint8_t* exp, int64_t rows, uint64_t* partials, int32_t* tile_cnt, latch_match* out, uint32_t* flags,
                                  cudaStream_t stream) {
     if (b.queries == 0) return cudaSuccess;
     CUtensorMap mapq, mapt;
@@ -830,22 +817,20 @@ cudaError_t launch_match_tc_rows(const MatchBatch& b, const uint8_t* exp, int64_
     for (int i = 0; i < b.count; ++i)
         if (b.p[i].nq > 0 && b.p[i].ntl == 0) fused = false;
     if (!fused) tile_cnt = nullptr;
-    if (b.count <= 1) return launch_match_np<1>(b, mapq, mapt, pop, partials, tile_cnt, out, flags, stream);
-    if (b.count <= 16) return launch_match_np<16>(b, mapq, mapt, pop, partials, tile_cnt, out, flags, stream);
-    return launch_match_np<kMaxProblems>(b, mapq, mapt, pop, partials, tile_cnt, out, flags, stream);
+    if (b.count <= 1) return launch_match_np<1>(b, mapq, mapt, partials, tile_cnt, out, flags, stream);
+    if (b.count <= 16) return launch_match_np<16>(b, mapq, mapt, partials, tile_cnt, out, flags, stream);
+    return launch_match_np<kMaxProblems>(b, mapq, mapt, partials, tile_cnt, out, flags, stream);
 }
 
-// Scratch: expanded rows (rows x 512 B), popcounts, partial records.  The expanded
-// rows and popcounts must already be filled (launch_expand).
+// Scratch: expanded rows (rows x kExpRowBytes), arrival counters, partial records.
+// The expanded rows must already be filled (launch_expand).
 cudaError_t launch_match_tc_batch(const MatchBatch& b, int64_t rows, int64_t counter_tiles, void* scratch,
                                   latch_match* out, uint32_t* flags, cudaStream_t stream) {
     uint8_t* base = static_cast<uint8_t*>(scratch);
     const size_t exp_bytes = align_up(static_cast<size_t>(rows) * kKBytes, 1024);
-    const size_t pop_bytes = align_up(static_cast<size_t>(rows) * 4, 256);
     const size_t cnt_bytes = match_tc_counter_bytes(counter_tiles);
-    return launch_match_tc_rows(b, base, rows, reinterpret_cast<const int32_t*>(base + exp_bytes),
-                                reinterpret_cast<uint64_t*>(base + exp_bytes + pop_bytes + cnt_bytes),
-                                reinterpret_cast<int32_t*>(base + exp_bytes + pop_bytes), out, flags, stream);
+    return launch_match_tc_rows(b, base, rows, reinterpret_cast<uint64_t*>(base + exp_bytes + cnt_bytes),
+                                reinterpret_cast<int32_t*>(base + exp_bytes), out, flags, stream);
 }
 
 static void single_problem(MatchBatch* b, int32_t nq, int32_t nt, int64_t sms, int32_t k = 2, int32_t r = 800) {
@@ -876,14 +861,12 @@ cudaError_t launch_match_tc(const latch_context* ctx, const uint8_t* q, int32_t 
     MatchBatch* b = new MatchBatch;
     single_problem(b, nq, nt, ctx->sm_count, k, r_milli);
     uint8_t* base = static_cast<uint8_t*>(scratch);
-    const size_t exp_bytes = align_up(static_cast<size_t>(nq + nt) * kKBytes, 1024);
-    int32_t* pop = reinterpret_cast<int32_t*>(base + exp_bytes);
     cudaError_t e = cudaSuccess;
     if (b->units > 0) {
         // the arrival counters are cleared ahead of the kernels, off their dependency chain
         e = cudaMemsetAsync(match_tc_batch_counters(scratch, nq + nt), 0, match_tc_counter_bytes(b->tiles), stream);
-        if (e == cudaSuccess) e = launch_expand(q, nq, base, pop, stream);
-        if (e == cudaSuccess) e = launch_expand(t, nt, base + static_cast<size_t>(nq) * kKBytes, pop + nq, stream);
+        if (e == cudaSuccess) e = launch_expand(q, nq, base, stream);
+        if (e == cudaSuccess) e = launch_expand(t, nt, base + static_cast<size_t>(nq) * kKBytes, stream);
     }
     if (e == cudaSuccess) e = launch_match_tc_batch(*b, nq + nt, b->tiles, scratch, out, ctx->d_flags, stream);
     delete b;
@@ -900,7 +883,7 @@ cudaError_t launch_match_tc(const latch_context* ctx, const uint8_t* q, int32_t 
 // from us could fail, or steal memory the application has budgeted), or a
 // latency-bound pipeline where cudaMalloc/cudaFree would synchronise the device and
 // stall the application's other streams.  hamming_match_noalloc serves them: its
-// scratch (expanded operands, popcounts, per-block partial results, status word)
+// scratch (expanded operands, per-block partial results, status word)
 // lives in the fixed array below, which the CUDA module reserves on every device
 // that loads this library for as long as the process lives.
 // ---------------------------------------------------------------------------

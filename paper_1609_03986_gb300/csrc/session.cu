@@ -35,7 +35,7 @@ namespace latch {
 namespace {
 
 constexpr int kMaxLanes = 8;
-constexpr int64_t kRowBytes = kExpRowBytes + 4;  // expanded row + popcount
+constexpr int64_t kRowBytes = kExpRowBytes;  // expanded row
 constexpr size_t kFreeMargin = size_t(512) << 20;  // device memory left free at session creation
 
 struct Ticket {
@@ -83,9 +83,8 @@ struct latch_session {
     int64_t max_batch_kps = 0;
     size_t lane_bytes = 0;
     size_t budget = 0;  // device bytes the session holds: min(caller's budget, free memory - margin)
-    // arena: [gallery rows | lane 0 query rows | lane 1 query rows | ...] x kExpRowBytes, then popcounts
+    // arena: [gallery rows | lane 0 query rows | lane 1 query rows | ...] x kExpRowBytes
     uint8_t* arena = nullptr;
-    int32_t* arena_pop = nullptr;
     int64_t arena_rows = 0;
     int64_t gallery_cap = 0;
     int64_t gallery_used = 0;
@@ -191,10 +190,9 @@ latch_status run_batch(latch_session* s, int li, DoneArg* done) {
     // the extraction writes the queries' expanded rows into the lane's arena rows
     if (e == cudaSuccess && total > 0)
         e = launch_extract_batch(s->ctx, imgs.data(), kp0.data(), n.data(), nb, d_kps, d_desc, ext_scratch, st,
-                                 s->arena + L.qrow0 * kExpRowBytes, s->arena_pop + L.qrow0, L.d_flags);
+                                 s->arena + L.qrow0 * kExpRowBytes, L.d_flags);
     if (e == cudaSuccess && total > 0)
-        e = launch_match_tc_rows(*mb, s->arena, s->arena_rows, s->arena_pop, partials, tile_cnt, d_match, L.d_flags,
-                                 st);
+        e = launch_match_tc_rows(*mb, s->arena, s->arena_rows, partials, tile_cnt, d_match, L.d_flags, st);
     for (int i = 0; i < nb && e == cudaSuccess; ++i) {
         const latch_request& r = L.batch[i]->req;
         if (r.n == 0) continue;
@@ -345,7 +343,6 @@ latch_status latch_session_create_lanes(int device, size_t hbm_budget, int64_t m
         if (cudaMalloc(&s->arena, arena_bytes) != cudaSuccess) st = LATCH_ENOMEM;
     }
     if (st == LATCH_OK) {
-        s->arena_pop = reinterpret_cast<int32_t*>(s->arena + round_up(static_cast<size_t>(s->arena_rows) * kExpRowBytes, 1024));
         for (int i = 0; i < lanes && st == LATCH_OK; ++i) {
             Lane& L = s->lanes[i];
             L.qrow0 = max_gallery_rows + i * max_batch_kps;
@@ -408,7 +405,7 @@ latch_status latch_gallery_add(latch_session* s, const uint8_t* h_desc, int32_t 
         if (cudaMalloc(&tmp, static_cast<size_t>(n) * 64) != cudaSuccess) return sfail(s, LATCH_ENOMEM, "cudaMalloc");
         cudaError_t e = cudaMemcpy(tmp, h_desc, static_cast<size_t>(n) * 64, cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
-            e = launch_expand(tmp, n, s->arena + s->gallery_used * kExpRowBytes, s->arena_pop + s->gallery_used, nullptr);
+            e = launch_expand(tmp, n, s->arena + s->gallery_used * kExpRowBytes, nullptr);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         cudaFree(tmp);
         if (e != cudaSuccess) return sfail(s, LATCH_ECUDA, cudaGetErrorString(e));

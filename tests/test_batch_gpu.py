@@ -64,6 +64,31 @@ def test_small_mixed_batch(gpu_ctx, triplets):
         _same(matches[p], oracle.match(wants[q], wants[t], 2, 0.8))
 
 
+def test_far_outside_keypoints_match_as_zero_descriptors(gpu_ctx, triplets):
+    """Keypoints so far outside their image that the window misses it get the zero
+    descriptor without being sampled; in the batched matcher they still take part on
+    both sides of a pair, at distance popc(other) (Eq. 1 with every SSD 0)."""
+    sizes = [(320, 240), (400, 300), (256, 256)]
+    imgs, kps = [], []
+    for i, (w, h) in enumerate(sizes):
+        imgs.append(synth.image(synth.seed(34, i, synth.KIND_IMAGE), w, h, n_ellipses=30))
+        k = synth.keypoints(synth.seed(34, i, synth.KIND_KEYPOINTS), w, h, 600, 0, True, 3)
+        far = np.array([[-5000, -5000], [w + 4000, 10], [20, h + 9000], [-3000, h // 2]], np.int32)
+        rows = np.arange(5 + i, 600, 37)[:len(far) * 6]
+        k[rows, 0] = np.tile(far[:, 0], 6)[:len(rows)]
+        k[rows, 1] = np.tile(far[:, 1], 6)[:len(rows)]
+        kps.append(k)
+    pairs = [(0, 1), (1, 0), (2, 2), (1, 2), (2, 0)]
+    descs, matches = _run_batch(gpu_ctx, imgs, sizes, kps, pairs)
+    wants = [oracle.extract(imgs[i], sizes[i][0], sizes[i][1], kps[i], triplets, synth.SCALES)
+             for i in range(len(imgs))]
+    for i in range(len(imgs)):
+        assert np.array_equal(descs[i], wants[i]), i
+        assert (wants[i][np.arange(5 + i, 600, 37)[:24]] == 0).all()
+    for p, (q, t) in enumerate(pairs):
+        _same(matches[p], oracle.match(wants[q], wants[t], 2, 0.8))
+
+
 def test_batch_equals_single_calls(gpu_ctx, triplets):
     """Same bytes as latch_extract per image and hamming_match per pair, for k = 1."""
     sizes = [(400, 300)] * 4

@@ -10,30 +10,32 @@
 //
 // One launch serves a batch of matching problems (query set x train set pairs; a
 // single hamming_match call is a batch of one).  All descriptors live in one
-// expanded buffer (two TMA tensor maps over it: 128-row query boxes, 160-row train
-// boxes).  The units (problem, 128-query tile, 160-train tile) of all problems are
+// expanded buffer (two TMA tensor maps over it: 128-row query boxes, 240-row train
+// boxes).  The units (problem, 128-query tile, 240-train tile) of all problems are
 // linearised and split into one contiguous range per block (one block per SM,
 // persistent):
 //   warp 0     TMA producer: the query tile (128 rows x 256 B, 32 KB) stays resident
-//              while consecutive units share it; train chunks (160 rows x 128 B, half
-//              of K) go through an 8-stage ring, 128-byte swizzle;
+//              while consecutive units share it; train chunks (240 rows x 128 B, half
+//              of K) go through a 6-stage ring, 128-byte swizzle;
 //   warps 1-2  MMA issuers (even / odd units): per unit 8 tcgen05.mma (M=128,
-//              N=160, K=64) into one of three 160-column TMEM accumulators in
-//              rotation (columns 0, 160, 320; the constant scale factors in 480-511);
-//              warp 2 also allocates TMEM;
+//              N=240, K=64) into one of two TMEM accumulators (columns 0 and 256; the
+//              constant scale factors in 496-511); warp 2 also allocates TMEM;
 //   warp 3     idle;
-//   warps 4-23 epilogue (one query row and 32 columns per thread): two reducing
-//              TMEM loads (tcgen05.ld.red .max) bring the 32 values and the largest
-//              of each 16, and the accumulator is released at once.  A half whose
-//              largest value is not above the row's running threshold (the value of
-//              its second-best match: later columns have larger train indices, so
-//              they enter the top two only with a smaller distance) costs nothing
-//              more; the others take the top-two update (max / second-max chains over
-//              64 v - column, unique values that break ties to the lower index).  When
-//              the block leaves a query tile the row's two (distance << 32 | index)
-//              keys go to a partial record; the last block to leave a tile (a per-tile
-//              arrival counter) combines the records of its rows and writes their
-//              matches (ties to the lowest train index, ratio test).
+//   warps 4-23 epilogue (one query row and 48 columns per thread): three reducing
+//              TMEM loads (tcgen05.ld.red .max) bring the 48 values and the largest
+//              of each 16, and the accumulator is released at once.  A group of 16
+//              whose largest value is below the row's bound costs nothing more: the
+//              bound is the smallest second-best distance any of the row's five
+//              column groups holds (shared memory), and a column displaces one of its
+//              own group's keys only with a larger value (later columns have larger
+//              train indices).  The others take the top-two update (max / second-max
+//              chains over 64 v - column, unique values that break ties to the lower
+//              index).  When the block leaves a query tile the row's two (distance <<
+//              32 | index) keys go to a partial record; the last block to leave a tile
+//              (a per-tile arrival counter) combines the records of its rows and writes
+//              their matches (ties to the lowest train index, ratio test).
+// The unit width is a compile-time choice (LATCH_TC_COLS): 160 gives three
+// accumulators in rotation (columns 0, 160, 320) and 32 columns per epilogue thread.
 // match_merge_kernel does the same combination as a separate pass; it serves the
 // batches in which some problem has queries but an empty train set (no unit, so no
 // block visits its tiles).  All mbarrier waits are bounded (sm103.h); on a timeout
@@ -54,32 +56,36 @@ using namespace sm103;
 
 constexpr int kRowsA = 128;             // rows per MMA (M) = queries per tile
 constexpr int kRowsQ = kRowsA;
-constexpr int kColsB = 160;             // train rows per unit (N)
+#ifndef LATCH_TC_COLS
+#define LATCH_TC_COLS 240
+#endif
+constexpr int kColsB = LATCH_TC_COLS;   // train rows per unit (N): 240 (two accumulators) or 160 (three)
 constexpr int kRowsP = kRowsQ;          // partial records per tile slot: one per query row
 constexpr int kKBytes = kExpRowBytes;   // expanded descriptor: 512 x 4-bit
 constexpr int kChunk = 128;             // K bytes per swizzle atom / TMA box
 constexpr int kChunks = kKBytes / kChunk;
 constexpr int kMmaKBytes = 32;          // K bytes per MMA: 64 E2M1 values
-constexpr int kStages = 8;              // train chunks in flight: four units
+constexpr int kStages = kColsB > 192 ? 6 : 8;  // train chunks in flight (three / four units)
 constexpr int kTileBytes = kRowsA * kChunk;   // 16 KB: a query chunk of 128 rows x 128 B (one TMA box)
-constexpr int kStageBytes = kColsB * kChunk;  // 20 KB: a train chunk of 160 rows x 128 B (one TMA box)
-constexpr int kAccs = 3;                // TMEM accumulators in rotation (unit i uses i % 3)
+constexpr int kStageBytes = kColsB * kChunk;  // a train chunk of kColsB rows x 128 B (one TMA box)
+constexpr int kAccs = kColsB > 160 ? 2 : 3;    // TMEM accumulators in rotation (unit i uses i % kAccs)
+constexpr int kAccStride = kColsB > 160 ? 256 : kColsB;  // accumulator a at TMEM columns [a kAccStride, +kColsB)
 constexpr int kEpiWarps = 20;           // epilogue: 4 lane quarters x 5 column groups
 constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kThreads = 128 + kEpiThreads;         // producer, two MMA issuers, an idle warp, then the epilogue
 constexpr int kColGroups = kEpiWarps / 4;
 constexpr int kColsPerThread = kColsB / kColGroups;  // accumulator columns one epilogue thread scans
 constexpr int kLdCols = 16;                          // columns per tcgen05.ld
+constexpr int kLds = kColsPerThread / kLdCols;       // loads per unit and thread
 constexpr int kTmemCols = 512;
-constexpr uint32_t kSfaCol = 480;       // scale factors of A: 4 columns (128 rows)
-constexpr uint32_t kSfbCol = 488;       // scale factors of B: 4 columns per 128 rows
+constexpr uint32_t kSfaCol = (kAccs - 1) * kAccStride + kColsB;  // scale factors of A: 4 columns (128 rows)
+constexpr uint32_t kSfbCol = kSfaCol + 8;  // scale factors of B: 4 columns per 128 rows
 constexpr uint32_t kScaleOne = 0x7F7F7F7Fu;  // four UE8M0 scale factors 2^0 (columns 480-511 all hold it)
 constexpr uint32_t kIdesc = idesc_mxf4_e2m1(kRowsA, kColsB);
 constexpr int32_t kNoBound = 1024;      // a distance bound above every distance (512 bits)
-static_assert(kAccs * kColsB <= static_cast<int>(kSfaCol) && kSfbCol + 8 * ((kColsB + 127) / 128) <= kTmemCols,
-              "TMEM columns overlap");
-static_assert(kColsPerThread == 2 * kLdCols, "epilogue: two 16-column loads per unit");
-static_assert(kColsB % 32 == 0 && kColsB <= 256 && kColsPerThread < 64, "unit shape");
+static_assert(kSfaCol % 8 == 0 && kSfbCol + 4 * ((kColsB + 127) / 128) <= kTmemCols, "TMEM columns overlap");
+static_assert(kColsPerThread == kLds * kLdCols && kColsB == kColGroups * kColsPerThread, "epilogue column split");
+static_assert(kColsB % 16 == 0 && kColsB <= 256 && kColsPerThread < 64 && kAccStride % 32 == 0, "unit shape");
 
 // max(a, b, c) in one instruction.
 __device__ __forceinline__ float fmax3(float a, float b, float c) {
@@ -449,7 +455,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t d = tmem + static_cast<uint32_t>(acc * kColsB);
+                    const uint32_t d = tmem + static_cast<uint32_t>(acc * kAccStride);
                     // unit j reads ring positions 2 j and 2 j + 1; its first MMA overwrites D
 #pragma unroll
                     for (int kc = 0; kc < kChunks; ++kc) {
@@ -508,8 +514,8 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
             // train set (the rest are rows of zeros or of the next problem)
             const int32_t n_last = u.ntl - 1;
             const int32_t lim_last = u.nt - n_last * kColsB - col0;
-            // the top-two update from 16 of the thread's columns (h = 0: columns 0-15,
-            // 1: 16-31) of train tile n.  w = 64 v - j orders the columns by value, then
+            // the top-two update from 16 of the thread's columns (group h: columns
+            // 16 h .. 16 h + 15) of train tile n.  w = 64 v - j orders the columns by value, then
             // by lower index, and is unique (|v| <= 512, j < 64: exact in fp32); two
             // independent max / second-max chains (even and odd columns)
             auto update = [&](const float (&e)[kColsPerThread], int h, int32_t n) {
@@ -559,11 +565,12 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                     // the thread's columns (512 - 2 Hamming, exact integers) and the largest
                     // of each half in one round trip; the accumulator is free again as soon
                     // as they are in registers
-                    const uint32_t base = lane_base + static_cast<uint32_t>(acc * kColsB);
-                    uint32_t va[kLdCols], vb[kLdCols];
-                    float ma, mb;
-                    tmem_ld_red_max_32x32b_x16(base, va, ma);
-                    tmem_ld_red_max_32x32b_x16(base + kLdCols, vb, mb);
+                    const uint32_t base = lane_base + static_cast<uint32_t>(acc * kAccStride);
+                    uint32_t v[kLds][kLdCols];
+                    float mx[kLds];
+#pragma unroll
+                    for (int h = 0; h < kLds; ++h)
+                        tmem_ld_red_max_32x32b_x16(base + static_cast<uint32_t>(h * kLdCols), v[h], mx[h]);
                     // some column group of the row holds two keys at distance <= bound, so a
                     // column enters the row's final top two only at a distance <= bound
                     // (equal: when its index is lower than a key's of another group), i.e.
@@ -576,21 +583,24 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                     if (lane == 0) mbar_arrive(&acc_empty[acc]);
                     float e[kColsPerThread];
 #pragma unroll
-                    for (int j = 0; j < kLdCols; ++j) {
-                        e[j] = __uint_as_float(va[j]);
-                        e[kLdCols + j] = __uint_as_float(vb[j]);
-                    }
-                    if (n == n_last && lim_last < kColsPerThread) {
-                        ma = mb = kNegInf;
+                    for (int h = 0; h < kLds; ++h)
 #pragma unroll
-                        for (int j = 0; j < kColsPerThread; ++j) {
-                            if (j >= lim_last) e[j] = kNegInf;
-                            if (j < kLdCols) ma = fmaxf(ma, e[j]); else mb = fmaxf(mb, e[j]);
+                        for (int j = 0; j < kLdCols; ++j) e[h * kLdCols + j] = __uint_as_float(v[h][j]);
+                    if (n == n_last && lim_last < kColsPerThread) {
+#pragma unroll
+                        for (int h = 0; h < kLds; ++h) {
+                            mx[h] = kNegInf;
+#pragma unroll
+                            for (int j = h * kLdCols; j < (h + 1) * kLdCols; ++j) {
+                                if (j >= lim_last) e[j] = kNegInf;
+                                mx[h] = fmaxf(mx[h], e[j]);
+                            }
                         }
                     }
-                    // only a half that reaches the row's bound takes the top-two update
-                    if (__any_sync(0xffffffffu, ma >= vmin)) update(e, 0, n);
-                    if (__any_sync(0xffffffffu, mb >= vmin)) update(e, 1, n);
+                    // only a group of 16 that reaches the row's bound takes the top-two update
+#pragma unroll
+                    for (int h = 0; h < kLds; ++h)
+                        if (__any_sync(0xffffffffu, mx[h] >= vmin)) update(e, h, n);
                 }
                 if (++acc == kAccs) acc = 0;
             }

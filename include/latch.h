@@ -106,7 +106,7 @@ enum {
 enum {
     LATCH_PATH_AUTO = 0,    /* chosen per shape */
     LATCH_PATH_POPC = 1,    /* XOR + population count on the CUDA cores */
-    LATCH_PATH_TENSOR = 2   /* bits expanded to 0/1 4-bit floats, dot products on the tensor cores */
+    LATCH_PATH_TENSOR = 2   /* bits expanded to +-1 4-bit floats, dot products (512 - 2 Hamming) on the tensor cores */
 };
 
 /* Create a context on CUDA device `device` (makes it current on this thread).

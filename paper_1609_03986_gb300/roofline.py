@@ -6,7 +6,7 @@ Algorithmic work (independent of how a kernel computes it):
                integer ops (subtract, multiply-add) = 100,352 int32 ops (Eq. 1).
   popc match   per pair: the 512-bit XOR and population count, 16 words each
                (Sec. 4's Hamming distance).
-  tensor match per pair: 2 x 512 multiply-adds of 0/1 values = 1,024 flop.
+  tensor match per pair: 2 x 512 multiply-adds of +-1 values = 1,024 flop.
 
 Ceilings:
   int32 ops    the measured issue rate of the plain integer add (IADD3) per SM per

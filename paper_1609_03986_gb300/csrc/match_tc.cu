@@ -515,31 +515,38 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
             const int32_t n_last = u.ntl - 1;
             const int32_t lim_last = u.nt - n_last * kColsB - col0;
             // the top-two update from 16 of the thread's columns (group h: columns
-            // 16 h .. 16 h + 15) of train tile n.  w = 64 v - j orders the columns by value, then
-            // by lower index, and is unique (|v| <= 512, j < 64: exact in fp32); two
-            // independent max / second-max chains (even and odd columns)
-            auto update = [&](const float (&e)[kColsPerThread], int h, int32_t n) {
-                float m1a = kNegInf, m2a = kNegInf, m1b = kNegInf, m2b = kNegInf;
+            // 16 h .. 16 h + 15) of train tile n.  w = 64 v - j orders the columns by
+            // value, then by lower index, and is unique (|v| <= 512, j < 64: exact in
+            // fp32); the best two of the 16 by a tournament: (max, min) of each pair,
+            // then three rounds of (a1, a2) + (b1, b2) -> (max, second max)
+            auto update = [&](const float (&e)[kColsPerThread], int h, int32_t n, float vmin) {
+                float t1[kLdCols / 2], t2[kLdCols / 2];
 #pragma unroll
-                for (int q = 0; q < kLdCols; q += 2) {
-                    const int j = h * kLdCols + q;
+                for (int q = 0; q < kLdCols / 2; ++q) {
+                    const int j = h * kLdCols + 2 * q;
                     const float wa = fmaf(e[j], 64.0f, -static_cast<float>(j));
                     const float wb = fmaf(e[j + 1], 64.0f, -static_cast<float>(j + 1));
-                    const float la = fminf(m1a, wa);
-                    m1a = fmaxf(m1a, wa);
-                    m2a = fmaxf(m2a, la);
-                    const float lb = fminf(m1b, wb);
-                    m1b = fmaxf(m1b, wb);
-                    m2b = fmaxf(m2b, lb);
+                    t1[q] = fmaxf(wa, wb);
+                    t2[q] = fminf(wa, wb);
                 }
-                // combine the chains (values are unique): (a1,a2) + (b1,b2) -> (max, second max)
-                const float hi = fmaxf(m1a, m1b), lo = fminf(m1a, m1b);
-                const float m2 = fmaxf(lo, fmaxf(m2a, m2b)), m1 = hi;
-                // the two best -> (distance << 32 | index) keys; -inf marks masked columns
+#pragma unroll
+                for (int w = kLdCols / 4; w >= 1; w >>= 1)
+#pragma unroll
+                    for (int q = 0; q < w; ++q) {
+                        const float lo = fminf(t1[q], t1[q + w]);
+                        t1[q] = fmaxf(t1[q], t1[q + w]);
+                        t2[q] = fmaxf(lo, fmaxf(t2[q], t2[q + w]));
+                    }
+                const float m1 = t1[0], m2 = t2[0];
+                // the two best -> (distance << 32 | index) keys (-inf marks masked
+                // columns); the second only where it can still enter (v >= vmin: w >=
+                // 64 vmin - 63) or the thread holds fewer than two keys, so that its own
+                // second-best stays defined
+                const bool want2 = m2 >= fmaf(vmin, 64.0f, -63.0f) || k2 == kNoKey;
 #pragma unroll
                 for (int b = 0; b < 2; ++b) {
                     const float mv = b == 0 ? m1 : m2;
-                    if (mv != kNegInf) {
+                    if (mv != kNegInf && (b == 0 || want2)) {
                         const int32_t w = static_cast<int32_t>(mv);
                         const int32_t j = (-w) & 63;
                         const int32_t d = 256 - ((w + j) >> 7);  // v = (w + j) / 64, d = (512 - v) / 2
@@ -600,7 +607,7 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                     // only a group of 16 that reaches the row's bound takes the top-two update
 #pragma unroll
                     for (int h = 0; h < kLds; ++h)
-                        if (__any_sync(0xffffffffu, mx[h] >= vmin)) update(e, h, n);
+                        if (__any_sync(0xffffffffu, mx[h] >= vmin)) update(e, h, n, vmin);
                 }
                 if (++acc == kAccs) acc = 0;
             }

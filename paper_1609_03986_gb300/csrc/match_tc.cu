@@ -28,17 +28,18 @@
 //              bound is the smallest second-best distance any of the row's five
 //              column groups holds (shared memory), and a column displaces one of its
 //              own group's keys only with a larger value (later columns have larger
-//              train indices).  The others take the top-two update (max / second-max
-//              chains over 64 v - column, unique values that break ties to the lower
-//              index).  When the block leaves a query tile the row's two (distance <<
-//              32 | index) keys go to a partial record; the last block to leave a tile
-//              (a per-tile arrival counter) combines the records of its rows and writes
+//              train indices).  The others take the top-two update (a tournament over
+//              64 v - column, unique values that break ties to the lower index).  When
+//              the block leaves a query tile the row's two (distance << 32 | index)
+//              keys go to a partial record.  In a launch of at most
+//              kFusedUnitsPerBlock units per block the last block to leave a tile (a
+//              per-tile arrival counter) combines the records of its rows and writes
 //              their matches (ties to the lowest train index, ratio test).
 // The unit width is a compile-time choice (LATCH_TC_COLS): 160 gives three
 // accumulators in rotation (columns 0, 160, 320) and 32 columns per epilogue thread.
-// match_merge_kernel does the same combination as a separate pass; it serves the
-// batches in which some problem has queries but an empty train set (no unit, so no
-// block visits its tiles).  All mbarrier waits are bounded (sm103.h); on a timeout
+// match_merge_kernel does the same combination as a separate pass; it serves longer
+// launches and the batches in which some problem has queries but an empty train set
+// (no unit, so no block visits its tiles).  All mbarrier waits are bounded (sm103.h); on a timeout
 // the block raises the device flag, drains its copies and MMAs, frees TMEM.
 #include <cuda.h>
 
@@ -83,6 +84,7 @@ constexpr uint32_t kSfbCol = kSfaCol + 8;  // scale factors of B: 4 columns per 
 constexpr uint32_t kScaleOne = 0x7F7F7F7Fu;  // four UE8M0 scale factors 2^0 (columns 480-511 all hold it)
 constexpr uint32_t kIdesc = idesc_mxf4_e2m1(kRowsA, kColsB);
 constexpr int32_t kNoBound = 1024;      // a distance bound above every distance (512 bits)
+constexpr int64_t kFusedUnitsPerBlock = 64;  // longer launches combine the tiles' records in a separate pass
 static_assert(kSfaCol % 8 == 0 && kSfbCol + 4 * ((kColsB + 127) / 128) <= kTmemCols, "TMEM columns overlap");
 static_assert(kColsPerThread == kLds * kLdCols && kColsB == kColGroups * kColsPerThread, "epilogue column split");
 static_assert(kColsB % 16 == 0 && kColsB <= 256 && kColsPerThread < 64 && kAccStride % 32 == 0, "unit shape");
@@ -828,9 +830,13 @@ cudaError_t launch_match_tc_rows(const MatchBatch& b, const uint8_t* exp, int64_
     CUtensorMap mapq, mapt;
     if (b.units > 0 && !(make_map(&mapq, exp, rows, kRowsA) && make_map(&mapt, exp, rows, kColsB)))
         return cudaErrorInvalidValue;
-    // the matcher combines each query tile's records itself unless some problem has
-    // queries but no train rows (its tiles have no unit, so no block visits them)
-    bool fused = b.units > 0 && tile_cnt != nullptr;
+    // a short launch (at most kFusedUnitsPerBlock units per block) combines each query
+    // tile's records itself, which saves the merge launch; a long one leaves them to
+    // match_merge_kernel, because the combine at a tile's end (a fence and an atomic
+    // round trip per block) holds the epilogue while the MMAs can run only an
+    // accumulator's worth ahead.  Neither when some problem has queries but no train
+    // rows (its tiles have no unit, so no block visits them).
+    bool fused = b.units > 0 && tile_cnt != nullptr && b.units <= kFusedUnitsPerBlock * b.grid;
     for (int i = 0; i < b.count; ++i)
         if (b.p[i].nq > 0 && b.p[i].ntl == 0) fused = false;
     if (!fused) tile_cnt = nullptr;

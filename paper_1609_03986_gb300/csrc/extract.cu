@@ -556,22 +556,27 @@ __global__ void __launch_bounds__(kThreads, 1) extract_lanes_kernel(
         return;
     }
 
-    // ================= evaluators =================
+    // ================= evaluators (named barrier 2) =================
     const int cw = warp - kBuildWarps;
+    const int ct = cw * 32 + lane;  // 0 .. kComputeThreads - 1
     for (int bt = bfirst; bt <= blast; ++bt) {
         const int i = bt - bfirst, buf = i & 1;
         const int nk = nrec - kBatch * bt < kBatch ? nrec - kBatch * bt : kBatch;
         const int64_t bu = static_cast<int64_t>(bt) * kChunks;  // the batch's first chunk
         const int ca = static_cast<int>((u0 > bu ? u0 : bu) - bu);
         const int cb = static_cast<int>((u1 < bu + kChunks ? u1 : bu + kChunks) - bu);
-        if (!mbar_wait(&S.full[buf], (i >> 1) & 1, abort)) {
-            if (lane == 0) atomicOr(flags, kFlagTimeout);
+        // the evaluator warps agree on the outcome of the wait, so that all of them
+        // reach the barriers below or none does
+        const bool got = mbar_wait(&S.full[buf], (i >> 1) & 1, abort);
+        if (!bar_and<2, kComputeThreads>(got)) {
+            if (!got && lane == 0) atomicOr(flags, kFlagTimeout);
             return;
         }
         // ---- Eq. 1: this warp's chunks [wa, wb), lane = keypoint ----
         const int n = cb - ca;
         const int wa = ca + cw * n / kComputeWarps, wb = ca + (cw + 1) * n / kComputeWarps;
-        const uint32_t* wl = s_win0 + buf * (kBatch * kLaneWords) + lane * kLaneWords;
+        uint32_t* wbuf = s_win0 + buf * (kBatch * kLaneWords);
+        const uint32_t* wl = wbuf + lane * kLaneWords;
         uint32_t v = 0;  // byte c - wa: chunk c
 #pragma unroll 1
         for (int c = wa; c < wb; ++c) {
@@ -580,26 +585,43 @@ __global__ void __launch_bounds__(kThreads, 1) extract_lanes_kernel(
             else
                 v |= eval_chunk(S.trip, wl, c) << (8 * (c - wa));
         }
-        // output row of this lane's keypoint
+        if (n == kChunks) {
+            // ---- the whole batch is this block's: warp cw holds bytes [4 cw, 4 cw + 4)
+            // of every lane's descriptor.  Once every warp is done with the windows,
+            // the words are staged in the buffer's head (transposed: word cw of lane r at
+            // [cw][r]) and whole rows leave as 16-byte stores: 4 threads per 64-byte
+            // descriptor, 16 per 256-byte expanded row ----
+            bar_sync<2, kComputeThreads>();
+            wbuf[cw * kBatch + lane] = v;
+            bar_sync<2, kComputeThreads>();
+            if (ct < 4 * nk) {
+                const int r = ct >> 2, q = ct & 3;
+                const uint4 d = make_uint4(wbuf[(4 * q) * kBatch + r], wbuf[(4 * q + 1) * kBatch + r],
+                                           wbuf[(4 * q + 2) * kBatch + r], wbuf[(4 * q + 3) * kBatch + r]);
+                reinterpret_cast<uint4*>(out + static_cast<size_t>(S.row[buf][r]) * kDescBytes)[q] = d;
+            }
+            if (exp_out && ct < 16 * nk) {
+                const int r = ct >> 4, w = ct & 15;
+                reinterpret_cast<uint4*>(exp_out + static_cast<size_t>(S.row[buf][r]) * kExpRowBytes)[w] =
+                    expand_word_e2m1(wbuf[w * kBatch + r]);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.empty[buf]);  // the windows and rows are free again
+            continue;
+        }
+        // ---- a batch shared with the neighbouring block: this block's bytes [ca, cb)
+        // only, descriptor bytes [wa, wb) and expanded bytes [8 wa, 8 wb) per warp ----
         const int32_t row = S.row[buf][lane];
         __syncwarp();
         if (lane == 0) mbar_arrive(&S.empty[buf]);  // the windows and rows are free again
-        if (wb == wa) continue;
-        // ---- descriptor bytes [wa, wb), expanded bytes [8 wa, 8 wb) ----
-        if (wb - wa == 4 && (wa & 3) == 0) {
-            if (lane < nk) reinterpret_cast<uint32_t*>(out + static_cast<size_t>(row) * kDescBytes)[wa >> 2] = v;
-            if (exp_out && lane < nk)  // the word's 32 expanded values: 16 bytes of the lane's row
-                reinterpret_cast<uint4*>(exp_out + static_cast<size_t>(row) * kExpRowBytes)[wa >> 2] =
-                    expand_word_e2m1(v);
-        } else if (lane < nk) {
-            uint8_t* d = out + static_cast<size_t>(row) * kDescBytes;
-            for (int c = wa; c < wb; ++c) {
-                const uint32_t byte = (v >> (8 * (c - wa))) & 0xffu;
-                d[c] = static_cast<uint8_t>(byte);
-                if (exp_out)
-                    reinterpret_cast<uint32_t*>(exp_out + static_cast<size_t>(row) * kExpRowBytes)[c] =
-                        expand_byte_e2m1(byte);
-            }
+        if (wb == wa || lane >= nk) continue;
+        uint8_t* d = out + static_cast<size_t>(row) * kDescBytes;
+        for (int c = wa; c < wb; ++c) {
+            const uint32_t byte = (v >> (8 * (c - wa))) & 0xffu;
+            d[c] = static_cast<uint8_t>(byte);
+            if (exp_out)
+                reinterpret_cast<uint32_t*>(exp_out + static_cast<size_t>(row) * kExpRowBytes)[c] =
+                    expand_byte_e2m1(byte);
         }
     }
 }

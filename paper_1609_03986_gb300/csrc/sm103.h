@@ -90,6 +90,12 @@ __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
+// Named barrier `kId` of `kCount` threads (memory ordering among them).
+template <int kId, int kCount>
+__device__ __forceinline__ void bar_sync() {
+    asm volatile("bar.sync %0, %1;" ::"n"(kId), "n"(kCount) : "memory");
+}
+
 // AND of `v` over the `kCount` threads meeting at named barrier `kId` (a barrier
 // with memory ordering among them, like __syncthreads_and for a part of a block).
 template <int kId, int kCount>

@@ -290,10 +290,10 @@ def _sfm_config(wl):
     return {"workload": HEADLINE, "images": f"{len(wl['images'])} x {wl['width']}x{wl['height']} u8",
             "keypoints": f"{min(n)}-{max(n)} per image, {n_desc} in all, 32 angle bins, scales 1/1.5/2.25",
             "pairs": f"{len(wl['pairs'])} (each image against its next 8), top-2 ratio 0.8, {pairs:.4e} pairs",
-            "entry": "latch_batch_run (one sort, one extraction, one tensor-core matching launch) replayed "
+            "entry": "latch_batch_run (one sort, one extraction, one tensor-core matching launch and its merge pass) replayed "
                      "from a CUDA graph",
             "l2": "inputs (768 MB of images) larger than L2; a 256 MB L2 flush between timed steps as well",
-            "match_path": "tensor (tcgen05 kind::mxf4, E2M1 0/1, block scales 2^0)"}
+            "match_path": "tensor (tcgen05 kind::mxf4, E2M1 +-1, block scales 2^0)"}
 
 
 def bench_sfm_batch(args, local, ws):

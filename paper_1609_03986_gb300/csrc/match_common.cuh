@@ -38,7 +38,8 @@ struct MatchProblem {
 template <int NP>
 struct MatchBatchT {
     int32_t count;
-    int32_t tiles;  // query tiles over all problems (sum of mt)
+    int32_t tiles;        // query tiles over all problems (sum of mt)
+    int32_t whole_tiles;  // 1: shares are whole query tiles (one owner per tile)
     int64_t units, grid, queries;
     MatchProblem p[NP];
 };

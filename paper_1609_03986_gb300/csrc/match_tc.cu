@@ -85,6 +85,7 @@ constexpr uint32_t kScaleOne = 0x7F7F7F7Fu;  // four UE8M0 scale factors 2^0 (co
 constexpr uint32_t kIdesc = idesc_mxf4_e2m1(kRowsA, kColsB);
 constexpr int32_t kNoBound = 1024;      // a distance bound above every distance (512 bits)
 constexpr int64_t kFusedUnitsPerBlock = 64;  // longer launches combine the tiles' records in a separate pass
+constexpr int64_t kWholeTilesPerBlock = 8;   // batches with this many query tiles per block share whole tiles
 static_assert(kSfaCol % 8 == 0 && kSfbCol + 4 * ((kColsB + 127) / 128) <= kTmemCols, "TMEM columns overlap");
 static_assert(kColsPerThread == kLds * kLdCols && kColsB == kColGroups * kColsPerThread, "epilogue column split");
 static_assert(kColsB % 16 == 0 && kColsB <= 256 && kColsPerThread < 64 && kAccStride % 32 == 0, "unit shape");
@@ -137,6 +138,16 @@ __device__ __noinline__ Share next_share(const B& b, int p, int64_t c) {
         const MatchProblem& P = b.p[p];
         const int64_t U = static_cast<int64_t>(P.mt) * P.ntl;
         if (U == 0) continue;
+        if (b.whole_tiles) {
+            // tiles [start(c'), start(c' + 1)) of the problem's mt, c' rotated by the
+            // problem's first tile index
+            const int64_t rot = P.g0 % b.grid;
+            const int64_t cp = c >= rot ? c - rot : c - rot + b.grid;
+            const int64_t t0 = split_start(cp, P.mt, b.grid), t1 = split_start(cp + 1, P.mt, b.grid);
+            if (t1 > t0)
+                return Share{p, static_cast<int32_t>(t0), 0, static_cast<int32_t>(cp), (t1 - t0) * P.ntl};
+            continue;
+        }
         const int64_t rot = P.unit0 % b.grid;
         const int64_t cp = c >= rot ? c - rot : c - rot + b.grid;
         const int64_t s0 = split_start(cp, U, b.grid), s1 = split_start(cp + 1, U, b.grid);
@@ -245,6 +256,10 @@ struct RunIter {
 // so the owners are those of the tile's ntl units.
 template <class B, class F>
 __device__ __forceinline__ int64_t for_each_owner(const B& b, const MatchProblem& P, int64_t m, F&& f) {
+    if (b.whole_tiles) {
+        f(split_owner(m, P.mt, b.grid));
+        return 1;
+    }
     const int64_t U = static_cast<int64_t>(P.mt) * P.ntl;
     const int64_t u0 = m * P.ntl;
     if (U >= b.grid) {
@@ -259,6 +274,7 @@ __device__ __forceinline__ int64_t for_each_owner(const B& b, const MatchProblem
 // Number of blocks that hold a record of query tile m of problem P.
 template <class B>
 __device__ __forceinline__ int64_t tile_owner_count(const B& b, const MatchProblem& P, int64_t m) {
+    if (b.whole_tiles) return 1;
     const int64_t U = static_cast<int64_t>(P.mt) * P.ntl;
     if (U < b.grid) return P.ntl;
     const int64_t u0 = m * P.ntl;
@@ -629,13 +645,19 @@ __global__ void __launch_bounds__(kThreads, 1) match_tc_kernel(const __grid_cons
                     top2_insert_u64(sPart[2 * (q * kRowsQ + row_in_tile)], k1, k2);
                     top2_insert_u64(sPart[2 * (q * kRowsQ + row_in_tile) + 1], k1, k2);
                 }
-                uint64_t* rec = partials + (u.slot(batch) * kRowsP + row_in_tile) * 2;
-                rec[0] = k1;
-                rec[1] = k2;
-                if (tile_cnt) __threadfence();  // the records are published before the arrival below
+                if (batch.whole_tiles) {
+                    // the block owns the whole tile: the row's two keys are final
+                    const int64_t row = m * kRowsQ + row_in_tile;
+                    if (row < P.nq) out[P.out0 + row] = final_match(k1, k2, P.k, P.r_milli);
+                } else {
+                    uint64_t* rec = partials + (u.slot(batch) * kRowsP + row_in_tile) * 2;
+                    rec[0] = k1;
+                    rec[1] = k2;
+                    if (tile_cnt) __threadfence();  // the records are published before the arrival below
+                }
             }
             group_sync();  // the shared records are free for the next run
-            if (tile_cnt) {
+            if (tile_cnt && !batch.whole_tiles) {
                 // the last owner of the tile to arrive combines the records
                 if (et == 0) {
                     const bool last = atomicAdd(&tile_cnt[g], 1) == tile_owner_count(batch, P, m) - 1;
@@ -753,6 +775,14 @@ void plan_match_batch(MatchBatch* b, int count, int64_t max_grid) {
     b->tiles = static_cast<int32_t>(g);
     b->queries = queries;
     b->grid = units < max_grid ? units : max_grid;
+    // whole query tiles per share when there are enough of them to balance the
+    // blocks (the block that walks a whole tile writes its matches directly, and a
+    // tile's walk pays its start-up -- the first units' top-two updates -- once);
+    // not when some problem has queries but no train rows (its tiles have no unit)
+    bool whole = g >= kWholeTilesPerBlock * b->grid;
+    for (int i = 0; i < count; ++i)
+        if (b->p[i].nq > 0 && b->p[i].ntl == 0) whole = false;
+    b->whole_tiles = whole ? 1 : 0;
 }
 
 // Slots g + c' + p (G - 1) (UnitIter): tiles + count (G - 1) of them.
@@ -787,6 +817,7 @@ template <int NP>
 static void shrink(const MatchBatch& b, MatchBatchT<NP>* o) {
     o->count = b.count;
     o->tiles = b.tiles;
+    o->whole_tiles = b.whole_tiles;
     o->units = b.units;
     o->grid = b.grid;
     o->queries = b.queries;
@@ -814,7 +845,7 @@ static cudaError_t launch_match_np(const MatchBatch& full, const CUtensorMap& ma
     if (b->units > 0)
         e = launch_chained(match_tc_kernel<NP>, dim3(static_cast<unsigned>(b->grid)), dim3(kThreads), kSmemBytes,
                            stream, mapq, mapt, *b, partials, tile_cnt, out, flags);
-    if (e == cudaSuccess && !tile_cnt && b->queries > 0) {
+    if (e == cudaSuccess && !tile_cnt && !b->whole_tiles && b->queries > 0) {
         const int threads = 256;
         const int64_t grid = (b->queries + threads - 1) / threads;
         e = launch_chained(match_merge_kernel<NP>, dim3(static_cast<unsigned>(grid)), dim3(threads), 0, stream, *b,

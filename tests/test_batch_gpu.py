@@ -130,6 +130,25 @@ def test_sfm_batch_full_size(gpu_ctx, triplets):
         same_matches(matches[p], want, picks[p])
 
 
+def test_whole_tile_shares_every_row(gpu_ctx, triplets):
+    """A batch with at least 8 query tiles per block (72 pairs x 21 tiles of 128
+    queries) takes whole query tiles per block, and each block writes its tiles'
+    matches itself: every match row of every pair equals the oracle's (sharded over
+    the host cores), ragged query and train tiles included."""
+    nimg, w, h = 24, 640, 480
+    imgs = [synth.image(synth.seed(36, i, synth.KIND_IMAGE), w, h, n_ellipses=60) for i in range(nimg)]
+    counts = [2600 - 37 * (i % 5) for i in range(nimg)]
+    kps = [synth.keypoints(synth.seed(36, i, synth.KIND_KEYPOINTS), w, h, counts[i], 32, True, 3) for i in range(nimg)]
+    pairs = [(i, (i + d) % nimg) for i in range(nimg) for d in (1, 2, 3)]
+    assert sum(-(-counts[q] // 128) for q, _ in pairs) >= 8 * 152
+    descs, matches = _run_batch(gpu_ctx, imgs, [(w, h)] * nimg, kps, pairs)
+    wants = oracle_shards.extract_many([(im, w, h, k, triplets, synth.SCALES) for im, k in zip(imgs, kps)], per=512)
+    for i in range(nimg):
+        assert np.array_equal(descs[i], wants[i]), i
+    for p, want in enumerate(oracle_shards.match_many([(wants[q], wants[t], 2, 0.8) for q, t in pairs], per=256)):
+        same_matches(matches[p], want)
+
+
 def test_more_pairs_than_one_launch(gpu_ctx, triplets):
     """700 pairs: two matching launches share the scratch (partial records and the
     per-query-tile arrival counters, which each complete launch leaves zero).  The

@@ -12,7 +12,8 @@
 // tile and every window (79 x 79 bytes, 0 outside the image) is staged once in shared
 // memory.  Per round two triplets t and t + 256:
 //   phase A (304 threads, 2 x 38 rows x 4 segments): a thread forms the product image
-//            along 14 pixels of one row and writes 8 horizontal 7-sums;
+//            along 14 pixels of one row (each patch's 14 bytes from five aligned
+//            words) and writes 8 horizontal 7-sums;
 //   phase B (256 threads, 2 x 32 columns x 4 segments): a thread adds 7 of them
 //            vertically for 8 pixels of one column, and bit t of those pixels is
 //            box > 0 (D1 > D2, strict).
@@ -56,6 +57,7 @@ struct DenseTriplets {
 
 struct DenseSmem {
     uint8_t img[kRegion * kRegionPitch];
+    uint8_t pad[16];                            // the last row's word loads may read past it
     uint16_t off[3][kBits];                     // staged-region offset of each patch's top-left pixel
     alignas(16) int32_t h[2][2][kHRows][kHPitch];  // [round parity][triplet slot][row][column]
 };
@@ -96,15 +98,31 @@ __global__ void __launch_bounds__(kDenseThreads) dense_extract_kernel(const uint
     const int sb = lb / kTile, cb = lb - sb * kTile;
     uint32_t bits[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 
+    // the 14 bytes at p as four words (byte i in byte i % 4 of word i / 4): five
+    // aligned word loads and funnel shifts instead of 14 byte loads
+    auto load14 = [](const uint8_t* p, uint32_t (&y)[4]) {
+        const uintptr_t addr = reinterpret_cast<uintptr_t>(p);
+        const uint32_t* w = reinterpret_cast<const uint32_t*>(addr & ~static_cast<uintptr_t>(3));
+        const uint32_t sh = static_cast<uint32_t>(addr & 3u) * 8u;
+        uint32_t x[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) x[q] = w[q];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) y[q] = __funnelshift_r(x[q], x[q + 1], sh);
+    };
+    auto byte_of = [](const uint32_t (&y)[4], int i) {
+        return static_cast<int>(__byte_perm(y[i >> 2], 0u, 0x4440u | static_cast<uint32_t>(i & 3)));
+    };
     auto phase_a = [&](int k) {
         const int t = ja * kHalfBits + k;
-        const uint8_t* pa = abase + S.off[0][t];
-        const uint8_t* p1 = abase + S.off[1][t];
-        const uint8_t* p2 = abase + S.off[2][t];
+        uint32_t ya[4], y1[4], y2[4];
+        load14(abase + S.off[0][t], ya);
+        load14(abase + S.off[1][t], y1);
+        load14(abase + S.off[2][t], y2);
         int f[14];
 #pragma unroll
         for (int i = 0; i < 14; ++i) {
-            const int a = pa[i], c1 = p1[i], c2 = p2[i];
+            const int a = byte_of(ya, i), c1 = byte_of(y1, i), c2 = byte_of(y2, i);
             f[i] = (c2 - c1) * (2 * a - c1 - c2);
         }
         int h[8];

@@ -1,12 +1,14 @@
 // Batched extract-then-match (the structure-from-motion shape of Sec. 4-5: many
 // images, each matched against its neighbours).  Enqueues, on one stream:
 //   1. one bucket launch and one persistent extraction launch per 64 images; the
-//      extraction also writes every descriptor's 0/1 E4M3 row for the tensor
+//      extraction also writes every descriptor's +-1 E2M1 row for the tensor
 //      matcher (each image's set once, although it serves as query and as train
 //      in several pairs),
 //   2. one persistent tensor-core matching launch per 512 pairs, whose blocks share
-//      the (pair, query tile, train tile) units of all pairs and combine each query
-//      tile's partial results themselves.
+//      the (pair, query tile, train tile) units of all pairs: whole query tiles per
+//      block in a large batch (each block writes its tiles' matches), otherwise
+//      units, with each query tile's partial results combined in the launch (short
+//      launches) or by a merge pass.
 // Nothing is allocated once latch_reserve_batch has sized the scratch, and nothing
 // synchronises, so the whole sequence can be captured into a CUDA graph.
 #include <cmath>

@@ -2,11 +2,13 @@
 //
 // A matching launch serves a batch of problems (a query set against a train set).
 // The units of problem p -- (query tile m, train tile n), m-major -- are numbered
-// from p.unit0, and all units are split into G contiguous ranges, range c =
-// [start(c), start(c+1)) with start(c) = floor(c * U / G).  Every block writes, for
-// each query tile it touches, the two smallest keys of each query row over its
-// train tiles ("partial records", slot = tile index + block index).
-// The merge combines the records of a row.  Keys are (distance << 32) | train
+// from p.unit0.  Each problem's units are split into G contiguous shares, share c' =
+// [start(c'), start(c'+1)) with start(c') = floor(c' * U / G) (c' rotated per
+// problem); a batch with enough query tiles splits whole tiles the same way
+// (whole_tiles).  With unit shares, every block writes, for each query tile it
+// touches, the two smallest keys of each query row over its train tiles ("partial
+// records", slot = tile index + share index), and the merge combines the records of
+// a row; with whole tiles the tile's only block writes the matches.  Keys are (distance << 32) | train
 // index, so the minimum of unique keys is the nearest train descriptor with ties
 // resolved to the lowest index (Sec. 4 matching; tie and ratio readings in latch.h).
 #pragma once
